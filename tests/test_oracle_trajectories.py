@@ -1,0 +1,162 @@
+"""Pins of the oracle's trajectory simulators and error estimator (CPU only)."""
+import copy
+import math
+
+import numpy as np
+import pytest
+
+from oracle import adjoint as A
+from oracle import trajectories as T
+from oracle import unravel as U
+from paper_2508_05745_gb300 import inputs as I
+
+
+@pytest.fixture(scope="module")
+def small():
+    return I.workload_small_exact(seed=0)
+
+
+def test_dense_and_mps_agree_without_truncation(small):
+    """chi >= 2^{n/2}: the MPS trajectory equals the state-vector trajectory
+    on the same Philox stream (two independent implementations of Alg. 1)."""
+    c = small["circuit"]
+    for tr in range(6):
+        d = T.dense_trajectory(c, tr, 0)
+        m = T.mps_trajectory(c, tr, 0, 16, keep_dense=True)
+        assert d.branch == m.branch
+        assert abs(abs(np.vdot(d.state, m.state)) - 1.0) < 1e-12
+        assert np.allclose(d.p_branch, m.p_branch, atol=1e-12)
+        assert np.allclose(d.z, m.z, atol=1e-12) and np.allclose(d.zz, m.zz, atol=1e-12)
+        assert abs(d.s_half - m.s_half) < 1e-11
+        assert max(m.discarded) < 1e-20 and m.eps_bound == 0.0
+
+
+@pytest.mark.slow
+def test_trajectory_average_reproduces_density_matrix(small):
+    """Unbiasedness (Eq. Kraus_to_ensemble averaged over branches): the mean of
+    <Z_i>, <Z_i Z_i+1> over 256 trajectories matches exact density-matrix
+    evolution; all 15 z-scores must stay below 4."""
+    c = small["circuit"]
+    rho = T.density_evolution(c)
+    zr, zzr = T.density_observables(rho, c.n_qubits)
+    recs = [T.dense_trajectory(c, tr, 0) for tr in range(256)]
+    mz, sz = T.trajectory_statistics([r.z for r in recs])
+    mzz, szz = T.trajectory_statistics([r.zz for r in recs])
+    z = np.concatenate([(mz - zr) / sz, (mzz - zzr) / szz])
+    assert np.max(np.abs(z)) < 4.0, z
+
+
+def test_given_mode_with_identity_noise_is_unitary(small):
+    c = copy.deepcopy(small["circuit"])
+    for l in c.layers:
+        l.kraus = np.eye(2, dtype=complex)[None]
+    d = T.dense_trajectory(c, 0, 0, mode="given")
+    psi = np.zeros(2 ** 8, complex)
+    psi[0] = 1
+    for l in c.layers:
+        for q, g in zip(l.left_qubits, l.gates):
+            psi = T.apply_2q(psi, g, int(q), 8)
+    assert abs(abs(np.vdot(psi, d.state)) - 1) < 1e-13
+
+
+def test_bell_pair_half_chain_entropy():
+    h = np.array([[1, 1], [1, -1]]) / math.sqrt(2)
+    cnot = np.array([[1, 0, 0, 0], [0, 1, 0, 0], [0, 0, 0, 1], [0, 0, 1, 0]], dtype=complex)
+    g = cnot @ np.kron(h, np.eye(2))
+    c = I.Circuit(2, [I.Layer(np.array([0], np.int32), g[None], np.eye(2, dtype=complex)[None])])
+    for rec in (T.dense_trajectory(c, 0, 0, mode="given"), T.mps_trajectory(c, 0, 0, 4, mode="given")):
+        assert abs(rec.s_half - math.log(2)) < 1e-13
+        assert np.allclose(rec.z, 0, atol=1e-13) and np.allclose(rec.zz, 1, atol=1e-13)
+
+
+def test_product_state_entropy_zero():
+    c = I.Circuit(4, [I.Layer(np.array([0, 2], np.int32), np.stack([np.eye(4, dtype=complex)] * 2),
+                              np.eye(2, dtype=complex)[None])])
+    rec = T.mps_trajectory(c, 0, 0, 4, mode="given")
+    assert rec.s_half == 0.0 and np.allclose(rec.z, 1.0)
+
+
+@pytest.mark.slow
+def test_error_bound_covers_observable_error():
+    """Thm. 1 soundness on a truncated run: |<O>_exact - <O>_trajectories| for
+    the single-site Z (||Z|| = 1) is below eps_hat + Hoeffding buffer + 4 s.e."""
+    c = I.random_brickwork(6, 6, I.depolarizing_kraus(0.05), seed=3)
+    rho = T.density_evolution(c)
+    zr, _ = T.density_observables(rho, 6)
+    recs = [T.mps_trajectory(c, tr, 11, chi_max=2, cutoff=1e-14) for tr in range(200)]
+    eps_hat, buf = T.error_estimate(np.array([r.eps_bound for r in recs]))
+    mz, sz = T.trajectory_statistics([r.z for r in recs])
+    assert eps_hat > 0.0
+    assert np.all(np.abs(mz - zr) <= eps_hat + buf + 4 * sz)
+
+
+def test_eps_bound_definition():
+    """eps_bound = sum_l 4 sqrt(2 sum_k eps_k) if that is <= eps_max - 2 else
+    eps_max (App. B, Eq. systematic_error_with_constant_bound)."""
+    c = I.random_brickwork(6, 4, I.depolarizing_kraus(0.05), seed=5)
+    rec = T.mps_trajectory(c, 0, 1, chi_max=2, cutoff=1e-14, eps_max=1e9)
+    per_layer = []
+    k = 0
+    for l in c.layers:
+        per_layer.append(sum(rec.discarded[k:k + len(l.left_qubits)]))
+        k += len(l.left_qubits)
+    want = sum(4 * math.sqrt(2 * e) for e in per_layer)
+    assert abs(rec.eps_bound - want) < 1e-12
+    capped = T.mps_trajectory(c, 0, 1, chi_max=2, cutoff=1e-14, eps_max=want + 1.0)
+    assert capped.eps_bound == want + 1.0
+
+
+def test_coin_noise_matches_density_matrix():
+    """Probabilistic noise (coin_p < 1, the two-qubit depolarizing reading):
+    the trajectory average still reproduces the exact channel."""
+    c = I.random_brickwork(4, 4, I.depolarizing_kraus(1.0), seed=9, coin_p=0.3)
+    rho = T.density_evolution(c)
+    zr, zzr = T.density_observables(rho, 4)
+    recs = [T.mps_trajectory(c, tr, 2, chi_max=4) for tr in range(400)]
+    mz, sz = T.trajectory_statistics([r.z for r in recs])
+    assert np.max(np.abs((mz - zr) / np.maximum(sz, 1e-12))) < 4.0
+    assert any(b == -1 for r in recs for b in r.branch) and any(b >= 0 for r in recs for b in r.branch)
+
+
+# --- adjoint oracle -------------------------------------------------------------------
+
+def test_expected_entropy_identity_remix_and_optimum(rng):
+    """E(H=0) is E_av of the given set; E(H) >= E_oF for random H (Thm. 2)."""
+    w = I.workload_adjoint(seed=1, batch=4, chi=4)
+    for b in range(4):
+        rho = A.reduced_target(w["theta"][b])
+        kr = I.depolarizing_kraus(w["p"][b])
+        assert abs(A.expected_entropy(np.zeros((4, 4)), rho, kr) - U.unraveling_entropy(kr, rho)) < 1e-14
+        best = U.unraveling_entropy(U.optimal_unraveling(rho, kr)[0], rho)
+        for _ in range(10):
+            a = rng.standard_normal((4, 4)) + 1j * rng.standard_normal((4, 4))
+            assert A.expected_entropy(a + a.conj().T, rho, kr) >= best - 1e-12
+
+
+def test_fd_gradient_directional_consistency(rng):
+    """The Hermitian FD gradient predicts directional changes: for random
+    Hermitian directions D, Re Tr(Gamma D) matches a 1e-4 step five-point
+    derivative of E along D."""
+    w = I.workload_adjoint(seed=2, batch=2, chi=4)
+    rho = A.reduced_target(w["theta"][0])
+    kr = I.depolarizing_kraus(w["p"][0])
+    h = w["H"][0]
+    g = A.fd_gradient(h, rho, kr)
+    assert np.allclose(g, g.conj().T)
+    for _ in range(4):
+        a = rng.standard_normal((4, 4)) + 1j * rng.standard_normal((4, 4))
+        d = a + a.conj().T
+        e = lambda t: A.expected_entropy(h + t * d, rho, kr)
+        s = 1e-4
+        deriv = (-e(2 * s) + 8 * e(s) - 8 * e(-s) + e(-2 * s)) / (12 * s)
+        assert abs(np.trace(g.conj().T @ d).real - deriv) < 1e-7 * max(1.0, abs(deriv))
+
+
+def test_gradient_descent_approaches_eof():
+    w = I.workload_adjoint(seed=3, batch=1, chi=4)
+    rho = A.reduced_target(w["theta"][0])
+    kr = I.depolarizing_kraus(w["p"][0])
+    _, costs = A.gradient_descent(w["H"][0], rho, kr, steps=30, lr=0.5)
+    best = U.unraveling_entropy(U.optimal_unraveling(rho, kr)[0], rho)
+    assert costs[-1] <= costs[0] + 1e-12
+    assert costs[-1] >= best - 1e-12
