@@ -1,0 +1,203 @@
+/*
+ * lemps.h — C ABI of the GB300 library for batched Monte-Carlo MPS
+ * trajectories with the locally entanglement-optimal unraveling
+ * (arXiv 2508.05745).
+ *
+ * The problem statement follows Sec. III (truncated trajectory sampling of a
+ * circuit description D = initial state |0...0>, a string of layers of
+ * nearest-neighbour two-qubit gates, each followed by single-qubit noise on the
+ * two gated qubits) and Sec. IV (the MPS update of Sec. IV.A, the channel
+ * unraveling subprocedure of Alg. 1, the optimal Kraus set of Sec. IV.B).
+ *
+ * Conventions shared by every call
+ *  - Complex numbers are interleaved (re, im) doubles.
+ *  - A two-qubit gate on qubits (q, q+1) is a row-major 4x4 matrix indexed by
+ *    2*s_q + s_{q+1}; a Kraus operator is a row-major 2x2 matrix K[s'][s].
+ *  - Pointers documented as "host" are caller-owned and only read (or written)
+ *    during the call.  Pointers documented as "device" must point to memory on
+ *    the handle's (or the given stream's) device.
+ *  - Functions never throw and never fall back to the CPU.  A non-OK status
+ *    leaves the handle usable, except LEMPS_ECUDA, which is sticky: every later
+ *    call on that handle returns LEMPS_ECUDA.  lemps_last_error() describes the
+ *    last failure of the calling thread.
+ *  - Random numbers: the uniform of slot s (0 = qubit q, 1 = qubit q+1, 2 = the
+ *    per-gate noise coin) of global gate g in trajectory t is
+ *    Philox4x64-10(counter = (t, g, s, 0), key = (seed, 0x4C454D5053545241)),
+ *    first output word >> 11, times 2^-53.  Results therefore do not depend on
+ *    how trajectories are batched or sharded (traj_offset).
+ */
+#ifndef LEMPS_H
+#define LEMPS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lemps_sim* lemps_handle;
+
+typedef enum {
+  LEMPS_OK = 0,
+  LEMPS_EINVAL = 1,    /* invalid argument; nothing was enqueued */
+  LEMPS_ENOMEM = 2,    /* device allocation failed */
+  LEMPS_ECUDA = 3,     /* CUDA error; sticky */
+  LEMPS_ENUMERIC = 4,  /* a trajectory produced NaN / lost its norm / eigensolver cap */
+  LEMPS_ESTATE = 5     /* call not valid in the handle's current state */
+} lemps_status;
+
+typedef enum {
+  LEMPS_FP64 = 0,      /* complex128 storage and arithmetic everywhere */
+  LEMPS_MIXED = 1      /* complex64 MPS storage, contractions and eigensolver;
+                          reduced densities, unraveling, branch weights,
+                          discarded weights and entropies in FP64 */
+} lemps_precision;
+
+typedef enum {
+  LEMPS_UNRAVEL_OPTIMAL = 0, /* remix each noise site's Kraus set into the
+                                locally entanglement-optimal one (Sec. IV.B) */
+  LEMPS_UNRAVEL_GIVEN = 1    /* sample the Kraus set as given */
+} lemps_unravel;
+
+/* Device allocator hook (PyTorch's caching allocator from Python).  NULL
+ * alloc means cudaMalloc / cudaFree. */
+typedef void* (*lemps_alloc_fn)(size_t bytes, void* stream, void* ctx);
+typedef void (*lemps_free_fn)(void* ptr, size_t bytes, void* stream, void* ctx);
+
+typedef struct {
+  int32_t n_qubits;       /* >= 2 */
+  int32_t chi_max;        /* maximum bond dimension, 1..128 */
+  double trunc_cutoff;    /* keep Schmidt weights > cutoff * total (Sec. II truncation) */
+  int64_t n_traj;         /* trajectories held by this handle */
+  int64_t traj_offset;    /* global id of the handle's first trajectory */
+  uint64_t seed;
+  int32_t precision;      /* lemps_precision */
+  int32_t unravel_mode;   /* lemps_unravel */
+  int32_t log_capacity;   /* gates whose sampled branch indices are kept (sample_branch) */
+  double eps_max;         /* per-trajectory error cap of Thm. 1 (App. B), >= 2 */
+  void* cuda_stream;      /* cudaStream_t used by every call, NULL = default stream */
+  lemps_alloc_fn alloc;
+  lemps_free_fn free;
+  void* alloc_ctx;
+} lemps_config;
+
+typedef struct {
+  int32_t n_gates;            /* gates of this layer, applied in list order */
+  const int32_t* left_qubit;  /* host [n_gates]; gate k acts on (q, q+1), pairs disjoint */
+  const double* gates;        /* host [n_gates][4][4] complex */
+  int32_t n_kraus;            /* 1..4 operators of the single-qubit noise channel */
+  const double* kraus;        /* host [n_kraus][2][2] complex, sum K^dagger K = I */
+  double coin_p;              /* the channel acts on both gated qubits with this
+                                 probability per gate (1 = always) */
+} lemps_layer;
+
+typedef struct {
+  /* per-trajectory outputs, host, optional (NULL = not returned) */
+  double* z;           /* [n_traj][n]     <Z_i> */
+  double* zz;          /* [n_traj][n-1]   <Z_i Z_{i+1}> */
+  double* s_half;      /* [n_traj]        entropy (nats) of bond n/2 */
+  double* eps_bound;   /* [n_traj]        error bound of Thm. 1 / App. B */
+  int32_t* status;     /* [n_traj]        0 = ok, else a LEMPS_ENUMERIC reason code */
+  /* reductions over trajectories, host, required */
+  double* z_mean;      /* [n] */
+  double* z_stderr;    /* [n] */
+  double* zz_mean;     /* [n-1] */
+  double* zz_stderr;   /* [n-1] */
+  double s_half_mean;
+  double s_half_stderr;
+  double eps_hat;      /* mean eps_bound */
+  double eps_buffer;   /* sqrt(eps_max^2 / (2N) ln(1/delta)), delta = 0.05 */
+  int64_t n_failed;    /* trajectories with a non-zero status */
+} lemps_measurement;
+
+/* Allocate a batch of n_traj trajectories in |0...0> (all bonds 1).  All
+ * device memory is owned by the handle. */
+lemps_status sim_create(const lemps_config* cfg, lemps_handle* out);
+
+/* Apply one layer (Sec. IV.A, layering option "local", Trunc o N(x)N o U per
+ * gate) to every trajectory: contract the gate into the two-site tensor,
+ * unravel the noise on q then q+1 (Alg. 1 with the Kraus set of Sec. IV.B),
+ * sample with the Philox stream above, re-split by a Hermitian eigensolve of
+ * the two-site Gram matrix and truncate to chi_max.  Asynchronous on the
+ * handle's stream; the host arrays are copied before return. */
+lemps_status apply_layer(lemps_handle h, const lemps_layer* layer);
+
+/* Standalone optimal unraveling (Sec. IV.B, App. F.2) of a batch of target
+ * reduced states.  rho_a: device [batch][2][2] complex (Hermitian, any trace);
+ * kraus: device [n_kraus][2][2] complex (n_kraus 1..4); kraus_out: device
+ * [batch][4][2][2] complex, kraus_out[b][k] = sum_j W[j][k] K_j; e_av: device
+ * [batch] ensemble-averaged entropy (nats) of the output set on rho_a/Tr.
+ * Asynchronous on stream. */
+lemps_status unravel_opt(const double* rho_a, const double* kraus, int32_t n_kraus, int64_t batch,
+                         double* kraus_out, double* e_av, void* stream);
+
+/* Branch indices sampled at global gate index `gate` (slot 0: qubit q, 1:
+ * qubit q+1) for every trajectory; -1 where the noise coin skipped the gate.
+ * branch_out: host [n_traj].  Synchronizes the stream. */
+lemps_status sample_branch(lemps_handle h, int64_t gate, int32_t slot, int32_t* branch_out);
+
+/* Observables of Sec. III.C / App. C on the current states, mean and standard
+ * error over trajectories, and the a-posteriori error estimate of Thm. 1.
+ * Moves every trajectory's orthogonality centre; synchronizes the stream. */
+lemps_status measure(lemps_handle h, lemps_measurement* m);
+
+/* Copy trajectory `traj`'s MPS to the host: bond_dims [n+1]; tensors receives
+ * site k as [d_k][2][d_{k+1}] complex, sites concatenated (caller sizes it for
+ * n * 2 * chi_max^2 complex).  Inspection only; synchronizes the stream. */
+lemps_status sim_export_mps(lemps_handle h, int64_t traj, int32_t* bond_dims, double* tensors);
+
+/* Wait for the handle's queued work; returns the sticky status and reports
+ * LEMPS_ENUMERIC if any trajectory flagged a numerical failure. */
+lemps_status sim_sync(lemps_handle h);
+
+/* Release every device allocation of the handle. */
+lemps_status destroy(lemps_handle h);
+
+/* Expected branch entropy of a remixed Kraus set and its gradient (the
+ * differentiation workload; cost of Eq. target_optimal_unitary, remix
+ * K'_k = sum_j U[j][k] K_j with U = exp(iH), Eq. unitarity_kraus).
+ *   theta:  device [batch][chi][2][2][chi] complex, double (theta_fp64 = 1) or
+ *           float (0); target = first physical index; any norm.
+ *   p:      device [batch] depolarizing rates of the channel being remixed
+ *           (Kraus set {sqrt(1-3p/4) I, sqrt(p)/2 X, Y, Z}).
+ *   h:      device [batch][4][4] complex Hermitian, read.
+ *   cost:   device [batch], E(H) in nats.
+ *   grad:   device [batch][4][4] complex Hermitian gradient Gamma with
+ *           dE = Re Tr(Gamma^dagger dH), or NULL.
+ *   rho_out: device [batch][2][2] complex reduced target states, or NULL.
+ * Asynchronous on stream. */
+lemps_status unravel_grad(const void* theta, int32_t theta_fp64, int64_t batch, int32_t chi,
+                          const double* p, const double* h, double* cost, double* grad,
+                          double* rho_out, void* stream);
+
+/* `steps` gradient-descent steps H <- H - lr * Gamma on the device for the
+ * reduced states rho_a (device [batch][2][2] complex, e.g. rho_out above);
+ * h is updated in place; cost_trace: device [steps][batch] or NULL. */
+lemps_status unravel_descend(const double* rho_a, const double* p, int64_t batch, int32_t steps,
+                             double lr, double* h, double* cost_trace, void* stream);
+
+/* Per-kernel timing with CUDA events recorded on the handle's stream around
+ * every launch made by apply_layer (enable = 1 starts a fresh record,
+ * enable = 0 stops recording).  With ms and launches non-NULL the call
+ * synchronizes and returns, per kernel kind (LEMPS_K_*), the summed event
+ * time in milliseconds and the launch count since recording started. */
+enum {
+  LEMPS_K_MOVE = 0,      /* centre move (Householder QR / LQ + merge) */
+  LEMPS_K_CONTRACT = 1,  /* two-site contraction + 4x4 reduced density */
+  LEMPS_K_UNRAVEL = 2,   /* noise sites: optimal unraveling + sampling */
+  LEMPS_K_GRAM = 3,      /* apply gate and Kraus operators, Gram matrix */
+  LEMPS_K_EIG = 4,       /* Hermitian Jacobi eigensolver */
+  LEMPS_K_SPLIT = 5,     /* truncation and new site tensors */
+  LEMPS_K_OTHER = 6,     /* layer bookkeeping */
+  LEMPS_NUM_KERNEL_KINDS = 7
+};
+lemps_status sim_profile(lemps_handle h, int32_t enable, double* ms, int64_t* launches);
+
+const char* lemps_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LEMPS_H */

@@ -224,11 +224,13 @@ class MPS:
 
 
 def mps_trajectory(circuit, traj: int, seed: int, chi_max: int, cutoff: float = 1e-20,
-                   mode: str = "optimal", eps_max: float = 4.0, keep_dense: bool = False):
+                   mode: str = "optimal", eps_max: float = 4.0, keep_dense: bool = False,
+                   layer_callback=None):
     """One MPS trajectory.  After gate (q, q+1) and its noise, the two-site
     tensor is split by SVD keeping chi' = min(chi_max, #{s_k^2 > cutoff * sum s^2})
     values; the discarded weight eps = sum_{k > chi'} s_k^2 / sum s^2 is
-    accumulated per layer and the state is renormalized."""
+    accumulated per layer and the state is renormalized.  layer_callback(l),
+    if given, is called after layer l (used to time the oracle per layer)."""
     n = circuit.n_qubits
     m = MPS(n)
     rec = TrajectoryRecord([], [], [], [])
@@ -282,6 +284,8 @@ def mps_trajectory(circuit, traj: int, seed: int, chi_max: int, cutoff: float = 
             m.center = q + 1
             g_glob += 1
         eps_tot += 4.0 * math.sqrt(2.0 * eps_layer)
+        if layer_callback is not None:
+            layer_callback(len(rec.discarded))
     rec.eps_bound = eps_tot if eps_tot <= eps_max - 2.0 else eps_max
     rec.z, rec.zz, rec.s_half = m.observables()
     if keep_dense:

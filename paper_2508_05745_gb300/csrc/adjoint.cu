@@ -1,0 +1,50 @@
+// C ABI of the differentiation entry points (unravel_grad, unravel_descend).
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "../../include/lemps.h"
+#include "adjoint.cuh"
+
+using namespace lemps;
+
+extern "C" lemps_status lemps_set_error_(int st, const char* msg);
+
+extern "C" {
+
+lemps_status unravel_grad(const void* theta, int32_t theta_fp64, int64_t batch, int32_t chi, const double* p,
+                          const double* h, double* cost, double* grad, double* rho_out, void* stream) {
+  if (!theta || !p || !h || !cost || batch < 0 || chi < 1)
+    return lemps_set_error_(LEMPS_EINVAL, "unravel_grad: bad argument");
+  if (batch == 0) return LEMPS_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  zd* rho = reinterpret_cast<zd*>(rho_out);
+  bool own = false;
+  if (!rho) {
+    if (cudaMallocAsync((void**)&rho, sizeof(zd) * 4 * batch, st) != cudaSuccess)
+      return lemps_set_error_(LEMPS_ENOMEM, "unravel_grad: scratch allocation failed");
+    own = true;
+  }
+  if (theta_fp64)
+    adj::k_rho_target<double><<<(unsigned)batch, 256, 0, st>>>((const zd*)theta, batch, chi, rho);
+  else
+    adj::k_rho_target<float><<<(unsigned)batch, 256, 0, st>>>((const zf*)theta, batch, chi, rho);
+  adj::k_cost_grad<<<(unsigned)((batch + 63) / 64), 64, 0, st>>>(rho, p, (const zd*)h, batch, cost, (zd*)grad);
+  if (own) cudaFreeAsync(rho, st);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return lemps_set_error_(LEMPS_ECUDA, cudaGetErrorString(e));
+  return LEMPS_OK;
+}
+
+lemps_status unravel_descend(const double* rho_a, const double* p, int64_t batch, int32_t steps, double lr, double* h,
+                             double* cost_trace, void* stream) {
+  if (!rho_a || !p || !h || batch < 0 || steps < 0) return lemps_set_error_(LEMPS_EINVAL, "unravel_descend: bad argument");
+  if (batch == 0 || steps == 0) return LEMPS_OK;
+  adj::k_descend<<<(unsigned)((batch + 63) / 64), 64, 0, (cudaStream_t)stream>>>((const zd*)rho_a, p, batch, steps, lr,
+                                                                                 (zd*)h, cost_trace);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return lemps_set_error_(LEMPS_ECUDA, cudaGetErrorString(e));
+  return LEMPS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,538 @@
+// C ABI of the library (include/lemps.h): device allocation, layer
+// orchestration and the measure/export calls.  All arithmetic runs in the
+// kernels of mps_kernels.cuh and unravel.cuh; the host only schedules them.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/lemps.h"
+#include "mps_kernels.cuh"
+#include "unravel_iface.h"
+
+using namespace lemps;
+
+namespace {
+
+thread_local std::string g_err;
+
+lemps_status fail(lemps_status st, const std::string& msg) {
+  g_err = msg;
+  return st;
+}
+
+constexpr int kThreads = 256;
+
+}  // namespace
+
+struct lemps_sim {
+  lemps_config cfg;
+  int n = 0;
+  int64_t B = 0;
+  int chi = 0;
+  int prec = 0;
+  cudaStream_t stream = nullptr;
+  bool sticky = false;
+  std::vector<std::pair<void*, size_t>> allocs;
+  std::vector<int32_t> cap_h;
+  std::vector<int64_t> off_h;
+  size_t elem = 0;           // bytes per complex element of the MPS
+  void* mps = nullptr;
+  int64_t* site_off = nullptr;
+  int32_t* cap = nullptr;
+  int32_t* bond = nullptr;
+  void* ws[4] = {nullptr, nullptr, nullptr, nullptr};
+  int64_t ws_stride = 0;
+  double* evals = nullptr;
+  zd* rho12 = nullptr;
+  zd* top = nullptr;
+  double* eps_layer = nullptr;
+  double* eps_tot = nullptr;
+  double* disc_last = nullptr;
+  int32_t* status = nullptr;
+  int8_t* blog = nullptr;
+  int64_t log_cap = 0;
+  zd* layer_buf = nullptr;   // gates + kraus of the current layer
+  int64_t layer_cap = 0;     // complex numbers
+  double* obs = nullptr;     // measure scratch: z [B][n], zz [B][n-1], s_half [B], eps_bound [B]
+  double* stats = nullptr;   // reductions
+  int64_t gates_done = 0;
+  int center = 0;
+  bool profiling = false;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof;  // (kind, (start, stop))
+  double prof_ms[LEMPS_NUM_KERNEL_KINDS] = {0};
+  int64_t prof_n[LEMPS_NUM_KERNEL_KINDS] = {0};
+
+  // Record an event pair around one launch when profiling.
+  template <class F>
+  void timed(int kind, F&& launch) {
+    if (!profiling) { launch(); return; }
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a, stream);
+    launch();
+    cudaEventRecord(b, stream);
+    prof.push_back({kind, {a, b}});
+  }
+  void collect_profile() {
+    cudaStreamSynchronize(stream);
+    for (auto& p : prof) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, p.second.first, p.second.second);
+      prof_ms[p.first] += ms;
+      prof_n[p.first] += 1;
+      cudaEventDestroy(p.second.first);
+      cudaEventDestroy(p.second.second);
+    }
+    prof.clear();
+  }
+
+  void* dalloc(size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    void* p = nullptr;
+    if (cfg.alloc) {
+      p = cfg.alloc(bytes, (void*)stream, cfg.alloc_ctx);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+      p = nullptr;
+    }
+    if (p) allocs.push_back({p, bytes});
+    return p;
+  }
+  void release() {
+    for (auto& a : allocs) {
+      if (cfg.free) cfg.free(a.first, a.second, (void*)stream, cfg.alloc_ctx);
+      else cudaFree(a.first);
+    }
+    allocs.clear();
+  }
+  template <class R>
+  SimView<R> view() const {
+    SimView<R> v;
+    v.mps = reinterpret_cast<cpx<R>*>(mps);
+    v.site_off = site_off;
+    v.cap = cap;
+    v.bond = bond;
+    v.n = n;
+    v.B = B;
+    v.chi = chi;
+    v.ws0 = reinterpret_cast<cpx<R>*>(ws[0]);
+    v.ws1 = reinterpret_cast<cpx<R>*>(ws[1]);
+    v.ws2 = reinterpret_cast<cpx<R>*>(ws[2]);
+    v.ws3 = reinterpret_cast<cpx<R>*>(ws[3]);
+    v.ws_stride = ws_stride;
+    v.evals = evals;
+    v.rho12 = rho12;
+    v.top = top;
+    v.eps_layer = eps_layer;
+    v.eps_tot = eps_tot;
+    v.disc_last = disc_last;
+    v.status = status;
+    return v;
+  }
+};
+
+namespace {
+
+lemps_status check_cuda(lemps_sim* h, const char* where) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    if (h) h->sticky = true;
+    return fail(LEMPS_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+  }
+  return LEMPS_OK;
+}
+
+template <class R>
+void launch_move(lemps_sim* h, int k, int dir) {
+  h->timed(LEMPS_K_MOVE, [&] { k_move_center<R><<<(unsigned)h->B, kThreads, 0, h->stream>>>(h->view<R>(), k, dir); });
+}
+
+template <class R>
+void move_center_to(lemps_sim* h, int target) {
+  while (h->center < target) { launch_move<R>(h, h->center, +1); ++h->center; }
+  while (h->center > target) { launch_move<R>(h, h->center, -1); --h->center; }
+}
+
+template <class R>
+struct JacobiParams;
+template <>
+struct JacobiParams<double> { static constexpr int sweeps = 20; static constexpr double tol = 1e-15; };
+template <>
+struct JacobiParams<float> { static constexpr int sweeps = 16; static constexpr float tol = 2e-7f; };
+
+template <class R>
+void launch_jacobi(lemps_sim* h, int q, int mode) {
+  h->timed(LEMPS_K_EIG, [&] {
+    k_jacobi<R><<<(unsigned)h->B, kThreads, 0, h->stream>>>(h->view<R>(), q, mode, JacobiParams<R>::sweeps,
+                                                             (R)JacobiParams<R>::tol);
+  });
+}
+
+template <class R>
+lemps_status apply_layer_t(lemps_sim* h, const lemps_layer* L) {
+  const int ng = L->n_gates;
+  const int64_t need = (int64_t)ng * 16 + (int64_t)L->n_kraus * 4;
+  if (need > h->layer_cap) return fail(LEMPS_EINVAL, "apply_layer: too many gates for this handle");
+  if (ng > 0) {
+    if (cudaMemcpyAsync(h->layer_buf, L->gates, sizeof(zd) * 16 * ng, cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
+      return check_cuda(h, "apply_layer copy");
+  }
+  zd* kraus_d = h->layer_buf + 16 * (int64_t)ng;
+  if (cudaMemcpyAsync(kraus_d, L->kraus, sizeof(zd) * 4 * L->n_kraus, cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
+    return check_cuda(h, "apply_layer copy");
+  const unsigned grid_t = (unsigned)((h->B + kThreads - 1) / kThreads);
+  SimView<R> sv = h->view<R>();
+  for (int g = 0; g < ng; ++g) {
+    const int q = L->left_qubit[g];
+    if (h->center < q) move_center_to<R>(h, q);
+    else if (h->center > q + 1) move_center_to<R>(h, q + 1);
+    h->timed(LEMPS_K_CONTRACT, [&] { k_contract<R><<<(unsigned)h->B, kThreads, 0, h->stream>>>(sv, q); });
+    LayerDev ld;
+    ld.gates = h->layer_buf;
+    ld.kraus = kraus_d;
+    ld.r = L->n_kraus;
+    ld.coin_p = L->coin_p;
+    ld.mode = h->cfg.unravel_mode;
+    ld.seed = h->cfg.seed;
+    ld.traj_offset = h->cfg.traj_offset;
+    ld.gate_global = h->gates_done + g;
+    ld.gate_local = g;
+    ld.blog = (ld.gate_global < h->log_cap) ? h->blog + ld.gate_global * 2 * h->B : nullptr;
+    GateState gs;
+    gs.rho12 = h->rho12;
+    gs.top = h->top;
+    gs.status = h->status;
+    gs.B = h->B;
+    h->timed(LEMPS_K_UNRAVEL, [&] { launch_unravel_gate(gs, ld, h->stream); });
+    int side;
+    if (g + 1 < ng) side = (L->left_qubit[g + 1] > q) ? 0 : 1;
+    else if (g > 0) side = (q > L->left_qubit[g - 1]) ? 0 : 1;
+    else side = 0;
+    h->timed(LEMPS_K_GRAM, [&] { k_apply_gram<R><<<(unsigned)h->B, kThreads, 0, h->stream>>>(sv, q, side); });
+    launch_jacobi<R>(h, q, side);
+    h->timed(LEMPS_K_SPLIT,
+             [&] { k_split<R><<<(unsigned)h->B, kThreads, 0, h->stream>>>(sv, q, side, h->cfg.trunc_cutoff); });
+    h->center = (side == 0) ? q + 1 : q;
+  }
+  h->timed(LEMPS_K_OTHER, [&] { k_layer_end<R><<<grid_t, kThreads, 0, h->stream>>>(sv); });
+  h->gates_done += ng;
+  return check_cuda(h, "apply_layer");
+}
+
+__global__ void k_finalize_obs(const double* eps_tot, double eps_max, int64_t B, double* eps_bound) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= B) return;
+  double e = eps_tot[t];
+  eps_bound[t] = (e <= eps_max - 2.0) ? e : eps_max;
+}
+
+// mean and standard error of column c of a [B][ncol] array (one block per column)
+__global__ void k_column_stats(const double* x, int64_t B, int ncol, double* mean, double* se) {
+  __shared__ double red[32];
+  const int c = blockIdx.x;
+  double s = 0.0;
+  for (int64_t t = threadIdx.x; t < B; t += blockDim.x) s += x[t * ncol + c];
+  s = block_sum(s, red);
+  const double m = s / (double)B;
+  double v = 0.0;
+  for (int64_t t = threadIdx.x; t < B; t += blockDim.x) {
+    double d = x[t * ncol + c] - m;
+    v += d * d;
+  }
+  v = block_sum(v, red);
+  if (threadIdx.x == 0) {
+    mean[c] = m;
+    se[c] = B > 1 ? sqrt(v / (double)(B - 1) / (double)B) : 0.0;
+  }
+}
+
+template <class R>
+lemps_status measure_t(lemps_sim* h, lemps_measurement* m) {
+  const int n = h->n;
+  const int64_t B = h->B;
+  const unsigned grid_t = (unsigned)((B + kThreads - 1) / kThreads);
+  SimView<R> sv = h->view<R>();
+  double* z = h->obs;
+  double* zz = z + B * n;
+  double* sh = zz + B * (n - 1);
+  double* eb = sh + B;
+  move_center_to<R>(h, 0);
+  const int hb = n / 2;  // bond n/2 lies between sites hb-1 and hb
+  for (int q = 0; q + 1 < n; ++q) {
+    k_contract<R><<<(unsigned)B, kThreads, 0, h->stream>>>(sv, q);
+    k_obs_from_rho12<<<grid_t, kThreads, 0, h->stream>>>(h->rho12, B, n, q, z, zz);
+    if (q == hb - 1) {
+      k_site_gram<R><<<(unsigned)B, kThreads, 0, h->stream>>>(sv, q);
+      launch_jacobi<R>(h, q, 2);
+      k_entropy_from_evals<<<grid_t, kThreads, 0, h->stream>>>(h->evals, 2 * h->chi, h->bond, n + 1, q + 1, B, sh);
+    }
+    launch_move<R>(h, q, +1);
+    ++h->center;
+  }
+  k_finalize_obs<<<grid_t, kThreads, 0, h->stream>>>(h->eps_tot, h->cfg.eps_max, B, eb);
+  double* st = h->stats;  // z_mean n, z_se n, zz_mean n-1, zz_se n-1, sh 2, eb 2
+  k_column_stats<<<n, kThreads, 0, h->stream>>>(z, B, n, st, st + n);
+  k_column_stats<<<n - 1, kThreads, 0, h->stream>>>(zz, B, n - 1, st + 2 * n, st + 3 * n - 1);
+  k_column_stats<<<1, kThreads, 0, h->stream>>>(sh, B, 1, st + 4 * n - 2, st + 4 * n - 1);
+  k_column_stats<<<1, kThreads, 0, h->stream>>>(eb, B, 1, st + 4 * n, st + 4 * n + 1);
+  lemps_status cs = check_cuda(h, "measure");
+  if (cs != LEMPS_OK) return cs;
+  std::vector<double> hs(4 * n + 2);
+  std::vector<int32_t> stat(B);
+  if (cudaMemcpyAsync(hs.data(), st, sizeof(double) * hs.size(), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+      cudaMemcpyAsync(stat.data(), h->status, sizeof(int32_t) * B, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
+    return check_cuda(h, "measure copy");
+  if (m->z) cudaMemcpyAsync(m->z, z, sizeof(double) * B * n, cudaMemcpyDeviceToHost, h->stream);
+  if (m->zz) cudaMemcpyAsync(m->zz, zz, sizeof(double) * B * (n - 1), cudaMemcpyDeviceToHost, h->stream);
+  if (m->s_half) cudaMemcpyAsync(m->s_half, sh, sizeof(double) * B, cudaMemcpyDeviceToHost, h->stream);
+  if (m->eps_bound) cudaMemcpyAsync(m->eps_bound, eb, sizeof(double) * B, cudaMemcpyDeviceToHost, h->stream);
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return check_cuda(h, "measure sync");
+  if (m->status) std::memcpy(m->status, stat.data(), sizeof(int32_t) * B);
+  for (int i = 0; i < n; ++i) { m->z_mean[i] = hs[i]; m->z_stderr[i] = hs[n + i]; }
+  for (int i = 0; i + 1 < n; ++i) { m->zz_mean[i] = hs[2 * n + i]; m->zz_stderr[i] = hs[3 * n - 1 + i]; }
+  m->s_half_mean = hs[4 * n - 2];
+  m->s_half_stderr = hs[4 * n - 1];
+  m->eps_hat = hs[4 * n];
+  m->eps_buffer = std::sqrt(h->cfg.eps_max * h->cfg.eps_max / (2.0 * (double)B) * std::log(1.0 / 0.05));
+  int64_t nf = 0;
+  for (int64_t t = 0; t < B; ++t) nf += (stat[t] != 0);
+  m->n_failed = nf;
+  return nf ? fail(LEMPS_ENUMERIC, "measure: some trajectories flagged a numerical failure") : LEMPS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lemps_last_error(void) { return g_err.c_str(); }
+
+// Shared with the other translation units of the library (not in lemps.h).
+lemps_status lemps_set_error_(int st, const char* msg) {
+  g_err = msg;
+  return (lemps_status)st;
+}
+
+lemps_status sim_create(const lemps_config* cfg, lemps_handle* out) {
+  if (!cfg || !out) return fail(LEMPS_EINVAL, "sim_create: null argument");
+  *out = nullptr;
+  if (cfg->n_qubits < 2 || cfg->n_qubits > 4096) return fail(LEMPS_EINVAL, "sim_create: n_qubits out of range");
+  if (cfg->chi_max < 1 || cfg->chi_max > 128) return fail(LEMPS_EINVAL, "sim_create: chi_max must be in 1..128");
+  if (cfg->n_traj < 1) return fail(LEMPS_EINVAL, "sim_create: n_traj must be positive");
+  if (cfg->precision != LEMPS_FP64 && cfg->precision != LEMPS_MIXED) return fail(LEMPS_EINVAL, "sim_create: bad precision");
+  if (cfg->unravel_mode != LEMPS_UNRAVEL_OPTIMAL && cfg->unravel_mode != LEMPS_UNRAVEL_GIVEN)
+    return fail(LEMPS_EINVAL, "sim_create: bad unravel_mode");
+  if (!(cfg->trunc_cutoff >= 0.0) || !(cfg->eps_max >= 2.0)) return fail(LEMPS_EINVAL, "sim_create: bad cutoff or eps_max");
+  if ((cfg->alloc == nullptr) != (cfg->free == nullptr)) return fail(LEMPS_EINVAL, "sim_create: alloc and free go together");
+  lemps_sim* h = new lemps_sim();
+  h->cfg = *cfg;
+  h->n = cfg->n_qubits;
+  h->B = cfg->n_traj;
+  h->chi = cfg->chi_max;
+  h->prec = cfg->precision;
+  h->stream = (cudaStream_t)cfg->cuda_stream;
+  h->elem = (h->prec == LEMPS_FP64) ? sizeof(zd) : sizeof(zf);
+  const int n = h->n;
+  h->cap_h.resize(n + 1);
+  for (int k = 0; k <= n; ++k) {
+    int e = std::min(k, n - k);
+    int64_t c = (e >= 30) ? (int64_t)1 << 30 : ((int64_t)1 << e);
+    h->cap_h[k] = (int32_t)std::min<int64_t>(c, h->chi);
+  }
+  h->off_h.resize(n);
+  int64_t tot = 0;
+  for (int k = 0; k < n; ++k) {
+    h->off_h[k] = tot;
+    tot += (int64_t)h->cap_h[k] * 2 * h->cap_h[k + 1] * h->B;
+  }
+  h->ws_stride = (int64_t)(2 * h->chi) * (2 * h->chi);
+  h->log_cap = cfg->log_capacity > 0 ? cfg->log_capacity : 0;
+  h->layer_cap = (int64_t)(n / 2 + 1) * 16 + 16;
+  bool ok = true;
+  auto A = [&](size_t bytes) {
+    void* p = h->dalloc(bytes);
+    if (!p) ok = false;
+    return p;
+  };
+  h->mps = A(h->elem * tot);
+  h->site_off = (int64_t*)A(sizeof(int64_t) * n);
+  h->cap = (int32_t*)A(sizeof(int32_t) * (n + 1));
+  h->bond = (int32_t*)A(sizeof(int32_t) * (n + 1) * h->B);
+  for (int i = 0; i < 4; ++i) h->ws[i] = A(h->elem * h->ws_stride * h->B);
+  h->evals = (double*)A(sizeof(double) * 2 * h->chi * h->B);
+  h->rho12 = (zd*)A(sizeof(zd) * 16 * h->B);
+  h->top = (zd*)A(sizeof(zd) * 16 * h->B);
+  h->eps_layer = (double*)A(sizeof(double) * h->B);
+  h->eps_tot = (double*)A(sizeof(double) * h->B);
+  h->disc_last = (double*)A(sizeof(double) * h->B);
+  h->status = (int32_t*)A(sizeof(int32_t) * h->B);
+  h->blog = (int8_t*)A(std::max<int64_t>(1, h->log_cap * 2 * h->B));
+  h->layer_buf = (zd*)A(sizeof(zd) * h->layer_cap);
+  h->obs = (double*)A(sizeof(double) * h->B * (2 * n + 1));
+  h->stats = (double*)A(sizeof(double) * (4 * n + 4));
+  if (!ok) {
+    h->release();
+    delete h;
+    return fail(LEMPS_ENOMEM, "sim_create: device allocation failed");
+  }
+  cudaMemsetAsync(h->mps, 0, h->elem * tot, h->stream);
+  if (h->log_cap > 0) cudaMemsetAsync(h->blog, 0xff, h->log_cap * 2 * h->B, h->stream);
+  cudaMemcpyAsync(h->site_off, h->off_h.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice, h->stream);
+  cudaMemcpyAsync(h->cap, h->cap_h.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice, h->stream);
+  if (h->prec == LEMPS_FP64) k_init_state<double><<<(unsigned)h->B, 64, 0, h->stream>>>(h->view<double>());
+  else k_init_state<float><<<(unsigned)h->B, 64, 0, h->stream>>>(h->view<float>());
+  lemps_status st = check_cuda(h, "sim_create");
+  if (st != LEMPS_OK) {
+    h->release();
+    delete h;
+    return st;
+  }
+  // The host vectors passed to cudaMemcpyAsync must outlive the copies.
+  cudaStreamSynchronize(h->stream);
+  *out = h;
+  return LEMPS_OK;
+}
+
+lemps_status apply_layer(lemps_handle h, const lemps_layer* layer) {
+  if (!h || !layer) return fail(LEMPS_EINVAL, "apply_layer: null argument");
+  if (h->sticky) return fail(LEMPS_ECUDA, "apply_layer: handle has a sticky CUDA error");
+  if (layer->n_gates < 0 || (layer->n_gates > 0 && (!layer->left_qubit || !layer->gates)) || !layer->kraus)
+    return fail(LEMPS_EINVAL, "apply_layer: bad layer arrays");
+  if (layer->n_kraus < 1 || layer->n_kraus > 4) return fail(LEMPS_EINVAL, "apply_layer: n_kraus must be 1..4");
+  if (!(layer->coin_p >= 0.0 && layer->coin_p <= 1.0)) return fail(LEMPS_EINVAL, "apply_layer: coin_p outside [0,1]");
+  std::vector<char> used(h->n, 0);
+  for (int g = 0; g < layer->n_gates; ++g) {
+    int q = layer->left_qubit[g];
+    if (q < 0 || q + 1 >= h->n) return fail(LEMPS_EINVAL, "apply_layer: gate qubit out of range");
+    if (used[q] || used[q + 1]) return fail(LEMPS_EINVAL, "apply_layer: gates of a layer must act on disjoint pairs");
+    used[q] = used[q + 1] = 1;
+  }
+  for (int i = 0; i < layer->n_gates * 32; ++i)
+    if (!std::isfinite(layer->gates[i])) return fail(LEMPS_EINVAL, "apply_layer: non-finite gate entry");
+  // sum K^dagger K = I
+  double s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (int k = 0; k < layer->n_kraus; ++k) {
+    const double* K = layer->kraus + 8 * k;
+    for (int i = 0; i < 2; ++i)
+      for (int j = 0; j < 2; ++j)
+        for (int l = 0; l < 2; ++l) {
+          double ar = K[(l * 2 + i) * 2], ai = -K[(l * 2 + i) * 2 + 1];
+          double br = K[(l * 2 + j) * 2], bi = K[(l * 2 + j) * 2 + 1];
+          s[(i * 2 + j) * 2] += ar * br - ai * bi;
+          s[(i * 2 + j) * 2 + 1] += ar * bi + ai * br;
+        }
+  }
+  double dev = std::fabs(s[0] - 1) + std::fabs(s[6] - 1) + std::fabs(s[1]) + std::fabs(s[7]) + std::fabs(s[2]) +
+               std::fabs(s[3]) + std::fabs(s[4]) + std::fabs(s[5]);
+  if (!(dev < 1e-9)) return fail(LEMPS_EINVAL, "apply_layer: Kraus set is not trace preserving");
+  if (h->prec == LEMPS_FP64) return apply_layer_t<double>(h, layer);
+  return apply_layer_t<float>(h, layer);
+}
+
+lemps_status unravel_opt(const double* rho_a, const double* kraus, int32_t n_kraus, int64_t batch, double* kraus_out,
+                         double* e_av, void* stream) {
+  if (!rho_a || !kraus || !kraus_out || batch < 0) return fail(LEMPS_EINVAL, "unravel_opt: bad argument");
+  if (n_kraus < 1 || n_kraus > 4) return fail(LEMPS_EINVAL, "unravel_opt: n_kraus must be 1..4");
+  if (batch == 0) return LEMPS_OK;
+  launch_unravel_batch((const zd*)rho_a, (const zd*)kraus, n_kraus, batch, (zd*)kraus_out, e_av, (cudaStream_t)stream);
+  return check_cuda(nullptr, "unravel_opt");
+}
+
+lemps_status sample_branch(lemps_handle h, int64_t gate, int32_t slot, int32_t* branch_out) {
+  if (!h || !branch_out || slot < 0 || slot > 1) return fail(LEMPS_EINVAL, "sample_branch: bad argument");
+  if (h->sticky) return fail(LEMPS_ECUDA, "sample_branch: sticky CUDA error");
+  if (gate < 0 || gate >= h->gates_done) return fail(LEMPS_ESTATE, "sample_branch: gate not applied yet");
+  if (gate >= h->log_cap) return fail(LEMPS_ESTATE, "sample_branch: gate beyond log_capacity");
+  std::vector<int8_t> tmp(h->B);
+  if (cudaMemcpyAsync(tmp.data(), h->blog + (gate * 2 + slot) * h->B, h->B, cudaMemcpyDeviceToHost, h->stream) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(h->stream) != cudaSuccess)
+    return check_cuda(h, "sample_branch");
+  for (int64_t t = 0; t < h->B; ++t) branch_out[t] = tmp[t];
+  return LEMPS_OK;
+}
+
+lemps_status measure(lemps_handle h, lemps_measurement* m) {
+  if (!h || !m || !m->z_mean || !m->z_stderr || !m->zz_mean || !m->zz_stderr) return fail(LEMPS_EINVAL, "measure: bad argument");
+  if (h->sticky) return fail(LEMPS_ECUDA, "measure: sticky CUDA error");
+  if (h->prec == LEMPS_FP64) return measure_t<double>(h, m);
+  return measure_t<float>(h, m);
+}
+
+lemps_status sim_export_mps(lemps_handle h, int64_t traj, int32_t* bond_dims, double* tensors) {
+  if (!h || !bond_dims || !tensors || traj < 0 || traj >= h->B) return fail(LEMPS_EINVAL, "sim_export_mps: bad argument");
+  if (h->sticky) return fail(LEMPS_ECUDA, "sim_export_mps: sticky CUDA error");
+  const int n = h->n;
+  if (cudaMemcpyAsync(bond_dims, h->bond + traj * (n + 1), sizeof(int32_t) * (n + 1), cudaMemcpyDeviceToHost, h->stream) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(h->stream) != cudaSuccess)
+    return check_cuda(h, "sim_export_mps");
+  int64_t out = 0;
+  for (int k = 0; k < n; ++k) {
+    const int cl = h->cap_h[k], cr = h->cap_h[k + 1];
+    const int64_t slot = (int64_t)cl * 2 * cr;
+    std::vector<char> buf(slot * h->elem);
+    const char* src = (const char*)h->mps + (h->off_h[k] + traj * slot) * h->elem;
+    if (cudaMemcpy(buf.data(), src, buf.size(), cudaMemcpyDeviceToHost) != cudaSuccess) return check_cuda(h, "sim_export_mps");
+    const int dl = bond_dims[k], dr = bond_dims[k + 1];
+    for (int r = 0; r < 2 * dl; ++r)
+      for (int b = 0; b < dr; ++b) {
+        const int64_t e = (int64_t)r * cr + b;
+        double re, im;
+        if (h->prec == LEMPS_FP64) {
+          const double* p = (const double*)buf.data();
+          re = p[2 * e]; im = p[2 * e + 1];
+        } else {
+          const float* p = (const float*)buf.data();
+          re = p[2 * e]; im = p[2 * e + 1];
+        }
+        tensors[2 * out] = re;
+        tensors[2 * out + 1] = im;
+        ++out;
+      }
+  }
+  return LEMPS_OK;
+}
+
+lemps_status sim_sync(lemps_handle h) {
+  if (!h) return fail(LEMPS_EINVAL, "sim_sync: null handle");
+  if (h->sticky) return fail(LEMPS_ECUDA, "sim_sync: sticky CUDA error");
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return check_cuda(h, "sim_sync");
+  std::vector<int32_t> st(h->B);
+  if (cudaMemcpy(st.data(), h->status, sizeof(int32_t) * h->B, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return check_cuda(h, "sim_sync");
+  for (auto v : st)
+    if (v) return fail(LEMPS_ENUMERIC, "sim_sync: a trajectory flagged a numerical failure");
+  return LEMPS_OK;
+}
+
+lemps_status sim_profile(lemps_handle h, int32_t enable, double* ms, int64_t* launches) {
+  if (!h) return fail(LEMPS_EINVAL, "sim_profile: null handle");
+  if (ms || launches) {
+    h->collect_profile();
+    for (int k = 0; k < LEMPS_NUM_KERNEL_KINDS; ++k) {
+      if (ms) ms[k] = h->prof_ms[k];
+      if (launches) launches[k] = h->prof_n[k];
+    }
+  }
+  if (enable && !h->profiling) {
+    h->collect_profile();
+    for (int k = 0; k < LEMPS_NUM_KERNEL_KINDS; ++k) { h->prof_ms[k] = 0.0; h->prof_n[k] = 0; }
+  }
+  h->profiling = enable != 0;
+  return check_cuda(h, "sim_profile");
+}
+
+lemps_status destroy(lemps_handle h) {
+  if (!h) return fail(LEMPS_EINVAL, "destroy: null handle");
+  cudaStreamSynchronize(h->stream);
+  h->collect_profile();
+  h->release();
+  delete h;
+  return LEMPS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,101 @@
+// Shared device helpers: complex arithmetic templated on the real type,
+// Philox4x64-10, reductions and the per-simulation device context.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <math.h>
+
+namespace lemps {
+
+template <class R>
+struct alignas(2 * sizeof(R)) cpx {
+  R re, im;
+};
+
+template <class R> __host__ __device__ __forceinline__ cpx<R> mk(R a, R b) { cpx<R> z; z.re = a; z.im = b; return z; }
+template <class R> __host__ __device__ __forceinline__ cpx<R> operator+(cpx<R> a, cpx<R> b) { return mk(a.re + b.re, a.im + b.im); }
+template <class R> __host__ __device__ __forceinline__ cpx<R> operator-(cpx<R> a, cpx<R> b) { return mk(a.re - b.re, a.im - b.im); }
+template <class R> __host__ __device__ __forceinline__ cpx<R> operator-(cpx<R> a) { return mk(-a.re, -a.im); }
+template <class R> __host__ __device__ __forceinline__ cpx<R> operator*(cpx<R> a, cpx<R> b) {
+  return mk(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
+}
+template <class R> __host__ __device__ __forceinline__ cpx<R> operator*(R s, cpx<R> a) { return mk(s * a.re, s * a.im); }
+template <class R> __host__ __device__ __forceinline__ cpx<R> operator*(cpx<R> a, R s) { return mk(s * a.re, s * a.im); }
+template <class R> __host__ __device__ __forceinline__ cpx<R>& operator+=(cpx<R>& a, cpx<R> b) { a.re += b.re; a.im += b.im; return a; }
+template <class R> __host__ __device__ __forceinline__ cpx<R>& operator-=(cpx<R>& a, cpx<R> b) { a.re -= b.re; a.im -= b.im; return a; }
+template <class R> __host__ __device__ __forceinline__ cpx<R> conj(cpx<R> a) { return mk(a.re, -a.im); }
+template <class R> __host__ __device__ __forceinline__ R norm2(cpx<R> a) { return a.re * a.re + a.im * a.im; }
+// conj(a) * b
+template <class R> __host__ __device__ __forceinline__ cpx<R> cdot(cpx<R> a, cpx<R> b) {
+  return mk(a.re * b.re + a.im * b.im, a.re * b.im - a.im * b.re);
+}
+// acc += a * b
+template <class R> __host__ __device__ __forceinline__ void cfma(cpx<R>& acc, cpx<R> a, cpx<R> b) {
+  acc.re = fma(a.re, b.re, fma(-a.im, b.im, acc.re));
+  acc.im = fma(a.re, b.im, fma(a.im, b.re, acc.im));
+}
+// acc += conj(a) * b
+template <class R> __host__ __device__ __forceinline__ void cfmac(cpx<R>& acc, cpx<R> a, cpx<R> b) {
+  acc.re = fma(a.re, b.re, fma(a.im, b.im, acc.re));
+  acc.im = fma(a.re, b.im, fma(-a.im, b.re, acc.im));
+}
+template <class D, class S> __host__ __device__ __forceinline__ cpx<D> cast(cpx<S> a) { return mk<D>((D)a.re, (D)a.im); }
+
+typedef cpx<double> zd;
+typedef cpx<float> zf;
+
+// ---- Philox4x64-10 (Salmon et al., SC'11) ------------------------------------
+__device__ __forceinline__ void philox4x64_10(uint64_t c[4], uint64_t k0, uint64_t k1) {
+  const uint64_t M0 = 0xD2E7470EE14C6C93ULL, M1 = 0xCA5A826395121157ULL;
+  const uint64_t W0 = 0x9E3779B97F4A7C15ULL, W1 = 0xBB67AE8584CAA73BULL;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) { k0 += W0; k1 += W1; }
+    uint64_t hi0 = __umul64hi(M0, c[0]), lo0 = M0 * c[0];
+    uint64_t hi1 = __umul64hi(M1, c[2]), lo1 = M1 * c[2];
+    uint64_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
+  }
+}
+
+constexpr uint64_t kDomainTrajectory = 0x4C454D5053545241ULL;
+
+__device__ __forceinline__ double philox_uniform(uint64_t seed, uint64_t traj, uint64_t gate, uint64_t slot) {
+  uint64_t c[4] = {traj, gate, slot, 0ULL};
+  philox4x64_10(c, seed, kDomainTrajectory);
+  return (double)(c[0] >> 11) * (1.0 / 9007199254740992.0);
+}
+
+// ---- status codes written per trajectory ------------------------------------
+enum TrajStatus : int32_t {
+  TS_OK = 0,
+  TS_NAN = 1,        // NaN / Inf in a reduced density or branch weight
+  TS_NORM = 2,       // two-site tensor lost its norm
+  TS_JACOBI = 4,     // eigensolver hit its sweep cap above tolerance
+  TS_SHAPE = 8       // bond dimensions outside capacity (internal error)
+};
+
+// ---- block reductions ---------------------------------------------------------
+template <class T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum over the block; every thread receives the result.  `scratch` holds at
+// least blockDim.x/32 values.
+template <class T>
+__device__ __forceinline__ T block_sum(T v, T* scratch) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  __syncthreads();
+  if (lane == 0) scratch[w] = v;
+  __syncthreads();
+  T s = 0;
+  for (int i = 0; i < nw; ++i) s += scratch[i];
+  return s;
+}
+
+}  // namespace lemps

@@ -1,0 +1,305 @@
+"""GPU parity tests: the CUDA path (through the C ABI) against the CPU oracle on
+the same seeded inputs and Philox stream.  Tolerances: FP64 mode 1e-10 per
+trajectory on observables and states (1e-8 after hundreds of truncating gates),
+mixed mode 1e-4 per trajectory on trajectories whose branch sequence matches,
+averages within 4 standard errors of exact density-matrix evolution."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import adjoint as A
+from oracle import trajectories as T
+from oracle import unravel as U
+from paper_2508_05745_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def L():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2508_05745_gb300 import build, lemps
+    build.build()
+    return lemps
+
+
+def run_gpu(L, circ, chi, n_traj, seed, precision="fp64", unravel="optimal", cutoff=None, traj_offset=0):
+    sim = L.Simulation(circ.n_qubits, chi, n_traj, seed=seed, precision=precision, unravel=unravel,
+                       cutoff=cutoff, log_capacity=circ.n_gates, traj_offset=traj_offset)
+    sim.run(circ)
+    res = sim.measure()
+    branches = np.zeros((n_traj, 2 * circ.n_gates), dtype=np.int32)
+    for g in range(circ.n_gates):
+        for s in range(2):
+            branches[:, 2 * g + s] = sim.sample_branch(g, s)
+    return sim, res, branches
+
+
+def contract(tensors):
+    psi = tensors[0].reshape(2, -1)
+    for t in tensors[1:]:
+        psi = np.einsum('xa,asb->xsb', psi, t).reshape(-1, t.shape[2])
+    return psi.reshape(-1)
+
+
+# --- K-c: the unraveling kernel ---------------------------------------------------
+
+CHANNELS = {
+    "depolarizing": I.depolarizing_kraus(0.02),
+    "full_depolarizing": I.depolarizing_kraus(1.0),
+    "amplitude_damping": I.amplitude_damping_kraus(0.3),
+    "dephasing": I.dephasing_kraus(0.25),
+    "ad_then_dephasing": I.compose_kraus(I.dephasing_kraus(0.01), I.amplitude_damping_kraus(0.01)),
+    "depolarizing_strong": I.depolarizing_kraus(0.7),
+}
+
+
+@pytest.mark.parametrize("name", list(CHANNELS))
+def test_unravel_opt_matches_oracle(L, name):
+    rng = np.random.default_rng(7)
+    kraus = CHANNELS[name]
+    rhos = []
+    for i in range(300):
+        a = rng.standard_normal((2, 2)) + 1j * rng.standard_normal((2, 2))
+        r = a @ a.conj().T
+        rhos.append(r / np.trace(r).real * (0.5 + i % 3))     # any trace
+    rhos += [np.eye(2) / 2, np.diag([1.0, 0.0]), np.diag([0.7, 0.3]) + 0j]
+    rho = np.stack(rhos).astype(np.complex128)
+    kout, e_av = L.unravel_opt(torch.from_numpy(rho).cuda(), torch.from_numpy(kraus).cuda())
+    kout, e_av = kout.cpu().numpy(), e_av.cpu().numpy()
+    for b in range(len(rho)):
+        rn = rho[b] / np.trace(rho[b]).real
+        ref, _ = U.optimal_unraveling(rn, kraus)
+        assert np.allclose(kout[b], ref[:4], atol=1e-10), (name, b)
+        assert abs(e_av[b] - U.unraveling_entropy(ref, rn)) < 1e-12
+        assert np.allclose(sum(k.conj().T @ k for k in kout[b]), np.eye(2), atol=1e-12)
+
+
+# --- full path, exact bond dimension -------------------------------------------------
+
+@pytest.fixture(scope="module")
+def small_exact(L):
+    w = I.workload_small_exact(seed=0)
+    sim, res, br = run_gpu(L, w["circuit"], 16, 256, seed=0)
+    states = [contract(sim.export_mps(t)[0]) for t in range(24)]
+    sim.destroy()
+    return w, res, br, states
+
+
+def test_small_exact_per_trajectory_fp64(small_exact):
+    """n=8 depth-8 depolarizing brickwork, chi=16 (no truncation): every checked
+    trajectory has the oracle's branch sequence and state to 1e-10."""
+    w, res, br, states = small_exact
+    assert res["n_failed"] == 0
+    for t in range(24):
+        ref = T.dense_trajectory(w["circuit"], t, 0)
+        assert list(br[t]) == ref.branch
+        assert abs(abs(np.vdot(ref.state, states[t])) - 1.0) < 1e-10
+        assert np.allclose(res["z"][t], ref.z, atol=1e-10)
+        assert np.allclose(res["zz"][t], ref.zz, atol=1e-10)
+        assert abs(res["s_half"][t] - ref.s_half) < 1e-10
+    assert np.all(res["eps_bound"] == 0.0)
+
+
+@pytest.mark.slow
+def test_small_exact_averages_match_density_matrix(small_exact):
+    w, res, _, _ = small_exact
+    rho = T.density_evolution(w["circuit"])
+    zr, zzr = T.density_observables(rho, 8)
+    z = np.concatenate([(res["z_mean"] - zr) / res["z_stderr"], (res["zz_mean"] - zzr) / res["zz_stderr"]])
+    assert np.max(np.abs(z)) < 4.0, z
+    m, s = T.trajectory_statistics(res["z"])
+    assert np.allclose(m, res["z_mean"], atol=1e-13) and np.allclose(s, res["z_stderr"], atol=1e-13)
+
+
+def test_small_exact_mixed_precision(L, small_exact):
+    """Mixed mode (complex64 storage and eigensolver): trajectories with the
+    same branch sequence agree with the FP64 oracle to 1e-4."""
+    w, res64, br64, _ = small_exact
+    sim, res, br = run_gpu(L, w["circuit"], 16, 256, seed=0, precision="mixed")
+    sim.destroy()
+    same = np.all(br == br64, axis=1)
+    assert same.mean() > 0.95
+    for t in np.nonzero(same)[0][:64]:
+        ref = T.dense_trajectory(w["circuit"], int(t), 0)
+        assert list(br[t]) == ref.branch
+        assert np.allclose(res["z"][t], ref.z, atol=1e-4)
+        assert np.allclose(res["zz"][t], ref.zz, atol=1e-4)
+        assert abs(res["s_half"][t] - ref.s_half) < 1e-4
+
+
+# --- truncation, uneven bond dimensions ---------------------------------------------
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-9), ("mixed", 1e-4)])
+def test_truncated_run_matches_oracle_mps(L, precision, tol):
+    circ = I.random_brickwork(10, 10, I.depolarizing_kraus(0.05), seed=4)
+    n_traj = 16
+    sim, res, br = run_gpu(L, circ, 4, n_traj, seed=3, precision=precision, cutoff=1e-14)
+    sim.destroy()
+    matched = 0
+    for t in range(n_traj):
+        ref = T.mps_trajectory(circ, t, 3, chi_max=4, cutoff=1e-14)
+        if precision == "mixed" and list(br[t]) != ref.branch:
+            continue
+        matched += 1
+        assert list(br[t]) == ref.branch
+        assert np.allclose(res["z"][t], ref.z, atol=tol)
+        assert np.allclose(res["zz"][t], ref.zz, atol=tol)
+        assert abs(res["s_half"][t] - ref.s_half) < tol
+        assert abs(res["eps_bound"][t] - ref.eps_bound) < max(tol, 1e-3 if precision == "mixed" else 0)
+    assert matched >= n_traj - 2
+    assert res["eps_hat"] > 0
+
+
+@pytest.mark.slow
+def test_ad_dephasing_n32_chi64(L):
+    """The AD-then-dephasing workload (n=32, depth 20, chi=64): FP64 GPU
+    trajectories equal the oracle MPS trajectories; mixed mode within 1e-4."""
+    w = I.workload_ad_dephasing(seed=0, n_traj=3)
+    circ = w["circuit"]
+    sim, res, br = run_gpu(L, circ, 64, 3, seed=0)
+    sim.destroy()
+    simm, resm, brm = run_gpu(L, circ, 64, 3, seed=0, precision="mixed")
+    simm.destroy()
+    for t in range(2):
+        ref = T.mps_trajectory(circ, t, 0, chi_max=64, cutoff=1e-20)
+        assert list(br[t]) == ref.branch
+        assert np.allclose(res["z"][t], ref.z, atol=1e-8)
+        assert np.allclose(res["zz"][t], ref.zz, atol=1e-8)
+        assert abs(res["s_half"][t] - ref.s_half) < 1e-8
+        assert abs(res["eps_bound"][t] - ref.eps_bound) < 1e-6
+        if list(brm[t]) == ref.branch:
+            assert np.allclose(resm["z"][t], ref.z, atol=1e-4)
+
+
+def test_coin_noise_full_depolarizing(L):
+    """Two-qubit depolarizing reading: with probability p both qubits are fully
+    depolarized (optimal unraveling of each), otherwise nothing happens."""
+    circ = I.random_brickwork(12, 8, I.depolarizing_kraus(1.0), seed=6, coin_p=0.3)
+    sim, res, br = run_gpu(L, circ, 16, 16, seed=9, cutoff=1e-14)
+    sim.destroy()
+    for t in range(16):
+        ref = T.mps_trajectory(circ, t, 9, chi_max=16, cutoff=1e-14)
+        assert list(br[t]) == ref.branch
+        assert np.allclose(res["z"][t], ref.z, atol=1e-9)
+        assert abs(res["s_half"][t] - ref.s_half) < 1e-9
+    assert (br == -1).any() and (br >= 0).any()
+
+
+def test_given_unraveling_mode(L):
+    circ = I.random_brickwork(6, 6, I.amplitude_damping_kraus(0.2), seed=2)
+    sim, res, br = run_gpu(L, circ, 8, 8, seed=1, unravel="given")
+    sim.destroy()
+    for t in range(8):
+        ref = T.dense_trajectory(circ, t, 1, mode="given")
+        assert list(br[t]) == ref.branch
+        assert np.allclose(res["z"][t], ref.z, atol=1e-10)
+
+
+def test_traj_offset_shards_reproduce_the_full_run(L):
+    """Trajectory ids key the Philox counter, so two shards reproduce one run."""
+    circ = I.random_brickwork(6, 4, I.depolarizing_kraus(0.05), seed=8)
+    _, full, _ = run_gpu(L, circ, 8, 8, seed=4)
+    _, a, _ = run_gpu(L, circ, 8, 4, seed=4)
+    _, b, _ = run_gpu(L, circ, 8, 4, seed=4, traj_offset=4)
+    assert np.array_equal(np.concatenate([a["z"], b["z"]]), full["z"])
+
+
+# --- edge cases ---------------------------------------------------------------------
+
+def test_two_qubits_single_trajectory(L):
+    circ = I.random_brickwork(2, 5, I.depolarizing_kraus(0.1), seed=3)
+    sim, res, br = run_gpu(L, circ, 2, 1, seed=2)
+    sim.destroy()
+    ref = T.dense_trajectory(circ, 0, 2)
+    assert list(br[0]) == ref.branch
+    assert np.allclose(res["z"][0], ref.z, atol=1e-10)
+
+
+def test_odd_n_and_empty_layer(L):
+    circ = I.random_brickwork(7, 5, I.depolarizing_kraus(0.05), seed=5)
+    circ.layers.insert(2, I.Layer(np.zeros(0, np.int32), np.zeros((0, 4, 4), complex), I.depolarizing_kraus(0.05)))
+    sim, res, br = run_gpu(L, circ, 8, 4, seed=6)
+    sim.destroy()
+    for t in range(4):
+        ref = T.dense_trajectory(circ, t, 6)
+        assert list(br[t]) == ref.branch
+        assert np.allclose(res["z"][t], ref.z, atol=1e-10)
+
+
+def test_invalid_inputs_are_rejected(L):
+    sim = L.Simulation(4, 4, 2, log_capacity=4)
+    bad_kraus = I.Layer(np.array([0], np.int32), np.eye(4, dtype=complex)[None], 1.1 * I.depolarizing_kraus(0.1))
+    with pytest.raises(L.LempsError) as e:
+        sim.apply_layer(bad_kraus)
+    assert e.value.status == L.LEMPS_EINVAL
+    overlap = I.Layer(np.array([0, 1], np.int32), np.stack([np.eye(4, dtype=complex)] * 2), I.depolarizing_kraus(0.1))
+    with pytest.raises(L.LempsError):
+        sim.apply_layer(overlap)
+    with pytest.raises(L.LempsError) as e:
+        sim.sample_branch(0, 0)
+    assert e.value.status == L.LEMPS_ESTATE
+    sim.destroy()
+    with pytest.raises(L.LempsError):
+        L.Simulation(4, 0, 2)
+
+
+# --- differentiation --------------------------------------------------------------------
+
+@pytest.mark.parametrize("chi,dtype", [(8, np.complex128), (64, np.complex128), (64, np.complex64)])
+def test_unravel_grad_matches_oracle(L, chi, dtype):
+    w = I.workload_adjoint(seed=11, batch=48, chi=chi, dtype=dtype)
+    th = torch.from_numpy(w["theta"]).cuda()
+    p = torch.from_numpy(w["p"]).cuda()
+    h = torch.from_numpy(w["H"]).cuda()
+    cost, grad, rho = L.unravel_grad(th, p, h)
+    cost, grad, rho = cost.cpu().numpy(), grad.cpu().numpy(), rho.cpu().numpy()
+    tol_rho = 1e-13 if dtype == np.complex128 else 1e-6
+    for b in range(0, 48, 3):
+        ref_rho = A.reduced_target(w["theta"][b].astype(np.complex128))
+        ref_rho /= np.trace(ref_rho).real
+        assert np.allclose(rho[b], ref_rho, atol=tol_rho)
+        kr = I.depolarizing_kraus(w["p"][b])
+        assert abs(cost[b] - A.expected_entropy(w["H"][b], rho[b], kr)) < 1e-12
+        fd = A.fd_gradient(w["H"][b], rho[b], kr)
+        assert np.allclose(grad[b], fd, atol=1e-7 * max(1.0, np.abs(fd).max())), (b, np.abs(grad[b] - fd).max())
+
+
+def test_descent_on_device_approaches_optimum(L):
+    w = I.workload_adjoint(seed=12, batch=32, chi=8)
+    th = torch.from_numpy(w["theta"]).cuda()
+    p = torch.from_numpy(w["p"]).cuda()
+    h = torch.from_numpy(w["H"]).cuda()
+    cost0, _, rho = L.unravel_grad(th, p, h, want_grad=False)
+    hn, trace = L.unravel_descend(rho, p, h, steps=50, lr=0.5)
+    trace = trace.cpu().numpy()
+    rho = rho.cpu().numpy()
+    cost0 = cost0.cpu().numpy()
+    grid_hits = 0
+    for b in range(32):
+        kr = I.depolarizing_kraus(w["p"][b])
+        eof = U.unraveling_entropy(U.optimal_unraveling(rho[b], kr)[0], rho[b])
+        assert trace[-1, b] >= eof - 1e-12
+        assert trace[-1, b] <= cost0[b] + 1e-12
+        if b < 4:
+            g = A.grid_search(rho[b], kr, 24)[0]
+            grid_hits += trace[-1, b] <= g + 1e-3
+            ref_h, ref_costs = A.gradient_descent(w["H"][b], rho[b], kr, steps=5, lr=0.5)
+            assert np.allclose(trace[:5, b], ref_costs, atol=1e-6)
+    assert grid_hits >= 2
+
+
+def test_autograd_function_backward(L):
+    w = I.workload_adjoint(seed=13, batch=4, chi=8)
+    th = torch.from_numpy(w["theta"]).cuda()
+    p = torch.from_numpy(w["p"]).cuda()
+    h = torch.from_numpy(w["H"]).cuda().requires_grad_(True)
+    F = L.UnravelCost.function()
+    cost = F.apply(h, th, p)
+    cost.sum().backward()
+    _, grad, _ = L.unravel_grad(th, p, h.detach())
+    assert torch.allclose(h.grad, grad)
