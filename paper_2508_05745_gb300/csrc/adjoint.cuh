@@ -26,18 +26,17 @@ namespace adj {
 __device__ inline void jacobi_herm4(zd* a, zd* v, double* w) {
   for (int i = 0; i < 4; ++i)
     for (int j = 0; j < 4; ++j) v[i * 4 + j] = mk(i == j ? 1.0 : 0.0, 0.0);
+  double tot = 0.0;
+  for (int i = 0; i < 16; ++i) tot += norm2(a[i]);
+  const double thresh = 1e-17 * sqrt(tot);
   for (int sweep = 0; sweep < 40; ++sweep) {
-    double off = 0.0, tot = 0.0;
-    for (int i = 0; i < 16; ++i) {
-      tot += norm2(a[i]);
-      if (i / 4 != i % 4) off += norm2(a[i]);
-    }
-    if (off <= 1e-32 * tot || tot == 0.0) break;
+    bool rotated = false;
     for (int p = 0; p < 3; ++p)
       for (int q = p + 1; q < 4; ++q) {
         zd g = a[p * 4 + q];
         double gn = sqrt(norm2(g));
-        if (gn == 0.0) continue;
+        if (gn <= thresh) continue;
+        rotated = true;
         double zeta = (a[q * 4 + q].re - a[p * 4 + p].re) / (2.0 * gn);
         double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
         double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
@@ -57,6 +56,7 @@ __device__ inline void jacobi_herm4(zd* a, zd* v, double* w) {
           a[q * 4 + k] = s * xp + c * xq;
         }
       }
+    if (!rotated) break;
   }
   for (int i = 0; i < 4; ++i) w[i] = a[i * 4 + i].re;
 }

@@ -53,6 +53,8 @@ struct lemps_sim {
   double* eps_tot = nullptr;
   double* disc_last = nullptr;
   int32_t* status = nullptr;
+  int32_t* kept = nullptr;
+  double* trace = nullptr;
   int8_t* blog = nullptr;
   int64_t log_cap = 0;
   zd* layer_buf = nullptr;   // gates + kraus of the current layer
@@ -131,6 +133,8 @@ struct lemps_sim {
     v.eps_tot = eps_tot;
     v.disc_last = disc_last;
     v.status = status;
+    v.kept = kept;
+    v.trace = trace;
     return v;
   }
 };
@@ -157,18 +161,16 @@ void move_center_to(lemps_sim* h, int target) {
   while (h->center > target) { launch_move<R>(h, h->center, -1); --h->center; }
 }
 
-template <class R>
-struct JacobiParams;
-template <>
-struct JacobiParams<double> { static constexpr int sweeps = 20; static constexpr double tol = 1e-15; };
-template <>
-struct JacobiParams<float> { static constexpr int sweeps = 16; static constexpr float tol = 2e-7f; };
+constexpr int kHeevThreads = 512;
 
+// Hermitian eigensolve of the Gram matrix; keeps the top min(chi_max,
+// #{l > cutoff * trace}) eigenpairs (vectors = 1) or computes every
+// eigenvalue (vectors = 0, cutoff = 0).
 template <class R>
-void launch_jacobi(lemps_sim* h, int q, int mode) {
+void launch_heev(lemps_sim* h, int q, int mode, double cutoff, int keep_max, int vectors) {
   h->timed(LEMPS_K_EIG, [&] {
-    k_jacobi<R><<<(unsigned)h->B, kThreads, 0, h->stream>>>(h->view<R>(), q, mode, JacobiParams<R>::sweeps,
-                                                             (R)JacobiParams<R>::tol);
+    k_heev<R><<<(unsigned)h->B, kHeevThreads, 0, h->stream>>>(heev_view(h->view<R>()), q, mode, cutoff, keep_max,
+                                                               vectors);
   });
 }
 
@@ -213,9 +215,8 @@ lemps_status apply_layer_t(lemps_sim* h, const lemps_layer* L) {
     else if (g > 0) side = (q > L->left_qubit[g - 1]) ? 0 : 1;
     else side = 0;
     h->timed(LEMPS_K_GRAM, [&] { k_apply_gram<R><<<(unsigned)h->B, kThreads, 0, h->stream>>>(sv, q, side); });
-    launch_jacobi<R>(h, q, side);
-    h->timed(LEMPS_K_SPLIT,
-             [&] { k_split<R><<<(unsigned)h->B, kThreads, 0, h->stream>>>(sv, q, side, h->cfg.trunc_cutoff); });
+    launch_heev<R>(h, q, side, h->cfg.trunc_cutoff, h->chi, 1);
+    h->timed(LEMPS_K_SPLIT, [&] { k_split<R><<<(unsigned)h->B, kThreads, 0, h->stream>>>(sv, q, side); });
     h->center = (side == 0) ? q + 1 : q;
   }
   h->timed(LEMPS_K_OTHER, [&] { k_layer_end<R><<<grid_t, kThreads, 0, h->stream>>>(sv); });
@@ -267,7 +268,7 @@ lemps_status measure_t(lemps_sim* h, lemps_measurement* m) {
     k_obs_from_rho12<<<grid_t, kThreads, 0, h->stream>>>(h->rho12, B, n, q, z, zz);
     if (q == hb - 1) {
       k_site_gram<R><<<(unsigned)B, kThreads, 0, h->stream>>>(sv, q);
-      launch_jacobi<R>(h, q, 2);
+      launch_heev<R>(h, q, 2, 0.0, h->chi, 0);
       k_entropy_from_evals<<<grid_t, kThreads, 0, h->stream>>>(h->evals, 2 * h->chi, h->bond, n + 1, q + 1, B, sh);
     }
     launch_move<R>(h, q, +1);
@@ -369,6 +370,8 @@ lemps_status sim_create(const lemps_config* cfg, lemps_handle* out) {
   h->eps_tot = (double*)A(sizeof(double) * h->B);
   h->disc_last = (double*)A(sizeof(double) * h->B);
   h->status = (int32_t*)A(sizeof(int32_t) * h->B);
+  h->kept = (int32_t*)A(sizeof(int32_t) * h->B);
+  h->trace = (double*)A(sizeof(double) * h->B);
   h->blog = (int8_t*)A(std::max<int64_t>(1, h->log_cap * 2 * h->B));
   h->layer_buf = (zd*)A(sizeof(zd) * h->layer_cap);
   h->obs = (double*)A(sizeof(double) * h->B * (2 * n + 1));

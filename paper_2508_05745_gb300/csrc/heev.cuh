@@ -1,0 +1,306 @@
+// Batched Hermitian eigensolver for the truncating split (one CTA per
+// trajectory): Householder tridiagonalization, bisection on Sturm counts for
+// the kept eigenvalues, inverse iteration for their eigenvectors,
+// Gram-Schmidt re-orthonormalization, and back-transformation.
+//
+// Only the top `keep` eigenpairs are formed, keep = min(chi_max, #{l >
+// cutoff * trace}, n); the count comes from one Sturm sequence at
+// cutoff * trace, so eigenvalues that will be discarded are never computed.
+//
+// Layout: G (n x n row-major, Hermitian) in ws1, overwritten.  Householder
+// vectors in ws3 (row j holds v_j, unit norm, entries > j).  Eigenvectors are
+// written column-major to ws2: U[k * n + i], k < keep.  Eigenvalues (double,
+// descending) to evals[0..keep), keep and the trace to kept[] / trace[].
+#pragma once
+
+#include "common.cuh"
+
+namespace lemps {
+
+template <class R>
+struct HeevView {
+  cpx<R>* ws1;      // Gram matrix, then LDL^T scratch of the inverse iteration
+  cpx<R>* ws2;      // eigenvectors (output)
+  cpx<R>* ws3;      // Householder vectors
+  int64_t ws_stride;
+  double* evals;    // [B][2 chi]
+  int32_t* kept;    // [B]
+  double* trace;    // [B]
+  int32_t* bond;    // [B][n+1]
+  int32_t nq;       // qubits (bond row length n+1)
+  int32_t chi;
+  int64_t B;
+};
+
+// Number of eigenvalues of the real symmetric tridiagonal (d, e) that are
+// strictly greater than x (Sturm sequence of T - x I with a pivot guard).
+template <class R>
+__device__ __forceinline__ int sturm_greater(const R* d, const R* e2, int n, R x, R pivmin) {
+  int neg = 0;
+  R q = d[0] - x;
+  if (fabs(q) < pivmin) q = -pivmin;
+  neg += (q < 0);
+  for (int i = 1; i < n; ++i) {
+    q = (d[i] - x) - e2[i - 1] / q;
+    if (fabs(q) < pivmin) q = -pivmin;
+    neg += (q < 0);
+  }
+  return n - neg;
+}
+
+// Deterministic start vector entries in [0.5, 1.5) (a hash of (k, i)).
+__device__ __forceinline__ float start_entry(int k, int i) {
+  uint32_t h = (uint32_t)k * 0x9E3779B1u ^ (uint32_t)(i + 1) * 0x85EBCA77u;
+  h ^= h >> 15; h *= 0x2C1B3C6Du; h ^= h >> 12; h *= 0x297A2D39u; h ^= h >> 15;
+  return 0.5f + (float)(h >> 8) * (1.0f / 16777216.0f);
+}
+
+// mode / q select the matrix size as in gram_size(); want_vectors = 0 returns
+// eigenvalues only (all n of them when cutoff = 0).
+template <class R>
+__global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, double cutoff, int keep_max,
+                                               int want_vectors) {
+  const int64_t t = blockIdx.x;
+  if (t >= s.B) return;
+  const int32_t* bd = s.bond + t * (s.nq + 1);
+  const int n = mode == 0 ? 2 * bd[q] : (mode == 1 ? 2 * bd[q + 2] : bd[q + 1]);
+  cpx<R>* G = s.ws1 + t * s.ws_stride;
+  cpx<R>* Hv = s.ws3 + t * s.ws_stride;
+  cpx<R>* U = s.ws2 + t * s.ws_stride;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+
+  __shared__ R sd[256], se[256], se2[256];   // real tridiagonal: diagonal, |offdiag|, offdiag^2
+  __shared__ cpx<R> sph[256];                // phases delta_i (T_real = D^dagger T_c D)
+  __shared__ cpx<R> sv[256], sw[256];        // Householder vector and w of the current step
+  __shared__ cpx<R> sec[256];                // complex off-diagonal e_j
+  __shared__ R red[32];
+  __shared__ double redd[32];
+  __shared__ int s_keep;
+  __shared__ double s_tr;
+
+  // trace (FP64) for the cutoff and the discarded weight
+  double trp = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) trp += (double)G[(int64_t)i * n + i].re;
+  trp = block_sum(trp, redd);
+  if (threadIdx.x == 0) s_tr = trp;
+
+  // ---- phase 1: tridiagonalization ------------------------------------------
+  for (int j = 0; j + 2 < n; ++j) {
+    const int m = n - j - 1;
+    R part = 0;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+      cpx<R> x = G[(int64_t)(j + 1 + i) * n + j];
+      sv[i] = x;
+      if (i > 0) part += norm2(x);
+    }
+    R sig = block_sum(part, red);  // syncs; sv visible
+    cpx<R> x0 = sv[0];
+    R ax0 = sqrt(norm2(x0));
+    R nrm = sqrt(sig + ax0 * ax0);
+    const bool reflect = sig > (R)0;
+    cpx<R> alpha = x0;
+    if (reflect) {
+      cpx<R> ph = (ax0 > 0) ? mk<R>(x0.re / ax0, x0.im / ax0) : mk<R>(1, 0);
+      alpha = mk<R>(-nrm * ph.re, -nrm * ph.im);
+      R inv = (R)1 / sqrt(sig + (ax0 + nrm) * (ax0 + nrm));   // ||x - alpha e1||
+      __syncthreads();
+      for (int i = threadIdx.x; i < m; i += blockDim.x) sv[i] = (i == 0) ? (x0 - alpha) * inv : sv[i] * inv;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      sd[j] = G[(int64_t)j * n + j].re;
+      sec[j] = alpha;
+    }
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+      Hv[(int64_t)j * n + i] = (i > j && reflect) ? sv[i - j - 1] : mk<R>(0, 0);
+    if (!reflect) continue;
+    // y = G_sub v (warp per row)
+    for (int r = warp; r < m; r += nwarp) {
+      const cpx<R>* row = G + (int64_t)(j + 1 + r) * n + (j + 1);
+      cpx<R> acc = mk<R>(0, 0);
+      for (int c = lane; c < m; c += 32) cfma(acc, row[c], sv[c]);
+      acc.re = warp_sum(acc.re);
+      acc.im = warp_sum(acc.im);
+      if (lane == 0) sw[r] = acc;
+    }
+    __syncthreads();
+    // s = v^dagger y (real), w = 2 y - 2 s v
+    R sp = 0;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+      cpx<R> c = cdot(sv[i], sw[i]);
+      sp += c.re;
+    }
+    R ss = block_sum(sp, red);
+    for (int i = threadIdx.x; i < m; i += blockDim.x) sw[i] = (R)2 * sw[i] - ((R)2 * ss) * sv[i];
+    __syncthreads();
+    // G_sub -= v w^dagger + w v^dagger
+    for (int64_t e = threadIdx.x; e < (int64_t)m * m; e += blockDim.x) {
+      const int r = (int)(e / m), c = (int)(e % m);
+      cpx<R>* g = G + (int64_t)(j + 1 + r) * n + (j + 1 + c);
+      *g = *g - sv[r] * conj(sw[c]) - sw[r] * conj(sv[c]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    if (n >= 2) {
+      sd[n - 2] = G[(int64_t)(n - 2) * n + (n - 2)].re;
+      sec[n - 2] = G[(int64_t)(n - 1) * n + (n - 2)];
+    }
+    sd[n - 1] = G[(int64_t)(n - 1) * n + (n - 1)].re;
+    // phase normalization: delta_{j+1} = delta_j e_j / |e_j|
+    cpx<R> dl = mk<R>(1, 0);
+    sph[0] = dl;
+    for (int j = 0; j + 1 < n; ++j) {
+      R a = sqrt(norm2(sec[j]));
+      se[j] = a;
+      se2[j] = a * a;
+      if (a > 0) dl = dl * mk<R>(sec[j].re / a, sec[j].im / a);
+      sph[j + 1] = dl;
+    }
+  }
+  __syncthreads();
+
+  // ---- phase 2: how many to keep, and the kept eigenvalues by bisection ------
+  R gl = sd[0], gu = sd[0], tnorm = 0;
+  for (int i = 0; i < n; ++i) {
+    R rad = (i > 0 ? se[i - 1] : (R)0) + (i + 1 < n ? se[i] : (R)0);
+    gl = fmin(gl, sd[i] - rad);
+    gu = fmax(gu, sd[i] + rad);
+    tnorm = fmax(tnorm, fabs(sd[i]) + rad);
+  }
+  const R eps = (sizeof(R) == 8) ? (R)2.2e-16 : (R)1.2e-7;
+  const R pivmin = fmax((R)1e-30 * tnorm, (sizeof(R) == 8) ? (R)1e-290 : (R)1e-35);
+  gl -= 2 * eps * tnorm + pivmin;
+  gu += 2 * eps * tnorm + pivmin;
+  if (threadIdx.x == 0) {
+    int cnt = (cutoff > 0.0) ? sturm_greater<R>(sd, se2, n, (R)(cutoff * s_tr), pivmin) : n;
+    int kp = min(cnt, min(keep_max, n));
+    s_keep = max(kp, 1);
+  }
+  __syncthreads();
+  const int keep = s_keep;
+  double* ev = s.evals + t * (2 * s.chi);
+  for (int k = threadIdx.x; k < keep; k += blockDim.x) {
+    // k-th largest: smallest x with sturm_greater(x) <= k
+    R lo = gl, hi = gu;
+    for (int it = 0; it < 200; ++it) {
+      R mid = (R)0.5 * (lo + hi);
+      if (hi - lo <= eps * (fabs(lo) + fabs(hi)) + (R)1e-3 * eps * tnorm + pivmin || mid <= lo || mid >= hi) break;
+      if (sturm_greater<R>(sd, se2, n, mid, pivmin) > k) lo = mid;
+      else hi = mid;
+    }
+    ev[k] = (double)((R)0.5 * (lo + hi));
+  }
+  if (threadIdx.x == 0) {
+    s.kept[t] = keep;
+    s.trace[t] = s_tr;
+  }
+  if (!want_vectors) return;
+  __syncthreads();
+
+  // ---- phase 3: inverse iteration (LDL^T of T - l I, two solves) ------------
+  // scratch in ws1 (the Gram matrix is no longer needed): per vector k the
+  // arrays dd[i], ll[i], z[i] at ((i * 3 + a) * keep + k) as R values.
+  R* scr = reinterpret_cast<R*>(G);
+  for (int k = threadIdx.x; k < keep; k += blockDim.x) {
+    const R lam = (R)ev[k];
+    R* zz = scr;
+    // factor: dd_0 = d_0 - l; ll_i = e_i / dd_i; dd_{i+1} = d_{i+1} - l - ll_i e_i
+    R dprev = sd[0] - lam;
+    if (fabs(dprev) < pivmin) dprev = pivmin;
+    zz[(0 * 3 + 0) * keep + k] = dprev;
+    for (int i = 0; i + 1 < n; ++i) {
+      R li = se[i] / dprev;
+      zz[(i * 3 + 1) * keep + k] = li;
+      R dn = (sd[i + 1] - lam) - li * se[i];
+      if (fabs(dn) < pivmin) dn = pivmin;
+      zz[((i + 1) * 3 + 0) * keep + k] = dn;
+      dprev = dn;
+    }
+    for (int i = 0; i < n; ++i) zz[(i * 3 + 2) * keep + k] = (R)start_entry(k, i);
+    for (int iter = 0; iter < 3; ++iter) {
+      // forward L y = b
+      R y = zz[(0 * 3 + 2) * keep + k];
+      zz[(0 * 3 + 2) * keep + k] = y;
+      for (int i = 1; i < n; ++i) {
+        y = zz[(i * 3 + 2) * keep + k] - zz[((i - 1) * 3 + 1) * keep + k] * y;
+        zz[(i * 3 + 2) * keep + k] = y;
+      }
+      // diagonal, backward L^T z = D^{-1} y
+      R zn = zz[((n - 1) * 3 + 2) * keep + k] / zz[((n - 1) * 3 + 0) * keep + k];
+      zz[((n - 1) * 3 + 2) * keep + k] = zn;
+      R amax = fabs(zn);
+      for (int i = n - 2; i >= 0; --i) {
+        zn = zz[(i * 3 + 2) * keep + k] / zz[(i * 3 + 0) * keep + k] - zz[(i * 3 + 1) * keep + k] * zn;
+        zz[(i * 3 + 2) * keep + k] = zn;
+        amax = fmax(amax, fabs(zn));
+      }
+      R sc = (amax > 0) ? (R)1 / amax : (R)1;
+      for (int i = 0; i < n; ++i) zz[(i * 3 + 2) * keep + k] *= sc;
+    }
+  }
+  __syncthreads();
+  // ---- phase 4: Gram-Schmidt (twice) in descending eigenvalue order ----------
+  // vectors are the columns z[i][k] = scr[(i*3+2)*keep + k]
+  for (int k = 0; k < keep; ++k) {
+    for (int pass = 0; pass < 2; ++pass) {
+      // coefficients c_j = <z_j, z_k> for j < k into sw[] (real parts)
+      for (int jj = warp; jj < k; jj += nwarp) {
+        R acc = 0;
+        for (int i = lane; i < n; i += 32) acc += scr[(i * 3 + 2) * keep + jj] * scr[(i * 3 + 2) * keep + k];
+        acc = warp_sum(acc);
+        if (lane == 0) sw[jj].re = acc;
+      }
+      __syncthreads();
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        R v = scr[(i * 3 + 2) * keep + k];
+        for (int jj = 0; jj < k; ++jj) v -= sw[jj].re * scr[(i * 3 + 2) * keep + jj];
+        scr[(i * 3 + 2) * keep + k] = v;
+      }
+      __syncthreads();
+    }
+    R part = 0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      R v = scr[(i * 3 + 2) * keep + k];
+      part += v * v;
+    }
+    R nn = block_sum(part, red);
+    R inv = nn > 0 ? (R)1 / sqrt(nn) : (R)0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) scr[(i * 3 + 2) * keep + k] *= inv;
+    __syncthreads();
+  }
+  // ---- phase 5: back-transformation U = Q D z, one warp per column ------------
+  constexpr int PER = 8;  // n <= 256 -> 8 elements per lane
+  for (int k = warp; k < keep; k += nwarp) {
+    cpx<R> y[PER];
+#pragma unroll
+    for (int a = 0; a < PER; ++a) {
+      const int i = lane + 32 * a;
+      y[a] = (i < n) ? sph[i] * scr[(i * 3 + 2) * keep + k] : mk<R>(0, 0);
+    }
+    for (int j = n - 3; j >= 0; --j) {
+      const cpx<R>* v = Hv + (int64_t)j * n;
+      cpx<R> dot = mk<R>(0, 0);
+#pragma unroll
+      for (int a = 0; a < PER; ++a) {
+        const int i = lane + 32 * a;
+        if (i > j && i < n) cfmac(dot, v[i], y[a]);
+      }
+      dot.re = warp_sum(dot.re);
+      dot.im = warp_sum(dot.im);
+      dot = (R)2 * dot;
+#pragma unroll
+      for (int a = 0; a < PER; ++a) {
+        const int i = lane + 32 * a;
+        if (i > j && i < n) y[a] -= v[i] * dot;
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < PER; ++a) {
+      const int i = lane + 32 * a;
+      if (i < n) U[(int64_t)k * n + i] = y[a];
+    }
+  }
+}
+
+}  // namespace lemps

@@ -10,6 +10,8 @@
 #pragma once
 
 #include "common.cuh"
+#include "heev.cuh"
+#include "gemm.cuh"
 
 namespace lemps {
 
@@ -34,6 +36,8 @@ struct SimView {
   double* eps_tot;           // [B]
   double* disc_last;         // [B] discarded weight of the last split
   int32_t* status;           // [B]
+  int32_t* kept;             // [B] eigenpairs kept by the last eigensolve
+  double* trace;             // [B] trace of the last Gram matrix (FP64)
 };
 
 template <class R>
@@ -115,10 +119,11 @@ __device__ void householder_qr(cpx<R>* X, cpx<R>* V, cpx<R>* Qm, int m, int n, i
 // Move the centre from site k to k+1 (dir = +1, QR of A_k as (2 dl) x dr) or
 // to k-1 (dir = -1, LQ of A_k as dl x (2 dr)).
 template <class R>
-__global__ void k_move_center(SimView<R> s, int k, int dir) {
+__global__ void __launch_bounds__(kGemmThreads) k_move_center(SimView<R> s, int k, int dir) {
   const int64_t t = blockIdx.x;
   if (t >= s.B) return;
   __shared__ R red[32];
+  __shared__ GemmSmem<R> sm;
   int32_t* bd = s.bond + t * (s.n + 1);
   const int dl = bd[k], dr = bd[k + 1];
   const int capr = s.cap[k + 1];
@@ -138,13 +143,13 @@ __global__ void k_move_center(SimView<R> s, int k, int dir) {
     // A_{k+1} <- R A_{k+1}: A_{k+1} is dr x (2 d2), R is r x dr (upper part of X)
     const int d2 = bd[k + 2], cap2 = s.cap[k + 2];
     cpx<R>* B = site_ptr(s, k + 1, t);
-    for (int64_t e = threadIdx.x; e < (int64_t)r * 2 * d2; e += blockDim.x) {
-      int i = (int)(e / (2 * d2)), cc = (int)(e % (2 * d2));
-      int ss = cc / d2, b = cc % d2;
-      cpx<R> acc = mk<R>(0, 0);
-      for (int l = i; l < dr; ++l) cfma(acc, X[(int64_t)l * m + i], B[(int64_t)(l * 2 + ss) * cap2 + b]);
-      Tm[e] = acc;
-    }
+    cta_gemm<R, false, false>(
+        r, 2 * d2, dr, [&](int i, int l) { return l >= i ? X[(int64_t)l * m + i] : mk<R>(0, 0); },
+        [&](int l, int cc) {
+          const int ss = cc / d2, b = cc - ss * d2;
+          return B[(int64_t)(l * 2 + ss) * cap2 + b];
+        },
+        [&](int i, int cc, cpx<R> v) { Tm[(int64_t)i * 2 * d2 + cc] = v; }, sm);
     __syncthreads();
     for (int64_t e = threadIdx.x; e < (int64_t)r * 2 * d2; e += blockDim.x) {
       int i = (int)(e / (2 * d2)), cc = (int)(e % (2 * d2));
@@ -171,12 +176,10 @@ __global__ void k_move_center(SimView<R> s, int k, int dir) {
     // A_{k-1} <- A_{k-1} L: A_{k-1} is (2 d0) x dl, result (2 d0) x r.
     const int d0 = bd[k - 1], cap1 = s.cap[k];
     cpx<R>* P = site_ptr(s, k - 1, t);
-    for (int64_t e = threadIdx.x; e < (int64_t)2 * d0 * r; e += blockDim.x) {
-      int row = (int)(e / r), j = (int)(e % r);
-      cpx<R> acc = mk<R>(0, 0);
-      for (int l = j; l < dl; ++l) cfma(acc, P[(int64_t)row * cap1 + l], conj(X[(int64_t)l * m + j]));
-      Tm[e] = acc;
-    }
+    cta_gemm<R, true, false>(
+        2 * d0, r, dl, [&](int row, int l) { return P[(int64_t)row * cap1 + l]; },
+        [&](int l, int j) { return l >= j ? conj(X[(int64_t)l * m + j]) : mk<R>(0, 0); },
+        [&](int row, int j, cpx<R> v) { Tm[(int64_t)row * r + j] = v; }, sm);
     __syncthreads();
     for (int64_t e = threadIdx.x; e < (int64_t)2 * d0 * r; e += blockDim.x) {
       int row = (int)(e / r), j = (int)(e % r);
@@ -197,39 +200,42 @@ __global__ void k_move_center(SimView<R> s, int k, int dir) {
 // (2 dl) x (2 dr) row-major matrix; rho12[(s1 s2), (t1 t2)] =
 // sum_{a,b} Theta[a,s1,s2,b] conj(Theta[a,t1,t2,b]) in FP64.
 template <class R>
-__global__ void k_contract(SimView<R> s, int q) {
+__global__ void __launch_bounds__(kGemmThreads) k_contract(SimView<R> s, int q) {
   const int64_t t = blockIdx.x;
   if (t >= s.B) return;
   __shared__ double red[32];
+  __shared__ GemmSmem<R> sm;
   const int32_t* bd = s.bond + t * (s.n + 1);
   const int dl = bd[q], dm = bd[q + 1], dr = bd[q + 2];
   const int capm = s.cap[q + 1], capr = s.cap[q + 2];
   const cpx<R>* A = site_ptr(s, q, t);
   const cpx<R>* B = site_ptr(s, q + 1, t);
   cpx<R>* th = s.ws0 + t * s.ws_stride;
+  const int64_t ld = 2 * dr;
+  cta_gemm<R, true, false>(
+      2 * dl, 2 * dr, dm, [&](int i, int k) { return A[(int64_t)i * capm + k]; },
+      [&](int k, int j) {
+        const int s2 = j / dr, b = j - s2 * dr;
+        return B[(int64_t)(2 * k + s2) * capr + b];
+      },
+      [&](int i, int j, cpx<R> v) { th[(int64_t)i * ld + j] = v; }, sm);
+  __syncthreads();
   double acc[16][2];
 #pragma unroll
   for (int i = 0; i < 16; ++i) acc[i][0] = acc[i][1] = 0.0;
   for (int e = threadIdx.x; e < dl * dr; e += blockDim.x) {
     const int a = e / dr, b = e % dr;
-    cpx<R> v[4] = {mk<R>(0, 0), mk<R>(0, 0), mk<R>(0, 0), mk<R>(0, 0)};
-    for (int m = 0; m < dm; ++m) {
-      cpx<R> a0 = A[(int64_t)(2 * a) * capm + m], a1 = A[(int64_t)(2 * a + 1) * capm + m];
-      cpx<R> b0 = B[(int64_t)(2 * m) * capr + b], b1 = B[(int64_t)(2 * m + 1) * capr + b];
-      cfma(v[0], a0, b0); cfma(v[1], a0, b1); cfma(v[2], a1, b0); cfma(v[3], a1, b1);
-    }
-    const int64_t ld = 2 * dr;
-    th[(int64_t)(2 * a) * ld + b] = v[0];
-    th[(int64_t)(2 * a) * ld + dr + b] = v[1];
-    th[(int64_t)(2 * a + 1) * ld + b] = v[2];
-    th[(int64_t)(2 * a + 1) * ld + dr + b] = v[3];
+    zd v[4];
+    v[0] = cast<double>(th[(int64_t)(2 * a) * ld + b]);
+    v[1] = cast<double>(th[(int64_t)(2 * a) * ld + dr + b]);
+    v[2] = cast<double>(th[(int64_t)(2 * a + 1) * ld + b]);
+    v[3] = cast<double>(th[(int64_t)(2 * a + 1) * ld + dr + b]);
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
-        zd vi = cast<double>(v[i]), vj = cast<double>(v[j]);
-        acc[i * 4 + j][0] += vi.re * vj.re + vi.im * vj.im;
-        acc[i * 4 + j][1] += vi.im * vj.re - vi.re * vj.im;
+        acc[i * 4 + j][0] += v[i].re * v[j].re + v[i].im * v[j].im;
+        acc[i * 4 + j][1] += v[i].im * v[j].re - v[i].re * v[j].im;
       }
   }
   for (int i = 0; i < 16; ++i) {
@@ -243,9 +249,10 @@ __global__ void k_contract(SimView<R> s, int q) {
 // side = 0: left Gram  G = Theta Theta^dagger (2dl x 2dl)
 // side = 1: right Gram G = Theta^dagger Theta (2dr x 2dr)
 template <class R>
-__global__ void k_apply_gram(SimView<R> s, int q, int side) {
+__global__ void __launch_bounds__(kGemmThreads) k_apply_gram(SimView<R> s, int q, int side) {
   const int64_t t = blockIdx.x;
   if (t >= s.B) return;
+  __shared__ GemmSmem<R> sm;
   const int32_t* bd = s.bond + t * (s.n + 1);
   const int dl = bd[q], dr = bd[q + 2];
   cpx<R>* th = s.ws0 + t * s.ws_stride;
@@ -273,29 +280,24 @@ __global__ void k_apply_gram(SimView<R> s, int q, int side) {
     th[(int64_t)(2 * a + 1) * ld + dr + b] = cast<R>(w[3]);
   }
   __syncthreads();
-  const int nr = 2 * dl, nc = 2 * dr;
-  const int ng = side == 0 ? nr : nc;
-  for (int e = threadIdx.x; e < ng * ng; e += blockDim.x) {
-    const int i = e / ng, j = e % ng;
-    if (j < i) continue;
-    cpx<R> acc = mk<R>(0, 0);
-    if (side == 0) {
-      for (int c = 0; c < nc; ++c) cfma(acc, th[(int64_t)i * ld + c], conj(th[(int64_t)j * ld + c]));
-    } else {
-      for (int r = 0; r < nr; ++r) cfmac(acc, th[(int64_t)r * ld + i], th[(int64_t)r * ld + j]);
+  const int ng = side == 0 ? 2 * dl : 2 * dr;
+  auto st = [&](int i, int j, cpx<R> v) {
+    if (j >= i) {
+      G[(int64_t)i * ng + j] = v;
+      G[(int64_t)j * ng + i] = conj(v);
     }
-    G[(int64_t)i * ng + j] = acc;
-    G[(int64_t)j * ng + i] = conj(acc);
+  };
+  if (side == 0) {
+    cta_gemm<R, true, true>(
+        ng, ng, 2 * dr, [&](int i, int k) { return th[(int64_t)i * ld + k]; },
+        [&](int k, int j) { return conj(th[(int64_t)j * ld + k]); }, st, sm, true);
+  } else {
+    cta_gemm<R, false, false>(
+        ng, ng, 2 * dl, [&](int i, int k) { return conj(th[(int64_t)k * ld + i]); },
+        [&](int k, int j) { return th[(int64_t)k * ld + j]; }, st, sm, true);
   }
 }
 
-// ---- Hermitian eigensolver: cyclic parallel two-sided Jacobi ----------------
-// Diagonalizes G (ng x ng row-major, in ws1) in place; eigenvectors
-// accumulate as columns of V (ws2, row-major).  Pairs follow a round-robin
-// tournament so each round's ng/2 rotations are disjoint; every round applies
-// all rotations to G through 2x2 blocks, so G and V make one pass per round.
-// Eigenvalues are written to evals sorted descending together with a
-// permutation perm (int stored in ws3 reinterpret).
 // Size of the Gram matrix: mode 0: 2 bond[k] (left Gram of the pair at k),
 // mode 1: 2 bond[k+2] (right Gram), mode 2: bond[k+1] (site Gram of A_k).
 __device__ __forceinline__ int gram_size(const int32_t* bd, int k, int mode) {
@@ -303,198 +305,109 @@ __device__ __forceinline__ int gram_size(const int32_t* bd, int k, int mode) {
 }
 
 template <class R>
-__global__ void k_jacobi(SimView<R> s, int q, int mode, int max_sweeps, R tol) {
-  const int64_t t = blockIdx.x;
-  if (t >= s.B) return;
-  const int32_t* bd = s.bond + t * (s.n + 1);
-  const int ng = gram_size(bd, q, mode);
-  cpx<R>* G = s.ws1 + t * s.ws_stride;
-  cpx<R>* V = s.ws2 + t * s.ws_stride;
-  __shared__ int pos[256];
-  __shared__ R rc[128], rs[128];
-  __shared__ cpx<R> rph[128];   // e^{-i phi} of each pair
-  __shared__ R red[32];
-  for (int e = threadIdx.x; e < ng * ng; e += blockDim.x) {
-    int i = e / ng, j = e % ng;
-    V[e] = mk<R>(i == j ? 1 : 0, 0);
-  }
-  R fro = 0;
-  for (int e = threadIdx.x; e < ng * ng; e += blockDim.x) fro += norm2(G[e]);
-  fro = block_sum(fro, red);
-  // Round robin needs an even count: an odd size gets a dummy index ng that
-  // never rotates.
-  const int np2 = ng + (ng & 1);
-  const int half = np2 / 2;
-  bool converged = (ng <= 1);
-  for (int sweep = 0; sweep < max_sweeps && !converged; ++sweep) {
-    for (int i = threadIdx.x; i < np2; i += blockDim.x) pos[i] = i;
-    __syncthreads();
-    for (int round = 0; round < np2 - 1; ++round) {
-      // rotation parameters for pair k: (pos[k], pos[np2-1-k])
-      for (int k = threadIdx.x; k < half; k += blockDim.x) {
-        int p = pos[k], qq = pos[np2 - 1 - k];
-        if (p > qq) { int tmp = p; p = qq; qq = tmp; }
-        R c = 1, sn = 0;
-        cpx<R> e = mk<R>(1, 0);
-        if (qq < ng) {
-          cpx<R> g = G[(int64_t)p * ng + qq];
-          R gn = sqrt(norm2(g));
-          R app = G[(int64_t)p * ng + p].re, aqq = G[(int64_t)qq * ng + qq].re;
-          if (gn > tol * sqrt(fabs(app * aqq)) && gn > (R)1e-300) {
-            R zeta = (aqq - app) / (2 * gn);
-            R tt = (zeta >= 0 ? (R)1 : (R)-1) / (fabs(zeta) + sqrt((R)1 + zeta * zeta));
-            c = (R)1 / sqrt((R)1 + tt * tt);
-            sn = c * tt;
-            e = mk<R>(g.re / gn, -g.im / gn);
-          }
-        }
-        rc[k] = c; rs[k] = sn; rph[k] = e;
-      }
-      __syncthreads();
-      // 2x2 block update of G: rows (p_i, q_i) x cols (p_j, q_j); the dummy
-      // index only ever pairs with an identity rotation and is skipped.
-      for (int e = threadIdx.x; e < half * half; e += blockDim.x) {
-        const int bi = e / half, bj = e % half;
-        int pi = pos[bi], qi = pos[np2 - 1 - bi];
-        if (pi > qi) { int tmp = pi; pi = qi; qi = tmp; }
-        int pj = pos[bj], qj = pos[np2 - 1 - bj];
-        if (pj > qj) { int tmp = pj; pj = qj; qj = tmp; }
-        const bool vi = qi < ng, vj = qj < ng;
-        cpx<R> g00 = G[(int64_t)pi * ng + pj];
-        cpx<R> g01 = vj ? G[(int64_t)pi * ng + qj] : mk<R>(0, 0);
-        cpx<R> g10 = vi ? G[(int64_t)qi * ng + pj] : mk<R>(0, 0);
-        cpx<R> g11 = (vi && vj) ? G[(int64_t)qi * ng + qj] : mk<R>(0, 0);
-        // columns: [g_p, g_q] J_j, J = [[c, s], [-s e, c e]]
-        R cj = rc[bj], sj = rs[bj];
-        cpx<R> ej = rph[bj];
-        cpx<R> h00 = cj * g00 - sj * (ej * g01), h01 = sj * g00 + cj * (ej * g01);
-        cpx<R> h10 = cj * g10 - sj * (ej * g11), h11 = sj * g10 + cj * (ej * g11);
-        // rows: J_i^dagger [h_p; h_q], J^dagger = [[c, -s e*], [s, c e*]]
-        R ci = rc[bi], si = rs[bi];
-        cpx<R> eci = conj(rph[bi]);
-        G[(int64_t)pi * ng + pj] = ci * h00 - si * (eci * h10);
-        if (vj) G[(int64_t)pi * ng + qj] = ci * h01 - si * (eci * h11);
-        if (vi) G[(int64_t)qi * ng + pj] = si * h00 + ci * (eci * h10);
-        if (vi && vj) G[(int64_t)qi * ng + qj] = si * h01 + ci * (eci * h11);
-      }
-      // V <- V J (columns p, q of every row)
-      for (int e = threadIdx.x; e < ng * half; e += blockDim.x) {
-        const int row = e / half, k = e % half;
-        int p = pos[k], qq = pos[np2 - 1 - k];
-        if (p > qq) { int tmp = p; p = qq; qq = tmp; }
-        if (qq >= ng) continue;
-        cpx<R> vp = V[(int64_t)row * ng + p], vq = rph[k] * V[(int64_t)row * ng + qq];
-        V[(int64_t)row * ng + p] = rc[k] * vp - rs[k] * vq;
-        V[(int64_t)row * ng + qq] = rs[k] * vp + rc[k] * vq;
-      }
-      __syncthreads();
-      // rotate positions 1..np2-1 (round robin)
-      if (threadIdx.x == 0) {
-        int last = pos[np2 - 1];
-        for (int i = np2 - 1; i > 1; --i) pos[i] = pos[i - 1];
-        pos[1] = last;
-      }
-      __syncthreads();
-    }
-    R off = 0;
-    for (int e = threadIdx.x; e < ng * ng; e += blockDim.x) {
-      int i = e / ng, j = e % ng;
-      if (i != j) off += norm2(G[e]);
-    }
-    off = block_sum(off, red);
-    converged = (off <= tol * tol * fro);
-  }
-  if (!converged && threadIdx.x == 0 && ng > 1) atomicOr(s.status + t, (int32_t)TS_JACOBI);
-  // sort eigenvalues descending: rank of each
-  double* ev = s.evals + t * (2 * s.chi);
-  int* perm = reinterpret_cast<int*>(s.ws3 + t * s.ws_stride);
-  for (int i = threadIdx.x; i < ng; i += blockDim.x) {
-    R li = G[(int64_t)i * ng + i].re;
-    int rank = 0;
-    for (int j = 0; j < ng; ++j) {
-      R lj = G[(int64_t)j * ng + j].re;
-      if (lj > li || (lj == li && j < i)) ++rank;
-    }
-    ev[rank] = (double)li;
-    perm[rank] = i;
-  }
+HeevView<R> heev_view(const SimView<R>& s) {
+  HeevView<R> h;
+  h.ws1 = s.ws1; h.ws2 = s.ws2; h.ws3 = s.ws3; h.ws_stride = s.ws_stride;
+  h.evals = s.evals; h.kept = s.kept; h.trace = s.trace; h.bond = s.bond;
+  h.nq = s.n; h.chi = s.chi; h.B = s.B;
+  return h;
 }
 
 // ---- split and truncate ------------------------------------------------------
-// Keeps chi' = min(chi_max, #{l_k > cutoff * sum l}) eigenpairs.  side 0:
-// A_q <- U' (left-orthonormal), A_{q+1} <- U'^dagger Theta / sqrt(kept),
-// centre at q+1.  side 1: A_{q+1} <- V'^dagger, A_q <- Theta V' / sqrt(kept),
-// centre at q.
+// U (ws2, column-major, ng x keep) holds the kept eigenvectors of the Gram
+// matrix.  side 0 (left Gram, centre -> q+1):
+//   A_q = U (left-orthonormal), B = U^dagger Theta, R = Theta - U B,
+//   A_{q+1} = B / ||B||.
+// side 1 (right Gram, centre -> q):
+//   A_{q+1} = U^dagger (right-orthonormal), B = Theta U, R = Theta - B U^dagger,
+//   A_q = B / ||B||.
+// The discarded weight is eps = ||R||_F^2 / ||Theta||_F^2, accumulated in FP64
+// from the residual itself, which keeps it accurate in complex64 (a sum of
+// discarded eigenvalues would carry an error of ~ n eps_32).
 template <class R>
-__global__ void k_split(SimView<R> s, int q, int side, double cutoff) {
+__global__ void __launch_bounds__(kGemmThreads) k_split(SimView<R> s, int q, int side) {
   const int64_t t = blockIdx.x;
   if (t >= s.B) return;
-  __shared__ int s_keep;
-  __shared__ double s_norm;
+  __shared__ double redd[32];
+  __shared__ GemmSmem<R> sm;
   int32_t* bd = s.bond + t * (s.n + 1);
   const int dl = bd[q], dr = bd[q + 2];
   const int ng = side == 0 ? 2 * dl : 2 * dr;
-  const double* ev = s.evals + t * (2 * s.chi);
-  const int* perm = reinterpret_cast<const int*>(s.ws3 + t * s.ws_stride);
-  if (threadIdx.x == 0) {
-    double tot = 0.0;
-    for (int k = 0; k < ng; ++k) tot += fmax(ev[k], 0.0);
-    int keep = 0;
-    for (int k = 0; k < ng; ++k)
-      if (ev[k] > cutoff * tot) ++keep;
-    keep = min(keep, s.chi);
-    keep = min(keep, min(2 * dl, 2 * dr));
-    keep = max(keep, 1);
-    double kept = 0.0;
-    for (int k = 0; k < keep; ++k) kept += fmax(ev[k], 0.0);
-    double disc = (tot > 0.0) ? fmax(tot - kept, 0.0) / tot : 0.0;
-    if (!(tot > 0.0) || !isfinite(tot)) atomicOr(s.status + t, (int32_t)TS_NORM);
-    s.disc_last[t] = disc;
-    s.eps_layer[t] += disc;
-    s_keep = keep;
-    s_norm = (kept > 0.0) ? 1.0 / sqrt(kept) : 0.0;
-  }
-  __syncthreads();
-  const int keep = s_keep;
-  const R nrm = (R)s_norm;
+  const int keep = s.kept[t];
+  const double tot = s.trace[t];
   const cpx<R>* th = s.ws0 + t * s.ws_stride;
-  const cpx<R>* V = s.ws2 + t * s.ws_stride;
+  const cpx<R>* U = s.ws2 + t * s.ws_stride;
   const int64_t ld = 2 * dr;
   cpx<R>* A = site_ptr(s, q, t);
   cpx<R>* B = site_ptr(s, q + 1, t);
   const int capm = s.cap[q + 1], capr = s.cap[q + 2];
+  auto bslot = [&](int k, int j) -> cpx<R>& {
+    const int s2 = j / dr, b = j - s2 * dr;
+    return B[(int64_t)(k * 2 + s2) * capr + b];
+  };
+  double bn = 0.0, rn = 0.0;
   if (side == 0) {
-    // A_q[a][s1][k] = U[2a+s1][perm[k]]
     for (int e = threadIdx.x; e < 2 * dl * keep; e += blockDim.x) {
-      int row = e / keep, k = e % keep;
-      A[(int64_t)row * capm + k] = V[(int64_t)row * ng + perm[k]];
+      const int row = e / keep, k = e % keep;
+      A[(int64_t)row * capm + k] = U[(int64_t)k * ng + row];
     }
-    // A_{q+1}[k][s2][b] = nrm * sum_r conj(U[r][perm k]) Theta[r][s2 dr + b]
+    // B = U^dagger Theta  (keep x 2dr)
+    cta_gemm<R, true, false>(
+        keep, 2 * dr, 2 * dl, [&](int i, int k) { return conj(U[(int64_t)i * ng + k]); },
+        [&](int k, int j) { return th[(int64_t)k * ld + j]; },
+        [&](int i, int j, cpx<R> v) {
+          bslot(i, j) = v;
+          bn += (double)norm2(v);
+        },
+        sm);
+    __syncthreads();
+    // residual Theta - U B
+    cta_gemm<R, false, false>(
+        2 * dl, 2 * dr, keep, [&](int i, int k) { return U[(int64_t)k * ng + i]; },
+        [&](int k, int j) { return bslot(k, j); },
+        [&](int i, int j, cpx<R> v) { rn += (double)norm2(th[(int64_t)i * ld + j] - v); }, sm);
+  } else {
     for (int e = threadIdx.x; e < keep * 2 * dr; e += blockDim.x) {
-      int k = e / (2 * dr), c = e % (2 * dr);
-      int col = perm[k];
-      cpx<R> acc = mk<R>(0, 0);
-      for (int r = 0; r < 2 * dl; ++r) cfmac(acc, V[(int64_t)r * ng + col], th[(int64_t)r * ld + c]);
-      int s2 = c / dr, b = c % dr;
-      B[(int64_t)(k * 2 + s2) * capr + b] = nrm * acc;
+      const int k = e / (2 * dr), c = e % (2 * dr);
+      bslot(k, c) = conj(U[(int64_t)k * ng + c]);
+    }
+    // B = Theta U  (2dl x keep) into A_q
+    cta_gemm<R, true, true>(
+        2 * dl, keep, 2 * dr, [&](int i, int k) { return th[(int64_t)i * ld + k]; },
+        [&](int k, int j) { return U[(int64_t)j * ng + k]; },
+        [&](int i, int j, cpx<R> v) {
+          A[(int64_t)i * capm + j] = v;
+          bn += (double)norm2(v);
+        },
+        sm);
+    __syncthreads();
+    // residual Theta - B U^dagger
+    cta_gemm<R, true, false>(
+        2 * dl, 2 * dr, keep, [&](int i, int k) { return A[(int64_t)i * capm + k]; },
+        [&](int k, int j) { return conj(U[(int64_t)k * ng + j]); },
+        [&](int i, int j, cpx<R> v) { rn += (double)norm2(th[(int64_t)i * ld + j] - v); }, sm);
+  }
+  rn = block_sum(rn, redd);
+  bn = block_sum(bn, redd);
+  const double nrm = bn > 0.0 ? 1.0 / sqrt(bn) : 0.0;
+  if (side == 0) {
+    for (int e = threadIdx.x; e < keep * 2 * dr; e += blockDim.x) {
+      cpx<R>& p = bslot(e / (2 * dr), e % (2 * dr));
+      p = (R)nrm * p;
     }
   } else {
-    // A_{q+1}[k][s2][b] = conj(V[s2 dr + b][perm k])
-    for (int e = threadIdx.x; e < keep * 2 * dr; e += blockDim.x) {
-      int k = e / (2 * dr), c = e % (2 * dr);
-      int s2 = c / dr, b = c % dr;
-      B[(int64_t)(k * 2 + s2) * capr + b] = conj(V[(int64_t)c * ng + perm[k]]);
-    }
-    // A_q[a][s1][k] = nrm * sum_c Theta[2a+s1][c] V[c][perm k]
     for (int e = threadIdx.x; e < 2 * dl * keep; e += blockDim.x) {
-      int row = e / keep, k = e % keep;
-      int col = perm[k];
-      cpx<R> acc = mk<R>(0, 0);
-      for (int c = 0; c < 2 * dr; ++c) cfma(acc, th[(int64_t)row * ld + c], V[(int64_t)c * ng + col]);
-      A[(int64_t)row * capm + k] = nrm * acc;
+      cpx<R>* p = A + (int64_t)(e / keep) * capm + (e % keep);
+      *p = (R)nrm * *p;
     }
   }
-  if (threadIdx.x == 0) bd[q + 1] = keep;
+  if (threadIdx.x == 0) {
+    const double disc = (tot > 0.0) ? fmin(fmax(rn / tot, 0.0), 1.0) : 0.0;
+    if (!(tot > 0.0) || !isfinite(tot) || !isfinite(rn) || !(bn > 0.0)) atomicOr(s.status + t, (int32_t)TS_NORM);
+    s.disc_last[t] = disc;
+    s.eps_layer[t] += disc;
+    bd[q + 1] = keep;
+  }
 }
 
 // ---- layer bookkeeping: eps_tot += 4 sqrt(2 sum_k eps_k) (App. B) -------------

@@ -7,13 +7,14 @@
 namespace lemps {
 
 void launch_unravel_gate(const GateState& s, const LayerDev& L, cudaStream_t st) {
-  const unsigned grid = (unsigned)((s.B + 127) / 128);
-  k_unravel_gate<<<grid, 128, 0, st>>>(s, L);
+  // FP64-bound per-thread work: small CTAs spread the batch over every SM.
+  const unsigned grid = (unsigned)((s.B + 31) / 32);
+  k_unravel_gate<<<grid, 32, 0, st>>>(s, L);
 }
 
 void launch_unravel_batch(const zd* rho, const zd* kraus, int r, int64_t batch, zd* kout, double* e_av, cudaStream_t st) {
-  const unsigned grid = (unsigned)((batch + 127) / 128);
-  k_unravel_batch<<<grid, 128, 0, st>>>(rho, kraus, r, batch, kout, e_av);
+  const unsigned grid = (unsigned)((batch + 31) / 32);
+  k_unravel_batch<<<grid, 32, 0, st>>>(rho, kraus, r, batch, kout, e_av);
 }
 
 }  // namespace lemps

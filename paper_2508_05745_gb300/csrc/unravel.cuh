@@ -65,18 +65,16 @@ __device__ __forceinline__ void spin_flip(const zd* w, zd* out) {
 __device__ inline void jacobi_sym(double* a, double* v, double* w, int n) {
   for (int i = 0; i < n; ++i)
     for (int j = 0; j < n; ++j) v[i * n + j] = (i == j) ? 1.0 : 0.0;
+  double tot = 0.0;
+  for (int i = 0; i < n * n; ++i) tot += a[i] * a[i];
+  const double thresh = 1e-17 * sqrt(tot);  // rotate only |a_pq| above this
   for (int sweep = 0; sweep < 60; ++sweep) {
-    double off = 0.0, tot = 0.0;
-    for (int i = 0; i < n; ++i)
-      for (int j = 0; j < n; ++j) {
-        tot += a[i * n + j] * a[i * n + j];
-        if (i != j) off += a[i * n + j] * a[i * n + j];
-      }
-    if (off <= 1e-34 * tot || tot == 0.0) break;
+    bool rotated = false;
     for (int p = 0; p < n - 1; ++p)
       for (int q = p + 1; q < n; ++q) {
         double apq = a[p * n + q];
-        if (apq == 0.0) continue;
+        if (fabs(apq) <= thresh) continue;
+        rotated = true;
         double zeta = (a[q * n + q] - a[p * n + p]) / (2.0 * apq);
         double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
         double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
@@ -96,6 +94,7 @@ __device__ inline void jacobi_sym(double* a, double* v, double* w, int n) {
           v[k * n + q] = s * vkp + c * vkq;
         }
       }
+    if (!rotated) break;
   }
   for (int i = 0; i < n; ++i) w[i] = a[i * n + i];
   for (int i = 0; i < n - 1; ++i) {  // selection sort, descending
@@ -306,6 +305,8 @@ __device__ __noinline__ bool optimal_unraveling(const zd* rho, const zd* kin, in
   zd vphi[16];
   for (int i = 0; i < 4; ++i)
     for (int j = 0; j < 4; ++j) vphi[j * 4 + i] = mk(i == j ? 1.0 : 0.0, 0.0);
+  double fnorm2 = 0.0;
+  for (int i = 0; i < 16; ++i) fnorm2 += norm2(f[i]);
   for (int sweep = 0; sweep < 40; ++sweep) {
     bool rotated = false;
     for (int p = 0; p < 3; ++p)
@@ -318,7 +319,7 @@ __device__ __noinline__ bool optimal_unraveling(const zd* rho, const zd* kin, in
           cfmac(g, f[p * 4 + i], f[q * 4 + i]);
         }
         double gn = sqrt(norm2(g));
-        if (gn <= 1e-17 * sqrt(al * be) || gn == 0.0) continue;
+        if (gn <= 1e-16 * sqrt(al * be) || gn <= 1e-30 * fnorm2) continue;
         rotated = true;
         double zeta = (be - al) / (2.0 * gn);
         double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
