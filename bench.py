@@ -305,7 +305,7 @@ def main():
     prof = mixed["profile"]
     dom = max(prof.items(), key=lambda kv: kv[1][0])
     total_prof = sum(v[0] for v in prof.values())
-    rl = roofline(dom, mixed["profile_updates"], args)
+    rl = roofline(prof, mixed["profile_updates"], args)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -335,17 +335,46 @@ def gpu_launches(prof, steps, prof_updates, updates):
     return int(launches * steps)
 
 
-def roofline(dom, prof_updates, args):
-    name, (ms, cnt) = dom
-    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
-        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
-    sm_max = peaks.get("sm_max_mhz", 2070.0)
+# Algorithmic work per bond update at uniform bond dimension chi, in complex
+# multiply-adds (1 CMAC = 8 real flops): contraction (2chi x chi)(chi x 2chi);
+# Hermitian Gram of a 2chi x 2chi matrix (one triangle); eigensolve:
+# tridiagonalization (4/3) n^3 plus back-transformation n^2 chi with n = 2chi;
+# split: projection U^dagger Theta plus the residual GEMM; centre move:
+# Householder QR of 2chi x chi, Q formation and the triangular merge.
+CMAC_PER_UPDATE = {"contract": 4.0, "gram": 4.0, "eig": 32.0 / 3.0 + 4.0, "split": 8.0,
+                   "move": 2 * (4.0 - 2.0 / 3.0) + 1.0}
+
+
+def fp32_peak_tflops():
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    sm_max = 2070.0
+    if os.path.exists(peaks_path):
+        sm_max = json.load(open(peaks_path)).get("sm_max_mhz", sm_max)
     # FP32 SIMT peak from unit counts: 152 SMs x 128 FP32 lanes x 2 flop x clock
-    fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12
-    avg_s = ms / 1000.0 / max(cnt, 1)
-    return {"kernel": name, "bound": "alu", "achieved": None, "peak": fp32_peak, "unit": "TFLOP/s",
-            "frac": None, "traffic": None, "avg_launch_ms": avg_s * 1000.0,
-            "note": "peak derived from 152 SMs x 128 FP32 lanes x 2 x max SM clock"}
+    return 152 * 128 * 2 * sm_max * 1e6 / 1e12
+
+
+def roofline(prof, prof_updates, args, fp64=False):
+    """Per kernel kind: achieved TFLOP/s on the algorithmic work of one profiled
+    step (units = bond updates of that step, chi = chi_max) over the summed
+    CUDA-event time of its launches; the dominant kind is reported."""
+    chi = args.chi
+    peak = fp32_peak_tflops() / (64.0 if fp64 else 1.0)
+    rows = {}
+    for kind, (ms, cnt) in prof.items():
+        if kind not in CMAC_PER_UPDATE or ms <= 0:
+            continue
+        flops = CMAC_PER_UPDATE[kind] * 8.0 * chi ** 3 * prof_updates
+        ach = flops / (ms / 1000.0) / 1e12
+        rows[kind] = {"ms": ms, "launches": cnt, "avg_launch_ms": ms / max(cnt, 1), "achieved_tflops": ach,
+                      "frac": ach / peak}
+    dom = max(prof.items(), key=lambda kv: kv[1][0])[0]
+    r = rows.get(dom, {})
+    return {"kernel": dom, "bound": "alu", "achieved": r.get("achieved_tflops"), "peak": peak, "unit": "TFLOP/s",
+            "frac": r.get("frac"), "traffic": None, "avg_launch_ms": r.get("avg_launch_ms"),
+            "peak_note": "FP32 SIMT peak derived from 152 SMs x 128 lanes x 2 x max SM clock (MEASURED_PEAKS sm_max_mhz)",
+            "work_note": "algorithmic CMAC per bond update at chi_max: " + json.dumps(CMAC_PER_UPDATE),
+            "kernels": rows}
 
 
 def main_reference(args):

@@ -152,7 +152,14 @@ lemps_status check_cuda(lemps_sim* h, const char* where) {
 
 template <class R>
 void launch_move(lemps_sim* h, int k, int dir) {
-  h->timed(LEMPS_K_MOVE, [&] { k_move_center<R><<<(unsigned)h->B, kThreads, 0, h->stream>>>(h->view<R>(), k, dir); });
+  const size_t smem = sizeof(QrSmem<R>);
+  static bool attr = false;  // one opt-in per instantiation
+  if (!attr) {
+    cudaFuncSetAttribute(k_move_center<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr = true;
+  }
+  h->timed(LEMPS_K_MOVE,
+           [&] { k_move_center<R><<<(unsigned)h->B, kThreads, smem, h->stream>>>(h->view<R>(), k, dir); });
 }
 
 template <class R>

@@ -174,7 +174,9 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
   gu += 2 * eps * tnorm + pivmin;
   if (threadIdx.x == 0) {
     int cnt = (cutoff > 0.0) ? sturm_greater<R>(sd, se2, n, (R)(cutoff * s_tr), pivmin) : n;
-    int kp = min(cnt, min(keep_max, n));
+    // a two-site Gram matrix has rank <= min(2 d_l, 2 d_r)
+    const int rank_bound = (mode == 2) ? n : min(2 * bd[q], 2 * bd[q + 2]);
+    int kp = min(cnt, min(keep_max, min(n, rank_bound)));
     s_keep = max(kp, 1);
   }
   __syncthreads();

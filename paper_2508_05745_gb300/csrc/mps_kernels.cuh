@@ -59,60 +59,163 @@ __global__ void k_init_state(SimView<R> s) {
   }
 }
 
-// ---- Householder QR of a column-major m x n matrix X (ld = m) --------------
-// Reflectors v_j (length m, zero above j) are stored column-major in V.
-// On exit the upper triangle of X holds R.  Then Q (m x kq) is formed in Qm.
+// ---- blocked Householder QR of a column-major m x n matrix X (ld = m) --------
+// Panels of NB columns are factored in shared memory (one warp per column,
+// reflectors H = I - 2 v v^dagger with unit v); each panel's compact WY form
+// H_0 ... H_{pb-1} = I - V T V^dagger updates the trailing columns and, in a
+// backward pass, forms Q = H_0 ... H_{kmin-1} [I; 0] (m x kq) with tiled GEMMs.
+// On exit the upper triangle of X holds R; V (m x kmin) keeps the reflectors.
 template <class R>
-__device__ void householder_qr(cpx<R>* X, cpx<R>* V, cpx<R>* Qm, int m, int n, int kq, R* red) {
+struct QrSmem {
+  static constexpr int NB = (sizeof(R) == 8) ? 8 : 16;
+  static constexpr int MMAX = 256;
+  cpx<R> vs[NB * MMAX];   // panel reflectors, column-major (pm rows)
+  cpx<R> p[NB * MMAX];    // panel being factored
+  cpx<R> w[NB * 128];     // W = V^dagger X_trail (NB x nt)
+  cpx<R> tm[NB * NB];     // T (upper triangular), row-major
+  GemmSmem<R> g;
+  R red[32];
+};
+
+template <class R>
+__device__ void qr_build_t(QrSmem<R>& sm, int pm, int pb) {
+  constexpr int NB = QrSmem<R>::NB;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-  const int kmin = min(m, n);
-  for (int j = 0; j < kmin; ++j) {
-    // norm of X[j:m, j]
-    R part = 0;
-    for (int i = j + threadIdx.x; i < m; i += blockDim.x) part += norm2(X[(int64_t)j * m + i]);
-    R nrm2 = block_sum(part, red);
-    R nrm = sqrt(nrm2);
-    cpx<R> x0 = X[(int64_t)j * m + j];
-    R ax0 = sqrt(norm2(x0));
-    cpx<R> ph = (ax0 > 0) ? mk<R>(x0.re / ax0, x0.im / ax0) : mk<R>(1, 0);
-    cpx<R> alpha = mk<R>(-nrm * ph.re, -nrm * ph.im);
-    // v = x - alpha e_j ; ||v||^2 = nrm2 - 2 Re(conj(alpha) x0) + |alpha|^2
-    R vn2 = nrm2 + nrm2 + 2 * nrm * ax0;
-    R inv = (vn2 > 0) ? (R)1 / sqrt(vn2) : (R)0;
-    for (int i = threadIdx.x; i < m; i += blockDim.x) {
-      cpx<R> vi = mk<R>(0, 0);
-      if (i > j) vi = X[(int64_t)j * m + i] * inv;
-      else if (i == j) vi = (x0 - alpha) * inv;
-      V[(int64_t)j * m + i] = vi;
+  // dots D[a][b] = v_a^dagger v_b for a < b, into w (reused), then the recurrence
+  for (int pr = warp; pr < pb * pb; pr += nwarp) {
+    const int a = pr / pb, bb = pr % pb;
+    if (a >= bb) continue;
+    cpx<R> d = mk<R>(0, 0);
+    for (int i = lane; i < pm; i += 32) cfmac(d, sm.vs[a * pm + i], sm.vs[bb * pm + i]);
+    d.re = warp_sum(d.re);
+    d.im = warp_sum(d.im);
+    if (lane == 0) sm.w[a * NB + bb] = d;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < pb; ++i) {
+      for (int r = 0; r < i; ++r) {
+        cpx<R> acc = mk<R>(0, 0);
+        for (int c = r; c < i; ++c) cfma(acc, sm.tm[r * NB + c], sm.w[c * NB + i]);
+        sm.tm[r * NB + i] = (R)-2 * acc;
+      }
+      sm.tm[i * NB + i] = mk<R>(2, 0);
+      for (int r = i + 1; r < pb; ++r) sm.tm[r * NB + i] = mk<R>(0, 0);
+    }
+  }
+  __syncthreads();
+}
+
+// Q_sub (rows p0.., kq columns) <- (I - V T V^dagger) Q_sub, or with T^dagger
+// when adjoint (the factorization's trailing update on X).
+template <class R>
+__device__ void qr_apply_block(QrSmem<R>& sm, cpx<R>* Y, int ldy, int row0, int col0, int pm, int pb, int nc,
+                               bool adjoint) {
+  constexpr int NB = QrSmem<R>::NB;
+  for (int c0 = 0; c0 < nc; c0 += 128) {
+    const int ncc = min(128, nc - c0);
+    // W = V^dagger Y  (pb x ncc)
+    cta_gemm<R, false, false>(
+        pb, ncc, pm, [&](int a, int i) { return conj(sm.vs[a * pm + i]); },
+        [&](int i, int c) { return Y[(int64_t)(col0 + c0 + c) * ldy + row0 + i]; },
+        [&](int a, int c, cpx<R> v) { sm.w[a * 128 + c] = v; }, sm.g);
+    __syncthreads();
+    // W <- T W  or  T^dagger W  (in place by rows, top-down for T^dagger? use a copy)
+    for (int e = threadIdx.x; e < ncc; e += blockDim.x) {
+      cpx<R> col[NB];
+      for (int a = 0; a < pb; ++a) col[a] = sm.w[a * 128 + e];
+      for (int a = 0; a < pb; ++a) {
+        cpx<R> acc = mk<R>(0, 0);
+        for (int b = 0; b < pb; ++b) {
+          const cpx<R> tab = adjoint ? conj(sm.tm[b * NB + a]) : sm.tm[a * NB + b];
+          cfma(acc, tab, col[b]);
+        }
+        sm.w[a * 128 + e] = acc;
+      }
     }
     __syncthreads();
-    // apply H = I - 2 v v^dagger to columns j..n-1 (one warp per column)
-    for (int c = j + warp; c < n; c += nwarp) {
-      cpx<R> d = mk<R>(0, 0);
-      for (int i = j + lane; i < m; i += 32) cfmac(d, V[(int64_t)j * m + i], X[(int64_t)c * m + i]);
-      d.re = warp_sum(d.re);
-      d.im = warp_sum(d.im);
-      d = (R)2 * d;
-      for (int i = j + lane; i < m; i += 32) X[(int64_t)c * m + i] -= V[(int64_t)j * m + i] * d;
-    }
+    // Y -= V W
+    cta_gemm<R, false, false>(
+        pm, ncc, pb, [&](int i, int a) { return sm.vs[a * pm + i]; }, [&](int a, int c) { return sm.w[a * 128 + c]; },
+        [&](int i, int c, cpx<R> v) {
+          cpx<R>& y = Y[(int64_t)(col0 + c0 + c) * ldy + row0 + i];
+          y = y - v;
+        },
+        sm.g);
     __syncthreads();
   }
-  // Q = H_0 ... H_{kmin-1} [I; 0] (m x kq)
+}
+
+template <class R>
+__device__ void householder_qr(cpx<R>* X, cpx<R>* V, cpx<R>* Qm, int m, int n, int kq, QrSmem<R>& sm) {
+  constexpr int NB = QrSmem<R>::NB;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  const int kmin = min(m, n);
+  for (int p0 = 0; p0 < kmin; p0 += NB) {
+    const int pb = min(NB, kmin - p0), pm = m - p0;
+    for (int e = threadIdx.x; e < pb * pm; e += blockDim.x) {
+      const int jj = e / pm, i = e % pm;
+      sm.p[e] = X[(int64_t)(p0 + jj) * m + p0 + i];
+    }
+    __syncthreads();
+    for (int jj = 0; jj < pb; ++jj) {
+      R part = 0;
+      for (int i = jj + threadIdx.x; i < pm; i += blockDim.x) part += norm2(sm.p[jj * pm + i]);
+      R nrm2 = block_sum(part, sm.red);
+      R nrm = sqrt(nrm2);
+      cpx<R> x0 = sm.p[jj * pm + jj];
+      R ax0 = sqrt(norm2(x0));
+      cpx<R> ph = (ax0 > 0) ? mk<R>(x0.re / ax0, x0.im / ax0) : mk<R>(1, 0);
+      cpx<R> alpha = mk<R>(-nrm * ph.re, -nrm * ph.im);
+      R vn2 = nrm2 + nrm2 + 2 * nrm * ax0;
+      R inv = (vn2 > 0) ? (R)1 / sqrt(vn2) : (R)0;
+      for (int i = threadIdx.x; i < pm; i += blockDim.x) {
+        cpx<R> vi = mk<R>(0, 0);
+        if (i > jj) vi = sm.p[jj * pm + i] * inv;
+        else if (i == jj) vi = (x0 - alpha) * inv;
+        sm.vs[jj * pm + i] = vi;
+      }
+      __syncthreads();
+      for (int c = jj + warp; c < pb; c += nwarp) {
+        cpx<R> d = mk<R>(0, 0);
+        for (int i = jj + lane; i < pm; i += 32) cfmac(d, sm.vs[jj * pm + i], sm.p[c * pm + i]);
+        d.re = warp_sum(d.re);
+        d.im = warp_sum(d.im);
+        d = (R)2 * d;
+        for (int i = jj + lane; i < pm; i += 32) sm.p[c * pm + i] -= sm.vs[jj * pm + i] * d;
+      }
+      __syncthreads();
+    }
+    for (int e = threadIdx.x; e < pb * pm; e += blockDim.x) {
+      const int jj = e / pm, i = e % pm;
+      X[(int64_t)(p0 + jj) * m + p0 + i] = sm.p[e];
+    }
+    for (int e = threadIdx.x; e < pb * m; e += blockDim.x) {
+      const int jj = e / m, i = e % m;
+      V[(int64_t)(p0 + jj) * m + i] = (i >= p0) ? sm.vs[jj * pm + (i - p0)] : mk<R>(0, 0);
+    }
+    __syncthreads();
+    if (p0 + pb < n) {
+      qr_build_t(sm, pm, pb);
+      qr_apply_block(sm, X, m, p0, p0 + pb, pm, pb, n - p0 - pb, true);
+    }
+  }
+  // Q = H_0 ... H_{kmin-1} [I; 0]
   for (int64_t e = threadIdx.x; e < (int64_t)m * kq; e += blockDim.x) {
-    int c = (int)(e / m), i = (int)(e % m);
+    const int c = (int)(e / m), i = (int)(e % m);
     Qm[e] = mk<R>(i == c ? 1 : 0, 0);
   }
   __syncthreads();
-  for (int j = kmin - 1; j >= 0; --j) {
-    for (int c = warp; c < kq; c += nwarp) {
-      cpx<R> d = mk<R>(0, 0);
-      for (int i = j + lane; i < m; i += 32) cfmac(d, V[(int64_t)j * m + i], Qm[(int64_t)c * m + i]);
-      d.re = warp_sum(d.re);
-      d.im = warp_sum(d.im);
-      d = (R)2 * d;
-      for (int i = j + lane; i < m; i += 32) Qm[(int64_t)c * m + i] -= V[(int64_t)j * m + i] * d;
+  const int npanel = (kmin + NB - 1) / NB;
+  for (int pi = npanel - 1; pi >= 0; --pi) {
+    const int p0 = pi * NB, pb = min(NB, kmin - p0), pm = m - p0;
+    for (int e = threadIdx.x; e < pb * pm; e += blockDim.x) {
+      const int jj = e / pm, i = e % pm;
+      sm.vs[e] = V[(int64_t)(p0 + jj) * m + p0 + i];
     }
     __syncthreads();
+    qr_build_t(sm, pm, pb);
+    qr_apply_block(sm, Qm, m, p0, 0, pm, pb, kq, false);
   }
 }
 
@@ -122,8 +225,9 @@ template <class R>
 __global__ void __launch_bounds__(kGemmThreads) k_move_center(SimView<R> s, int k, int dir) {
   const int64_t t = blockIdx.x;
   if (t >= s.B) return;
-  __shared__ R red[32];
-  __shared__ GemmSmem<R> sm;
+  extern __shared__ __align__(16) unsigned char move_smem[];
+  QrSmem<R>& qs = *reinterpret_cast<QrSmem<R>*>(move_smem);
+  GemmSmem<R>& sm = qs.g;
   int32_t* bd = s.bond + t * (s.n + 1);
   const int dl = bd[k], dr = bd[k + 1];
   const int capr = s.cap[k + 1];
@@ -139,7 +243,7 @@ __global__ void __launch_bounds__(kGemmThreads) k_move_center(SimView<R> s, int 
       X[e] = A[(int64_t)i * capr + c];
     }
     __syncthreads();
-    householder_qr(X, V, Qm, m, n, r, red);
+    householder_qr(X, V, Qm, m, n, r, qs);
     // A_{k+1} <- R A_{k+1}: A_{k+1} is dr x (2 d2), R is r x dr (upper part of X)
     const int d2 = bd[k + 2], cap2 = s.cap[k + 2];
     cpx<R>* B = site_ptr(s, k + 1, t);
@@ -171,7 +275,7 @@ __global__ void __launch_bounds__(kGemmThreads) k_move_center(SimView<R> s, int 
       X[e] = conj(A[(int64_t)(c * 2 + ss) * capr + b]);
     }
     __syncthreads();
-    householder_qr(X, V, Qm, m, n, r, red);
+    householder_qr(X, V, Qm, m, n, r, qs);
     // A_k = L Q with L = R'^dagger (dl x r), Q = Q'^dagger (r x 2dr).
     // A_{k-1} <- A_{k-1} L: A_{k-1} is (2 d0) x dl, result (2 d0) x r.
     const int d0 = bd[k - 1], cap1 = s.cap[k];
@@ -402,7 +506,9 @@ __global__ void __launch_bounds__(kGemmThreads) k_split(SimView<R> s, int q, int
     }
   }
   if (threadIdx.x == 0) {
-    const double disc = (tot > 0.0) ? fmin(fmax(rn / tot, 0.0), 1.0) : 0.0;
+    // keeping the full rank min(2 dl, 2 dr) discards nothing: eps = 0 exactly
+    const bool full = keep >= min(2 * dl, 2 * dr);
+    const double disc = (tot > 0.0 && !full) ? fmin(fmax(rn / tot, 0.0), 1.0) : 0.0;
     if (!(tot > 0.0) || !isfinite(tot) || !isfinite(rn) || !(bn > 0.0)) atomicOr(s.status + t, (int32_t)TS_NORM);
     s.disc_last[t] = disc;
     s.eps_layer[t] += disc;
