@@ -52,7 +52,17 @@ def parse():
     ap.add_argument("--cpu-sample-s", type=float, default=20.0, help="target CPU seconds for the oracle baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--sizes", default="24,48,64", help="system sizes to include (profiling cases use one)")
     return ap.parse_args()
+
+
+T_START = time.time()
+
+
+def log(msg):
+    sys.stderr.write(f"[bench {time.time() - T_START:7.1f}s] {msg}\n")
+    sys.stderr.flush()
 
 
 # --- clocks -----------------------------------------------------------------------
@@ -200,7 +210,6 @@ def observable_error(res_m, res_d, bf_by_n):
 # --- CPU oracle baseline -------------------------------------------------------------------
 
 def _oracle_worker(job):
-    os.environ.setdefault("OMP_NUM_THREADS", "1")
     n, traj, seed, chi, depth, pre, budget_s = job
     from oracle import trajectories as T
     from paper_2508_05745_gb300 import inputs as I
@@ -231,10 +240,21 @@ def _oracle_worker(job):
 def cpu_baseline(args, pre_layers, budget_s):
     import multiprocessing as mp
     cores = os.cpu_count() or 1
+    # one BLAS thread per worker: set before the spawned children import numpy
+    saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in saved:
+        os.environ[k] = "1"
     jobs = [(48, t, args.seed, args.chi, args.depth, pre_layers, budget_s) for t in range(cores)]
     ctx = mp.get_context("spawn")
-    with ctx.Pool(cores) as pool:
-        res = pool.map(_oracle_worker, jobs)
+    try:
+        with ctx.Pool(cores) as pool:
+            res = pool.map(_oracle_worker, jobs)
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
     upd = sum(r[0] for r in res)
     secs = sum(r[1] for r in res)
     rate = upd / (secs / cores) if secs > 0 else 0.0
@@ -265,11 +285,17 @@ def main():
     # replicas: rank r takes trajectories [r*B, (r+1)*B) of the global sample
     per_rank = args.traj
     labels = w["n_of_traj"][rank * per_rank:(rank + 1) * per_rank]
-    sizes = {int(n): int(np.sum(labels == n)) for n in (24, 48, 64)}
+    want = [int(x) for x in args.sizes.split(",")]
+    if len(want) == 3:
+        sizes = {int(n): int(np.sum(labels == n)) for n in (24, 48, 64)}
+    else:
+        sizes = {n: per_rank // len(want) for n in want}
+    log(f"sizes {sizes}")
     clocks = ClockSampler(local)
     clocks.start()
     mixed = run_arm(L, torch, w, sizes, "mixed", args, args.pre_layers, args.warmup, args.steps,
-                    profile_step=True, e2e=True)
+                    profile_step=True, e2e=not args.no_e2e)
+    log(f"mixed arm: {mixed['updates']} updates in {mixed['ms']:.1f} ms")
     clk = clocks.stop()
     ms = mixed["ms"]
     if world > 1:
@@ -291,8 +317,8 @@ def main():
         bf = {n: min(b, max(1, args.fp64_traj * b // max(1, sum(sizes.values())))) for n, b in sizes.items() if b}
         d = run_arm(L, torch, w, bf, "fp64", args, args.pre_layers, args.warmup, args.steps)
         fp64 = d["updates"] / (d["ms"] / 1000.0)
+        log(f"fp64 arm: {d['updates']} updates in {d['ms']:.1f} ms")
         # bring the mixed sims to the same depth as the FP64 sims and compare
-        res_m = {n: s.measure() for n, s in mixed["sims"].items()} if False else None
         res_d = {}
         for n, s in d["sims"].items():
             res_d[n] = s.measure()
@@ -300,6 +326,7 @@ def main():
         mm = run_arm(L, torch, w, bf, "mixed", args, args.pre_layers, args.warmup, args.steps)
         res_m = {n: s.measure() for n, s in mm["sims"].items()}
         obs_err = observable_error(res_m, res_d, bf)
+        log("observable error done")
         for s in list(d["sims"].values()) + list(mm["sims"].values()):
             s.destroy()
     prof = mixed["profile"]
@@ -324,6 +351,7 @@ def main():
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args, args.pre_layers, args.cpu_sample_s)
+        log("cpu baseline done")
     for s in mixed["sims"].values():
         s.destroy()
     if rank == 0:

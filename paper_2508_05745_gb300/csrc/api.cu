@@ -175,9 +175,15 @@ constexpr int kHeevThreads = 512;
 // eigenvalue (vectors = 0, cutoff = 0).
 template <class R>
 void launch_heev(lemps_sim* h, int q, int mode, double cutoff, int keep_max, int vectors) {
+  const size_t smem = HeevSmem<R>::kBytes;
+  static bool attr = false;  // one opt-in per instantiation
+  if (!attr) {
+    cudaFuncSetAttribute(k_heev<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr = true;
+  }
   h->timed(LEMPS_K_EIG, [&] {
-    k_heev<R><<<(unsigned)h->B, kHeevThreads, 0, h->stream>>>(heev_view(h->view<R>()), q, mode, cutoff, keep_max,
-                                                               vectors);
+    k_heev<R><<<(unsigned)h->B, kHeevThreads, smem, h->stream>>>(heev_view(h->view<R>()), q, mode, cutoff,
+                                                                  keep_max, vectors);
   });
 }
 

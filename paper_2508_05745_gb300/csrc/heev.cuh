@@ -55,6 +55,16 @@ __device__ __forceinline__ float start_entry(int k, int i) {
   return 0.5f + (float)(h >> 8) * (1.0f / 16777216.0f);
 }
 
+// Shared-memory budget of k_heev (dynamic): a packed lower triangle of the
+// trailing block once it fits, later the eigenvector block for Gram-Schmidt.
+template <class R>
+struct HeevSmem {
+  static constexpr int kBytes = 196 * 1024;
+  static constexpr int kCap = kBytes / (int)sizeof(cpx<R>);   // complex entries
+};
+
+__device__ __forceinline__ int pidx(int r, int c) { return r * (r + 1) / 2 + c; }
+
 // mode / q select the matrix size as in gram_size(); want_vectors = 0 returns
 // eigenvalues only (all n of them when cutoff = 0).
 template <class R>
@@ -68,6 +78,8 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
   cpx<R>* Hv = s.ws3 + t * s.ws_stride;
   cpx<R>* U = s.ws2 + t * s.ws_stride;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  extern __shared__ __align__(16) unsigned char heev_smem[];
+  cpx<R>* Lp = reinterpret_cast<cpx<R>*>(heev_smem);   // packed lower triangle (trailing block)
 
   __shared__ R sd[256], se[256], se2[256];   // real tridiagonal: diagonal, |offdiag|, offdiag^2
   __shared__ cpx<R> sph[256];                // phases delta_i (T_real = D^dagger T_c D)
@@ -85,7 +97,12 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
   if (threadIdx.x == 0) s_tr = trp;
 
   // ---- phase 1: tridiagonalization ------------------------------------------
-  for (int j = 0; j + 2 < n; ++j) {
+  // Steps whose trailing block does not fit in shared memory work on the full
+  // matrix in global memory; from j0 on, the lower triangle of G[j0:, j0:] is
+  // packed into shared memory and the remaining steps stay on chip.
+  int j0 = 0;
+  while ((n - j0) * (n - j0 + 1) / 2 > HeevSmem<R>::kCap) ++j0;
+  for (int j = 0; j < j0 && j + 2 < n; ++j) {
     const int m = n - j - 1;
     R part = 0;
     for (int i = threadIdx.x; i < m; i += blockDim.x) {
@@ -93,7 +110,7 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
       sv[i] = x;
       if (i > 0) part += norm2(x);
     }
-    R sig = block_sum(part, red);  // syncs; sv visible
+    R sig = block_sum(part, red);
     cpx<R> x0 = sv[0];
     R ax0 = sqrt(norm2(x0));
     R nrm = sqrt(sig + ax0 * ax0);
@@ -102,7 +119,7 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
     if (reflect) {
       cpx<R> ph = (ax0 > 0) ? mk<R>(x0.re / ax0, x0.im / ax0) : mk<R>(1, 0);
       alpha = mk<R>(-nrm * ph.re, -nrm * ph.im);
-      R inv = (R)1 / sqrt(sig + (ax0 + nrm) * (ax0 + nrm));   // ||x - alpha e1||
+      R inv = (R)1 / sqrt(sig + (ax0 + nrm) * (ax0 + nrm));
       __syncthreads();
       for (int i = threadIdx.x; i < m; i += blockDim.x) sv[i] = (i == 0) ? (x0 - alpha) * inv : sv[i] * inv;
     }
@@ -114,7 +131,6 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
     for (int i = threadIdx.x; i < n; i += blockDim.x)
       Hv[(int64_t)j * n + i] = (i > j && reflect) ? sv[i - j - 1] : mk<R>(0, 0);
     if (!reflect) continue;
-    // y = G_sub v (warp per row)
     for (int r = warp; r < m; r += nwarp) {
       const cpx<R>* row = G + (int64_t)(j + 1 + r) * n + (j + 1);
       cpx<R> acc = mk<R>(0, 0);
@@ -124,16 +140,11 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
       if (lane == 0) sw[r] = acc;
     }
     __syncthreads();
-    // s = v^dagger y (real), w = 2 y - 2 s v
     R sp = 0;
-    for (int i = threadIdx.x; i < m; i += blockDim.x) {
-      cpx<R> c = cdot(sv[i], sw[i]);
-      sp += c.re;
-    }
+    for (int i = threadIdx.x; i < m; i += blockDim.x) sp += cdot(sv[i], sw[i]).re;
     R ss = block_sum(sp, red);
     for (int i = threadIdx.x; i < m; i += blockDim.x) sw[i] = (R)2 * sw[i] - ((R)2 * ss) * sv[i];
     __syncthreads();
-    // G_sub -= v w^dagger + w v^dagger
     for (int64_t e = threadIdx.x; e < (int64_t)m * m; e += blockDim.x) {
       const int r = (int)(e / m), c = (int)(e % m);
       cpx<R>* g = G + (int64_t)(j + 1 + r) * n + (j + 1 + c);
@@ -141,20 +152,87 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
     }
     __syncthreads();
   }
-  if (threadIdx.x == 0) {
-    if (n >= 2) {
-      sd[n - 2] = G[(int64_t)(n - 2) * n + (n - 2)].re;
-      sec[n - 2] = G[(int64_t)(n - 1) * n + (n - 2)];
+  // pack the lower triangle of the trailing block G[j0:, j0:]
+  const int M0 = n - j0;
+  for (int r = warp; r < M0; r += nwarp)
+    for (int c = lane; c <= r; c += 32) Lp[pidx(r, c)] = G[(int64_t)(j0 + r) * n + (j0 + c)];
+  __syncthreads();
+  for (int j = j0; j + 2 < n; ++j) {
+    const int jl = j - j0;     // local index of column j
+    const int m = n - j - 1;   // trailing size; local rows jl+1 .. M0-1
+    R part = 0;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+      cpx<R> x = Lp[pidx(jl + 1 + i, jl)];
+      sv[i] = x;
+      if (i > 0) part += norm2(x);
     }
-    sd[n - 1] = G[(int64_t)(n - 1) * n + (n - 1)].re;
+    R sig = block_sum(part, red);
+    cpx<R> x0 = sv[0];
+    R ax0 = sqrt(norm2(x0));
+    R nrm = sqrt(sig + ax0 * ax0);
+    const bool reflect = sig > (R)0;
+    cpx<R> alpha = x0;
+    if (reflect) {
+      cpx<R> ph = (ax0 > 0) ? mk<R>(x0.re / ax0, x0.im / ax0) : mk<R>(1, 0);
+      alpha = mk<R>(-nrm * ph.re, -nrm * ph.im);
+      R inv = (R)1 / sqrt(sig + (ax0 + nrm) * (ax0 + nrm));
+      __syncthreads();
+      for (int i = threadIdx.x; i < m; i += blockDim.x) sv[i] = (i == 0) ? (x0 - alpha) * inv : sv[i] * inv;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      sd[j] = Lp[pidx(jl, jl)].re;
+      sec[j] = alpha;
+    }
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+      Hv[(int64_t)j * n + i] = (i > j && reflect) ? sv[i - j - 1] : mk<R>(0, 0);
+    if (!reflect) continue;
+    // y = G_sub v, Hermitian from the lower triangle: rows (r >= c) then the
+    // strictly-upper part as conj of columns
+    for (int r = warp; r < m; r += nwarp) {
+      const cpx<R>* row = Lp + pidx(jl + 1 + r, jl + 1);
+      cpx<R> acc = mk<R>(0, 0);
+      for (int c = lane; c <= r; c += 32) cfma(acc, row[c], sv[c]);
+      acc.re = warp_sum(acc.re);
+      acc.im = warp_sum(acc.im);
+      if (lane == 0) sw[r] = acc;
+    }
+    __syncthreads();
+    for (int c = warp; c < m; c += nwarp) {
+      cpx<R> acc = mk<R>(0, 0);
+      for (int r = c + 1 + lane; r < m; r += 32) cfmac(acc, Lp[pidx(jl + 1 + r, jl + 1 + c)], sv[r]);
+      acc.re = warp_sum(acc.re);
+      acc.im = warp_sum(acc.im);
+      if (lane == 0) sw[c] += acc;
+    }
+    __syncthreads();
+    R sp = 0;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) sp += cdot(sv[i], sw[i]).re;
+    R ss = block_sum(sp, red);
+    for (int i = threadIdx.x; i < m; i += blockDim.x) sw[i] = (R)2 * sw[i] - ((R)2 * ss) * sv[i];
+    __syncthreads();
+    for (int r = warp; r < m; r += nwarp) {
+      cpx<R>* row = Lp + pidx(jl + 1 + r, jl + 1);
+      const cpx<R> vr = sv[r], wr = sw[r];
+      for (int c = lane; c <= r; c += 32) row[c] = row[c] - vr * conj(sw[c]) - wr * conj(sv[c]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const int a = n - 2 - j0, b = n - 1 - j0;   // local indices of the last two rows
+    if (n >= 2) {
+      sd[n - 2] = Lp[pidx(a, a)].re;
+      sec[n - 2] = Lp[pidx(b, a)];
+    }
+    sd[n - 1] = Lp[pidx(b, b)].re;
     // phase normalization: delta_{j+1} = delta_j e_j / |e_j|
     cpx<R> dl = mk<R>(1, 0);
     sph[0] = dl;
     for (int j = 0; j + 1 < n; ++j) {
-      R a = sqrt(norm2(sec[j]));
-      se[j] = a;
-      se2[j] = a * a;
-      if (a > 0) dl = dl * mk<R>(sec[j].re / a, sec[j].im / a);
+      R aa = sqrt(norm2(sec[j]));
+      se[j] = aa;
+      se2[j] = aa * aa;
+      if (aa > 0) dl = dl * mk<R>(sec[j].re / aa, sec[j].im / aa);
       sph[j + 1] = dl;
     }
   }
@@ -206,69 +284,68 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
   R* scr = reinterpret_cast<R*>(G);
   for (int k = threadIdx.x; k < keep; k += blockDim.x) {
     const R lam = (R)ev[k];
-    R* zz = scr;
-    // factor: dd_0 = d_0 - l; ll_i = e_i / dd_i; dd_{i+1} = d_{i+1} - l - ll_i e_i
     R dprev = sd[0] - lam;
     if (fabs(dprev) < pivmin) dprev = pivmin;
-    zz[(0 * 3 + 0) * keep + k] = dprev;
+    scr[(0 * 3 + 0) * keep + k] = dprev;
     for (int i = 0; i + 1 < n; ++i) {
       R li = se[i] / dprev;
-      zz[(i * 3 + 1) * keep + k] = li;
+      scr[(i * 3 + 1) * keep + k] = li;
       R dn = (sd[i + 1] - lam) - li * se[i];
       if (fabs(dn) < pivmin) dn = pivmin;
-      zz[((i + 1) * 3 + 0) * keep + k] = dn;
+      scr[((i + 1) * 3 + 0) * keep + k] = dn;
       dprev = dn;
     }
-    for (int i = 0; i < n; ++i) zz[(i * 3 + 2) * keep + k] = (R)start_entry(k, i);
-    for (int iter = 0; iter < 3; ++iter) {
-      // forward L y = b
-      R y = zz[(0 * 3 + 2) * keep + k];
-      zz[(0 * 3 + 2) * keep + k] = y;
+    for (int i = 0; i < n; ++i) scr[(i * 3 + 2) * keep + k] = (R)start_entry(k, i);
+    for (int iter = 0; iter < 2; ++iter) {
+      R y = scr[(0 * 3 + 2) * keep + k];
       for (int i = 1; i < n; ++i) {
-        y = zz[(i * 3 + 2) * keep + k] - zz[((i - 1) * 3 + 1) * keep + k] * y;
-        zz[(i * 3 + 2) * keep + k] = y;
+        y = scr[(i * 3 + 2) * keep + k] - scr[((i - 1) * 3 + 1) * keep + k] * y;
+        scr[(i * 3 + 2) * keep + k] = y;
       }
-      // diagonal, backward L^T z = D^{-1} y
-      R zn = zz[((n - 1) * 3 + 2) * keep + k] / zz[((n - 1) * 3 + 0) * keep + k];
-      zz[((n - 1) * 3 + 2) * keep + k] = zn;
+      R zn = scr[((n - 1) * 3 + 2) * keep + k] / scr[((n - 1) * 3 + 0) * keep + k];
+      scr[((n - 1) * 3 + 2) * keep + k] = zn;
       R amax = fabs(zn);
       for (int i = n - 2; i >= 0; --i) {
-        zn = zz[(i * 3 + 2) * keep + k] / zz[(i * 3 + 0) * keep + k] - zz[(i * 3 + 1) * keep + k] * zn;
-        zz[(i * 3 + 2) * keep + k] = zn;
+        zn = scr[(i * 3 + 2) * keep + k] / scr[(i * 3 + 0) * keep + k] - scr[(i * 3 + 1) * keep + k] * zn;
+        scr[(i * 3 + 2) * keep + k] = zn;
         amax = fmax(amax, fabs(zn));
       }
       R sc = (amax > 0) ? (R)1 / amax : (R)1;
-      for (int i = 0; i < n; ++i) zz[(i * 3 + 2) * keep + k] *= sc;
+      for (int i = 0; i < n; ++i) scr[(i * 3 + 2) * keep + k] *= sc;
     }
   }
   __syncthreads();
   // ---- phase 4: Gram-Schmidt (twice) in descending eigenvalue order ----------
-  // vectors are the columns z[i][k] = scr[(i*3+2)*keep + k]
+  // The vectors move to shared memory (vector-contiguous, Z[k * n + i]) when
+  // they fit, otherwise they stay in the global scratch.
+  const bool zsm = (int64_t)keep * n * (int64_t)sizeof(R) <= HeevSmem<R>::kBytes;
+  R* Zs = reinterpret_cast<R*>(heev_smem);
+  if (zsm)
+    for (int e = threadIdx.x; e < keep * n; e += blockDim.x) Zs[e] = scr[((e % n) * 3 + 2) * keep + e / n];
+  __syncthreads();
+  auto Z = [&](int k, int i) -> R& { return zsm ? Zs[k * n + i] : scr[(i * 3 + 2) * keep + k]; };
+  R* cbuf = reinterpret_cast<R*>(sw);
   for (int k = 0; k < keep; ++k) {
     for (int pass = 0; pass < 2; ++pass) {
-      // coefficients c_j = <z_j, z_k> for j < k into sw[] (real parts)
       for (int jj = warp; jj < k; jj += nwarp) {
         R acc = 0;
-        for (int i = lane; i < n; i += 32) acc += scr[(i * 3 + 2) * keep + jj] * scr[(i * 3 + 2) * keep + k];
+        for (int i = lane; i < n; i += 32) acc += Z(jj, i) * Z(k, i);
         acc = warp_sum(acc);
-        if (lane == 0) sw[jj].re = acc;
+        if (lane == 0) cbuf[jj] = acc;
       }
       __syncthreads();
       for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        R v = scr[(i * 3 + 2) * keep + k];
-        for (int jj = 0; jj < k; ++jj) v -= sw[jj].re * scr[(i * 3 + 2) * keep + jj];
-        scr[(i * 3 + 2) * keep + k] = v;
+        R v = Z(k, i);
+        for (int jj = 0; jj < k; ++jj) v -= cbuf[jj] * Z(jj, i);
+        Z(k, i) = v;
       }
       __syncthreads();
     }
     R part = 0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      R v = scr[(i * 3 + 2) * keep + k];
-      part += v * v;
-    }
+    for (int i = threadIdx.x; i < n; i += blockDim.x) part += Z(k, i) * Z(k, i);
     R nn = block_sum(part, red);
     R inv = nn > 0 ? (R)1 / sqrt(nn) : (R)0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) scr[(i * 3 + 2) * keep + k] *= inv;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) Z(k, i) *= inv;
     __syncthreads();
   }
   // ---- phase 5: back-transformation U = Q D z, one warp per column ------------
@@ -278,7 +355,7 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
 #pragma unroll
     for (int a = 0; a < PER; ++a) {
       const int i = lane + 32 * a;
-      y[a] = (i < n) ? sph[i] * scr[(i * 3 + 2) * keep + k] : mk<R>(0, 0);
+      y[a] = (i < n) ? sph[i] * Z(k, i) : mk<R>(0, 0);
     }
     for (int j = n - 3; j >= 0; --j) {
       const cpx<R>* v = Hv + (int64_t)j * n;
