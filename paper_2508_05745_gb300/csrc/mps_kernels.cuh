@@ -250,7 +250,7 @@ __global__ void __launch_bounds__(kGemmThreads) k_move_center(SimView<R> s, int 
     cta_gemm<R, false, false>(
         r, 2 * d2, dr, [&](int i, int l) { return l >= i ? X[(int64_t)l * m + i] : mk<R>(0, 0); },
         [&](int l, int cc) {
-          const int ss = cc / d2, b = cc - ss * d2;
+          const int ss = cc >= d2, b = cc - ss * d2;   // cc < 2 d2
           return B[(int64_t)(l * 2 + ss) * cap2 + b];
         },
         [&](int i, int cc, cpx<R> v) { Tm[(int64_t)i * 2 * d2 + cc] = v; }, sm);
@@ -319,7 +319,7 @@ __global__ void __launch_bounds__(kGemmThreads) k_contract(SimView<R> s, int q) 
   cta_gemm<R, true, false>(
       2 * dl, 2 * dr, dm, [&](int i, int k) { return A[(int64_t)i * capm + k]; },
       [&](int k, int j) {
-        const int s2 = j / dr, b = j - s2 * dr;
+        const int s2 = j >= dr, b = j - s2 * dr;   // j < 2 dr
         return B[(int64_t)(2 * k + s2) * capr + b];
       },
       [&](int i, int j, cpx<R> v) { th[(int64_t)i * ld + j] = v; }, sm);
@@ -446,7 +446,7 @@ __global__ void __launch_bounds__(kGemmThreads) k_split(SimView<R> s, int q, int
   cpx<R>* B = site_ptr(s, q + 1, t);
   const int capm = s.cap[q + 1], capr = s.cap[q + 2];
   auto bslot = [&](int k, int j) -> cpx<R>& {
-    const int s2 = j / dr, b = j - s2 * dr;
+    const int s2 = j >= dr, b = j - s2 * dr;   // j < 2 dr
     return B[(int64_t)(k * 2 + s2) * capr + b];
   };
   double bn = 0.0, rn = 0.0;
