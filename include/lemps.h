@@ -177,6 +177,23 @@ lemps_status unravel_grad(const void* theta, int32_t theta_fp64, int64_t batch, 
 lemps_status unravel_descend(const double* rho_a, const double* p, int64_t batch, int32_t steps,
                              double lr, double* h, double* cost_trace, void* stream);
 
+/* Allocation-free variant of unravel_grad (the paper has no counterpart; it
+ * is a service for callers that must not allocate device memory during a call:
+ * code whose device memory is fully owned by another allocator, or latency
+ * paths where cudaMalloc/cudaFree would synchronize the device).  Same
+ * arguments and results as unravel_grad with rho_out = NULL, but the per-call
+ * scratch (the reduced target states) lives in a static device array sized for
+ * at most 16384 problems (1 MiB), which every GPU that loads the library holds
+ * until the process exits.  batch > 16384 returns LEMPS_EINVAL.  The first call
+ * on a device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current, so make that first call before any stream capture.  All
+ * calls on one device share its copy of the array, which keeps the last call's
+ * contents: calls that overlap on the same GPU (e.g. on different streams) race
+ * and must be ordered by the caller.  No cudaMalloc, cudaFree or other
+ * allocating routine is called. */
+lemps_status unravel_grad_noalloc(const void* theta, int32_t theta_fp64, int64_t batch, int32_t chi,
+                                  const double* p, const double* h, double* cost, double* grad, void* stream);
+
 /* Per-kernel timing with CUDA events recorded on the handle's stream around
  * every launch made by apply_layer (enable = 1 starts a fresh record,
  * enable = 0 stops recording).  With ms and launches non-NULL the call

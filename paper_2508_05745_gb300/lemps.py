@@ -23,7 +23,8 @@ ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, c
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 
 EXPORTED = ["sim_create", "apply_layer", "unravel_opt", "sample_branch", "measure", "sim_export_mps",
-            "sim_sync", "sim_profile", "destroy", "unravel_grad", "unravel_descend", "lemps_last_error"]
+            "sim_sync", "sim_profile", "destroy", "unravel_grad", "unravel_descend", "unravel_grad_noalloc",
+            "lemps_last_error"]
 KERNEL_KINDS = ["move", "contract", "unravel", "gram", "eig", "split", "other"]
 
 
@@ -88,6 +89,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     lib.destroy.argtypes = [vp]
     lib.unravel_grad.argtypes = [vp, i32, i64, i32, vp, vp, vp, vp, vp, vp]
     lib.unravel_descend.argtypes = [vp, vp, i64, i32, ctypes.c_double, vp, vp, vp]
+    lib.unravel_grad_noalloc.argtypes = [vp, i32, i64, i32, vp, vp, vp, vp, vp]
     lib.lemps_last_error.restype = ctypes.c_char_p
     for name in EXPORTED[:-1]:
         getattr(lib, name).restype = ctypes.c_int
