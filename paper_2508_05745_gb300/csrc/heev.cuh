@@ -97,18 +97,34 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
   if (threadIdx.x == 0) s_tr = trp;
 
   // ---- phase 1: tridiagonalization ------------------------------------------
-  // Steps whose trailing block does not fit in shared memory work on the full
-  // matrix in global memory; from j0 on, the lower triangle of G[j0:, j0:] is
-  // packed into shared memory and the remaining steps stay on chip.
+  // Steps whose trailing block does not fit in shared memory form one panel
+  // (LATRD style): G stays read-only in global memory, and the rank-2 updates
+  // G_eff = G - sum_k (v_k w_k^dagger + w_k v_k^dagger) of earlier panel steps
+  // are applied on the fly to the column and to the matvec.  After the panel,
+  // one tiled rank-2 j0 update brings the trailing block G[j0:, j0:] up to
+  // date; its lower triangle is then packed into shared memory and the
+  // remaining steps stay on chip.  V and W (j0 x n each, row k = step k) live
+  // in ws2, which receives the eigenvectors only at the end.
   int j0 = 0;
   while ((n - j0) * (n - j0 + 1) / 2 > HeevSmem<R>::kCap) ++j0;
+  cpx<R>* Vp = U;
+  cpx<R>* Wp = U + (int64_t)j0 * n;
   for (int j = 0; j < j0 && j + 2 < n; ++j) {
     const int m = n - j - 1;
+    // column j of G_eff below the diagonal, and its diagonal entry
     R part = 0;
     for (int i = threadIdx.x; i < m; i += blockDim.x) {
-      cpx<R> x = G[(int64_t)(j + 1 + i) * n + j];
+      const int gi = j + 1 + i;
+      cpx<R> x = G[(int64_t)gi * n + j];
+      for (int k = 0; k < j; ++k)
+        x -= Vp[(int64_t)k * n + gi] * conj(Wp[(int64_t)k * n + j]) + Wp[(int64_t)k * n + gi] * conj(Vp[(int64_t)k * n + j]);
       sv[i] = x;
       if (i > 0) part += norm2(x);
+    }
+    if (threadIdx.x == 0) {
+      R dj = G[(int64_t)j * n + j].re;
+      for (int k = 0; k < j; ++k) dj -= (R)2 * cdot(Wp[(int64_t)k * n + j], Vp[(int64_t)k * n + j]).re;
+      sd[j] = dj;
     }
     R sig = block_sum(part, red);
     cpx<R> x0 = sv[0];
@@ -124,13 +140,29 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
       for (int i = threadIdx.x; i < m; i += blockDim.x) sv[i] = (i == 0) ? (x0 - alpha) * inv : sv[i] * inv;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-      sd[j] = G[(int64_t)j * n + j].re;
-      sec[j] = alpha;
+    if (threadIdx.x == 0) sec[j] = alpha;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const cpx<R> vi = (i > j && reflect) ? sv[i - j - 1] : mk<R>(0, 0);
+      Hv[(int64_t)j * n + i] = vi;
+      Vp[(int64_t)j * n + i] = vi;
     }
-    for (int i = threadIdx.x; i < n; i += blockDim.x)
-      Hv[(int64_t)j * n + i] = (i > j && reflect) ? sv[i - j - 1] : mk<R>(0, 0);
-    if (!reflect) continue;
+    if (!reflect) {
+      for (int i = threadIdx.x; i < n; i += blockDim.x) Wp[(int64_t)j * n + i] = mk<R>(0, 0);
+      __syncthreads();
+      continue;
+    }
+    // corrections c1_k = w_k^dagger v, c2_k = v_k^dagger v (k < j); sph is
+    // free until the end of phase 1 and holds 2 j < 2 j0 <= 256 entries
+    cpx<R>* cc = sph;
+    for (int kk = warp; kk < 2 * j; kk += nwarp) {
+      const cpx<R>* src = (kk < j) ? (Wp + (int64_t)kk * n) : (Vp + (int64_t)(kk - j) * n);
+      cpx<R> acc = mk<R>(0, 0);
+      for (int i = lane; i < m; i += 32) cfmac(acc, src[j + 1 + i], sv[i]);
+      acc.re = warp_sum(acc.re);
+      acc.im = warp_sum(acc.im);
+      if (lane == 0) cc[kk] = acc;
+    }
+    // y = G_sub v from the original (read-only) G, one warp per row
     for (int r = warp; r < m; r += nwarp) {
       const cpx<R>* row = G + (int64_t)(j + 1 + r) * n + (j + 1);
       cpx<R> acc = mk<R>(0, 0);
@@ -140,17 +172,83 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
       if (lane == 0) sw[r] = acc;
     }
     __syncthreads();
+    // y -= sum_k v_k (w_k^dagger v) + w_k (v_k^dagger v)
     R sp = 0;
-    for (int i = threadIdx.x; i < m; i += blockDim.x) sp += cdot(sv[i], sw[i]).re;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+      const int gi = j + 1 + i;
+      cpx<R> y = sw[i];
+      for (int k = 0; k < j; ++k) y -= Vp[(int64_t)k * n + gi] * cc[k] + Wp[(int64_t)k * n + gi] * cc[j + k];
+      sw[i] = y;
+      sp += cdot(sv[i], y).re;
+    }
     R ss = block_sum(sp, red);
-    for (int i = threadIdx.x; i < m; i += blockDim.x) sw[i] = (R)2 * sw[i] - ((R)2 * ss) * sv[i];
-    __syncthreads();
-    for (int64_t e = threadIdx.x; e < (int64_t)m * m; e += blockDim.x) {
-      const int r = (int)(e / m), c = (int)(e % m);
-      cpx<R>* g = G + (int64_t)(j + 1 + r) * n + (j + 1 + c);
-      *g = *g - sv[r] * conj(sw[c]) - sw[r] * conj(sv[c]);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const cpx<R> wi = (i > j) ? (R)2 * sw[i - j - 1] - ((R)2 * ss) * sv[i - j - 1] : mk<R>(0, 0);
+      Wp[(int64_t)j * n + i] = wi;
     }
     __syncthreads();
+  }
+  if (j0 > 0) {
+    // G[j0:, j0:] -= sum_k v_k w_k^dagger + w_k v_k^dagger over the panel
+    // (lower triangle only).  V and W are staged in shared memory in chunks
+    // of kch steps; 64 x 64 output tiles, each of the 512 threads (32 x 16)
+    // owns rows ty + 16 r and columns tx + 32 c of a tile.
+    const int mt = n - j0;
+    const int kch = min(j0, (int)(HeevSmem<R>::kBytes / (2 * (size_t)mt * sizeof(cpx<R>))));
+    cpx<R>* Vs = Lp;
+    cpx<R>* Ws = Lp + (int64_t)kch * mt;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int ntile = (mt + 63) / 64;
+    for (int k0 = 0; k0 < j0; k0 += kch) {
+      const int kc = min(kch, j0 - k0);
+      for (int e = threadIdx.x; e < kc * mt; e += blockDim.x) {
+        const int kk = e / mt, i = e - kk * mt;
+        Vs[e] = Vp[(int64_t)(k0 + kk) * n + j0 + i];
+        Ws[e] = Wp[(int64_t)(k0 + kk) * n + j0 + i];
+      }
+      __syncthreads();
+      for (int ti = 0; ti < ntile; ++ti)
+        for (int tc = 0; tc <= ti; ++tc) {
+          cpx<R> acc[4][2];
+#pragma unroll
+          for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int c = 0; c < 2; ++c) acc[r][c] = mk<R>(0, 0);
+          for (int kk = 0; kk < kc; ++kk) {
+            cpx<R> va[4], wa[4], vb[2], wb[2];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+              const int i = ti * 64 + ty + 16 * r;
+              va[r] = i < mt ? Vs[kk * mt + i] : mk<R>(0, 0);
+              wa[r] = i < mt ? Ws[kk * mt + i] : mk<R>(0, 0);
+            }
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+              const int i = tc * 64 + tx + 32 * c;
+              vb[c] = i < mt ? Vs[kk * mt + i] : mk<R>(0, 0);
+              wb[c] = i < mt ? Ws[kk * mt + i] : mk<R>(0, 0);
+            }
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+              for (int c = 0; c < 2; ++c) {
+                cfmac(acc[r][c], wb[c], va[r]);
+                cfmac(acc[r][c], vb[c], wa[r]);
+              }
+          }
+#pragma unroll
+          for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+              const int i = ti * 64 + ty + 16 * r, cc = tc * 64 + tx + 32 * c;
+              if (i < mt && cc <= i) {
+                cpx<R>* g = G + (int64_t)(j0 + i) * n + (j0 + cc);
+                *g = *g - acc[r][c];
+              }
+            }
+        }
+      __syncthreads();
+    }
   }
   // pack the lower triangle of the trailing block G[j0:, j0:]
   const int M0 = n - j0;
@@ -279,46 +377,66 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
   __syncthreads();
 
   // ---- phase 3: inverse iteration (LDL^T of T - l I, two solves) ------------
-  // scratch in ws1 (the Gram matrix is no longer needed): per vector k the
-  // arrays dd[i], ll[i], z[i] at ((i * 3 + a) * keep + k) as R values.
+  // Each thread owns one kept eigenvalue.  The LDL^T factors and the iterate
+  // live in shared memory (the packed triangle is no longer needed) when a
+  // chunk of vectors fits, else in the global scratch (ws1): per vector k the
+  // arrays dd[i], ll[i], z[i] at ((i * 3 + a) * kc + k).  Results go to the
+  // global scratch z[i][k] = scr[(i * 3 + 2) * keep + k].
   R* scr = reinterpret_cast<R*>(G);
-  for (int k = threadIdx.x; k < keep; k += blockDim.x) {
-    const R lam = (R)ev[k];
-    R dprev = sd[0] - lam;
-    if (fabs(dprev) < pivmin) dprev = pivmin;
-    scr[(0 * 3 + 0) * keep + k] = dprev;
-    for (int i = 0; i + 1 < n; ++i) {
-      R li = se[i] / dprev;
-      scr[(i * 3 + 1) * keep + k] = li;
-      R dn = (sd[i + 1] - lam) - li * se[i];
-      if (fabs(dn) < pivmin) dn = pivmin;
-      scr[((i + 1) * 3 + 0) * keep + k] = dn;
-      dprev = dn;
-    }
-    for (int i = 0; i < n; ++i) scr[(i * 3 + 2) * keep + k] = (R)start_entry(k, i);
-    for (int iter = 0; iter < 2; ++iter) {
-      R y = scr[(0 * 3 + 2) * keep + k];
-      for (int i = 1; i < n; ++i) {
-        y = scr[(i * 3 + 2) * keep + k] - scr[((i - 1) * 3 + 1) * keep + k] * y;
-        scr[(i * 3 + 2) * keep + k] = y;
+  {
+    const int chunk_cap = HeevSmem<R>::kBytes / (3 * n * (int)sizeof(R));
+    const bool in_smem = chunk_cap >= 32;
+    const int kc_max = in_smem ? min(chunk_cap, (int)blockDim.x) : keep;
+    R* wsp = in_smem ? reinterpret_cast<R*>(heev_smem) : scr;
+    for (int k0 = 0; k0 < keep; k0 += kc_max) {
+      const int kc = min(kc_max, keep - k0);
+      const int ld = in_smem ? kc : keep;      // row stride of the work arrays
+      const int koff = in_smem ? 0 : k0;
+      for (int kk = threadIdx.x; kk < kc; kk += blockDim.x) {
+        const int k = k0 + kk;
+        R* w3 = wsp + koff + kk;
+        const R lam = (R)ev[k];
+        R dprev = sd[0] - lam;
+        if (fabs(dprev) < pivmin) dprev = pivmin;
+        w3[(0 * 3 + 0) * ld] = dprev;
+        for (int i = 0; i + 1 < n; ++i) {
+          R li = se[i] / dprev;
+          w3[(i * 3 + 1) * ld] = li;
+          R dn = (sd[i + 1] - lam) - li * se[i];
+          if (fabs(dn) < pivmin) dn = pivmin;
+          w3[((i + 1) * 3 + 0) * ld] = dn;
+          dprev = dn;
+        }
+        for (int i = 0; i < n; ++i) w3[(i * 3 + 2) * ld] = (R)start_entry(k, i);
+        for (int iter = 0; iter < 2; ++iter) {
+          R y = w3[(0 * 3 + 2) * ld];
+          for (int i = 1; i < n; ++i) {
+            y = w3[(i * 3 + 2) * ld] - w3[((i - 1) * 3 + 1) * ld] * y;
+            w3[(i * 3 + 2) * ld] = y;
+          }
+          R zn = w3[((n - 1) * 3 + 2) * ld] / w3[((n - 1) * 3 + 0) * ld];
+          w3[((n - 1) * 3 + 2) * ld] = zn;
+          R amax = fabs(zn);
+          for (int i = n - 2; i >= 0; --i) {
+            zn = w3[(i * 3 + 2) * ld] / w3[(i * 3 + 0) * ld] - w3[(i * 3 + 1) * ld] * zn;
+            w3[(i * 3 + 2) * ld] = zn;
+            amax = fmax(amax, fabs(zn));
+          }
+          R sc = (amax > 0) ? (R)1 / amax : (R)1;
+          for (int i = 0; i < n; ++i) w3[(i * 3 + 2) * ld] *= sc;
+        }
+        if (in_smem)
+          for (int i = 0; i < n; ++i) scr[(i * 3 + 2) * keep + k] = w3[(i * 3 + 2) * ld];
       }
-      R zn = scr[((n - 1) * 3 + 2) * keep + k] / scr[((n - 1) * 3 + 0) * keep + k];
-      scr[((n - 1) * 3 + 2) * keep + k] = zn;
-      R amax = fabs(zn);
-      for (int i = n - 2; i >= 0; --i) {
-        zn = scr[(i * 3 + 2) * keep + k] / scr[(i * 3 + 0) * keep + k] - scr[(i * 3 + 1) * keep + k] * zn;
-        scr[(i * 3 + 2) * keep + k] = zn;
-        amax = fmax(amax, fabs(zn));
-      }
-      R sc = (amax > 0) ? (R)1 / amax : (R)1;
-      for (int i = 0; i < n; ++i) scr[(i * 3 + 2) * keep + k] *= sc;
+      __syncthreads();
     }
   }
-  __syncthreads();
   // ---- phase 4: Gram-Schmidt (twice) in descending eigenvalue order ----------
   // The vectors move to shared memory (vector-contiguous, Z[k * n + i]) when
   // they fit, otherwise they stay in the global scratch.
-  const bool zsm = (int64_t)keep * n * (int64_t)sizeof(R) <= HeevSmem<R>::kBytes;
+  // (room is left for at least 8 staged reflector rows of the back-transform)
+  const bool zsm = (int64_t)keep * n * (int64_t)sizeof(R) + 16 + 8 * (int64_t)n * (int64_t)sizeof(cpx<R>) <=
+                   HeevSmem<R>::kBytes;
   R* Zs = reinterpret_cast<R*>(heev_smem);
   if (zsm)
     for (int e = threadIdx.x; e < keep * n; e += blockDim.x) Zs[e] = scr[((e % n) * 3 + 2) * keep + e / n];
@@ -348,36 +466,70 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
     for (int i = threadIdx.x; i < n; i += blockDim.x) Z(k, i) *= inv;
     __syncthreads();
   }
-  // ---- phase 5: back-transformation U = Q D z, one warp per column ------------
+  // ---- phase 5: back-transformation U = Q D z --------------------------------
+  // Each warp owns two columns held in registers (8 entries per lane each);
+  // reflectors are staged through shared memory in chunks of rc rows, placed
+  // after the shared-memory copy of z.
   constexpr int PER = 8;  // n <= 256 -> 8 elements per lane
-  for (int k = warp; k < keep; k += nwarp) {
-    cpx<R> y[PER];
+  const size_t zbytes = zsm ? (((size_t)keep * n * sizeof(R) + 15) / 16) * 16 : 0;
+  const int rc = min(32, (int)((HeevSmem<R>::kBytes - zbytes) / ((size_t)n * sizeof(cpx<R>))));
+  cpx<R> y0[PER], y1[PER];
+  cpx<R>* vst = reinterpret_cast<cpx<R>*>(heev_smem + zbytes);
+  const int npairs = (keep + 1) / 2;
+  const int passes = (npairs + nwarp - 1) / nwarp;
+  for (int pass = 0; pass < passes; ++pass) {
+    const int pr = warp + pass * nwarp;
+    const int k0c = 2 * pr, k1c = 2 * pr + 1;
+    const bool act0 = k0c < keep, act1 = k1c < keep;
 #pragma unroll
     for (int a = 0; a < PER; ++a) {
       const int i = lane + 32 * a;
-      y[a] = (i < n) ? sph[i] * Z(k, i) : mk<R>(0, 0);
+      y0[a] = (i < n && act0) ? sph[i] * Z(k0c, i) : mk<R>(0, 0);
+      y1[a] = (i < n && act1) ? sph[i] * Z(k1c, i) : mk<R>(0, 0);
     }
-    for (int j = n - 3; j >= 0; --j) {
-      const cpx<R>* v = Hv + (int64_t)j * n;
-      cpx<R> dot = mk<R>(0, 0);
-#pragma unroll
-      for (int a = 0; a < PER; ++a) {
-        const int i = lane + 32 * a;
-        if (i > j && i < n) cfmac(dot, v[i], y[a]);
+    __syncthreads();
+    for (int jtop = n - 3; jtop >= 0; jtop -= rc) {
+      const int jlo = max(0, jtop - rc + 1);
+      for (int e = threadIdx.x; e < (jtop - jlo + 1) * n; e += blockDim.x) {
+        const int rr = e / n, i = e % n;
+        vst[rr * n + i] = Hv[(int64_t)(jlo + rr) * n + i];
       }
-      dot.re = warp_sum(dot.re);
-      dot.im = warp_sum(dot.im);
-      dot = (R)2 * dot;
+      __syncthreads();
+      if (act0 || act1) {
+        for (int j = jtop; j >= jlo; --j) {
+          const cpx<R>* v = vst + (j - jlo) * n;
+          cpx<R> d0 = mk<R>(0, 0), d1 = mk<R>(0, 0);
 #pragma unroll
-      for (int a = 0; a < PER; ++a) {
-        const int i = lane + 32 * a;
-        if (i > j && i < n) y[a] -= v[i] * dot;
+          for (int a = 0; a < PER; ++a) {
+            const int i = lane + 32 * a;
+            if (i > j && i < n) {
+              cfmac(d0, v[i], y0[a]);
+              cfmac(d1, v[i], y1[a]);
+            }
+          }
+          d0.re = warp_sum(d0.re); d0.im = warp_sum(d0.im);
+          d1.re = warp_sum(d1.re); d1.im = warp_sum(d1.im);
+          d0 = (R)2 * d0;
+          d1 = (R)2 * d1;
+#pragma unroll
+          for (int a = 0; a < PER; ++a) {
+            const int i = lane + 32 * a;
+            if (i > j && i < n) {
+              y0[a] -= v[i] * d0;
+              y1[a] -= v[i] * d1;
+            }
+          }
+        }
       }
+      __syncthreads();
     }
 #pragma unroll
     for (int a = 0; a < PER; ++a) {
       const int i = lane + 32 * a;
-      if (i < n) U[(int64_t)k * n + i] = y[a];
+      if (i < n) {
+        if (act0) U[(int64_t)k0c * n + i] = y0[a];
+        if (act1) U[(int64_t)k1c * n + i] = y1[a];
+      }
     }
   }
 }
