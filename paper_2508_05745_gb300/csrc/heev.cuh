@@ -13,6 +13,8 @@
 // descending) to evals[0..keep), keep and the trace to kept[] / trace[].
 #pragma once
 
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace lemps {
@@ -432,46 +434,203 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
     }
   }
   // ---- phase 4: Gram-Schmidt (twice) in descending eigenvalue order ----------
-  // The vectors move to shared memory (vector-contiguous, Z[k * n + i]) when
-  // they fit, otherwise they stay in the global scratch.
-  // (room is left for at least 8 staged reflector rows of the back-transform)
-  const bool zsm = (int64_t)keep * n * (int64_t)sizeof(R) + 16 + 8 * (int64_t)n * (int64_t)sizeof(cpx<R>) <=
-                   HeevSmem<R>::kBytes;
+  // When the vectors fit in shared memory (Z[k * ldz + i], rows padded so
+  // that 16-byte loads of consecutive rows hit distinct banks) they are
+  // orthonormalized in blocks of 16 (block classical Gram-Schmidt, twice):
+  // project the block against all earlier vectors, then orthonormalize it
+  // by Cholesky QR of its 16 x 16 Gram matrix.  A block whose Cholesky
+  // pivots show near-dependence (pivot < tol * squared norm) is redone by
+  // per-vector classical Gram-Schmidt (twice).  Otherwise the vectors stay
+  // in the global scratch and the per-vector scheme runs for all of them.
+  constexpr int NB = 16;
+  constexpr int E = 16 / (int)sizeof(R);             // elements per 16-byte load
+  constexpr int ROWQ = 128 / (int)sizeof(R);         // elements per 128 bytes
+  const int ldz = ((n + ROWQ - 1) / ROWQ) * ROWQ + E;
+  const size_t zs_bytes = (size_t)keep * ldz * sizeof(R);
+  const size_t cb_bytes = (size_t)128 * NB * sizeof(R);
+  const bool zsm = keep <= 128 && zs_bytes + cb_bytes + 8 * (size_t)n * sizeof(cpx<R>) <= (size_t)HeevSmem<R>::kBytes;
   R* Zs = reinterpret_cast<R*>(heev_smem);
   if (zsm)
-    for (int e = threadIdx.x; e < keep * n; e += blockDim.x) Zs[e] = scr[((e % n) * 3 + 2) * keep + e / n];
+    for (int e = threadIdx.x; e < keep * ldz; e += blockDim.x) {
+      const int k = e / ldz, i = e - k * ldz;
+      Zs[e] = (i < n) ? scr[(i * 3 + 2) * keep + k] : (R)0;
+    }
   __syncthreads();
-  auto Z = [&](int k, int i) -> R& { return zsm ? Zs[k * n + i] : scr[(i * 3 + 2) * keep + k]; };
+  auto Z = [&](int k, int i) -> R& { return zsm ? Zs[k * ldz + i] : scr[(i * 3 + 2) * keep + k]; };
   R* cbuf = reinterpret_cast<R*>(sw);
-  for (int k = 0; k < keep; ++k) {
-    for (int pass = 0; pass < 2; ++pass) {
-      for (int jj = warp; jj < k; jj += nwarp) {
-        R acc = 0;
-        for (int i = lane; i < n; i += 32) acc += Z(jj, i) * Z(k, i);
-        acc = warp_sum(acc);
-        if (lane == 0) cbuf[jj] = acc;
+  // per-vector CGS2 + normalization of vectors k in [k_from, k_to), against
+  // all vectors in [p_from, k)
+  auto cgs_vectors = [&](int p_from, int k_from, int k_to) {
+    for (int k = k_from; k < k_to; ++k) {
+      for (int pass = 0; pass < 2; ++pass) {
+        for (int jj = p_from + warp; jj < k; jj += nwarp) {
+          R acc = 0;
+          for (int i = lane; i < n; i += 32) acc += Z(jj, i) * Z(k, i);
+          acc = warp_sum(acc);
+          if (lane == 0) cbuf[jj - p_from] = acc;
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+          R v = Z(k, i);
+          for (int jj = p_from; jj < k; ++jj) v -= cbuf[jj - p_from] * Z(jj, i);
+          Z(k, i) = v;
+        }
+        __syncthreads();
       }
-      __syncthreads();
-      for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        R v = Z(k, i);
-        for (int jj = 0; jj < k; ++jj) v -= cbuf[jj] * Z(jj, i);
-        Z(k, i) = v;
-      }
+      R part = 0;
+      for (int i = threadIdx.x; i < n; i += blockDim.x) part += Z(k, i) * Z(k, i);
+      R nn = block_sum(part, red);
+      R inv = nn > 0 ? (R)1 / sqrt(nn) : (R)0;
+      for (int i = threadIdx.x; i < n; i += blockDim.x) Z(k, i) *= inv;
       __syncthreads();
     }
-    R part = 0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) part += Z(k, i) * Z(k, i);
-    R nn = block_sum(part, red);
-    R inv = nn > 0 ? (R)1 / sqrt(nn) : (R)0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) Z(k, i) *= inv;
-    __syncthreads();
+  };
+  if (!zsm) {
+    cgs_vectors(0, 0, keep);
+  } else {
+    using V16 = typename std::conditional<sizeof(R) == 4, float4, double2>::type;
+    R* cb = Zs + (size_t)keep * ldz;                   // [128][NB] projection coefficients
+    R* gq = reinterpret_cast<R*>(sv);                  // [NB][NB] block Gram matrix
+    R* lq = gq + NB * NB;                              // [NB][NB] its Cholesky factor
+    __shared__ int s_fail;
+    const int nvec = (n + E - 1) / E;
+    const R tol = (sizeof(R) == 8) ? (R)1e-8 : (R)1e-3;
+    for (int kb = 0; kb < keep; kb += NB) {
+      const int nbk = min(NB, keep - kb);
+      for (int rep = 0; rep < 2; ++rep) {
+        if (kb > 0) {
+          // cb[a][b] = <z_a, z_{kb+b}>, a < kb: thread (a, 4 consecutive b)
+          {
+            const int b0 = (threadIdx.x >> 7) * 4;
+            for (int aa = threadIdx.x & 127; aa < kb; aa += 128) {
+              R acc[4] = {0, 0, 0, 0};
+              const V16* za = reinterpret_cast<const V16*>(Zs + (size_t)aa * ldz);
+              const V16* zb[4];
+#pragma unroll
+              for (int c = 0; c < 4; ++c)
+                zb[c] = reinterpret_cast<const V16*>(Zs + (size_t)min(kb + b0 + c, keep - 1) * ldz);
+              for (int v = 0; v < nvec; ++v) {
+                const V16 x = za[v];
+                const R* xr = reinterpret_cast<const R*>(&x);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                  const V16 y = zb[c][v];
+                  const R* yr = reinterpret_cast<const R*>(&y);
+#pragma unroll
+                  for (int e = 0; e < E; ++e) acc[c] = fma(xr[e], yr[e], acc[c]);
+                }
+              }
+#pragma unroll
+              for (int c = 0; c < 4; ++c)
+                if (b0 + c < nbk) cb[aa * NB + b0 + c] = acc[c];
+            }
+          }
+          __syncthreads();
+          // z_{kb+b} -= sum_a cb[a][b] z_a: thread (16-byte column slice, 2 b)
+          {
+            const int b0 = (threadIdx.x >> 6) * 2;
+            if (b0 < nbk)
+              for (int v = threadIdx.x & 63; v < nvec; v += 64) {
+                V16* y0p = reinterpret_cast<V16*>(Zs + (size_t)(kb + b0) * ldz) + v;
+                V16* y1p = reinterpret_cast<V16*>(Zs + (size_t)(kb + min(b0 + 1, nbk - 1)) * ldz) + v;
+                V16 y0 = *y0p, y1 = *y1p;
+                R* r0 = reinterpret_cast<R*>(&y0);
+                R* r1 = reinterpret_cast<R*>(&y1);
+                for (int aa = 0; aa < kb; ++aa) {
+                  const V16 x = reinterpret_cast<const V16*>(Zs + (size_t)aa * ldz)[v];
+                  const R* xr = reinterpret_cast<const R*>(&x);
+                  const R c0 = cb[aa * NB + b0], c1 = cb[aa * NB + b0 + 1];
+#pragma unroll
+                  for (int e = 0; e < E; ++e) {
+                    r0[e] = fma(-c0, xr[e], r0[e]);
+                    r1[e] = fma(-c1, xr[e], r1[e]);
+                  }
+                }
+                *y0p = y0;
+                if (b0 + 1 < nbk) *y1p = y1;
+              }
+          }
+          __syncthreads();
+        }
+        // Gram matrix of the block: thread pair (b, c), halves of the row
+        {
+          const int ent = threadIdx.x >> 1, h = threadIdx.x & 1;
+          const int bb = ent / NB, cc2 = ent % NB;
+          R acc = 0;
+          if (bb < nbk && cc2 < nbk) {
+            const V16* zb = reinterpret_cast<const V16*>(Zs + (size_t)(kb + bb) * ldz);
+            const V16* zc = reinterpret_cast<const V16*>(Zs + (size_t)(kb + cc2) * ldz);
+            for (int v = h; v < nvec; v += 2) {
+              const V16 x = zb[v], y = zc[v];
+              const R* xr = reinterpret_cast<const R*>(&x);
+              const R* yr = reinterpret_cast<const R*>(&y);
+#pragma unroll
+              for (int e = 0; e < E; ++e) acc = fma(xr[e], yr[e], acc);
+            }
+          }
+          acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+          if (h == 0 && ent < NB * NB) gq[ent] = acc;
+        }
+        __syncthreads();
+        // Cholesky G = L L^T by warp 0 (lane i owns row i)
+        if (warp == 0) {
+          R li[NB];
+#pragma unroll
+          for (int c = 0; c < NB; ++c) li[c] = 0;
+          int fail = 0;
+          const R gii = (lane < nbk) ? gq[lane * NB + lane] : (R)1;
+#pragma unroll
+          for (int j = 0; j < NB; ++j) {
+            if (j < nbk) {
+              R sj = (lane < nbk) ? gq[lane * NB + j] : (R)0;
+#pragma unroll
+              for (int c = 0; c < j; ++c) sj -= li[c] * __shfl_sync(0xffffffffu, li[c], j);
+              const R piv = __shfl_sync(0xffffffffu, sj, j);
+              const R gjj = __shfl_sync(0xffffffffu, gii, j);
+              if (!(piv > tol * gjj) || !(gjj > (R)0)) fail = 1;
+              const R ljj = sqrt(fmax(piv, (R)0));
+              if (lane == j) li[j] = ljj;
+              else if (lane > j) li[j] = (ljj > 0) ? sj / ljj : (R)0;
+            }
+          }
+          if (lane < NB)
+#pragma unroll
+            for (int c = 0; c < NB; ++c) lq[lane * NB + c] = li[c];
+          if (lane == 0) s_fail = fail;
+        }
+        __syncthreads();
+        if (s_fail) {
+          cgs_vectors(kb, kb, kb + nbk);
+        } else {
+          // Z_blk <- L^{-1} Z_blk, one column entry i per thread
+          for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            R x[NB];
+#pragma unroll
+            for (int b = 0; b < NB; ++b) x[b] = (b < nbk) ? Zs[(size_t)(kb + b) * ldz + i] : (R)0;
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
+              if (b < nbk) {
+                R v = x[b];
+#pragma unroll
+                for (int c = 0; c < b; ++c) v -= lq[b * NB + c] * x[c];
+                x[b] = v / lq[b * NB + b];
+              }
+            }
+#pragma unroll
+            for (int b = 0; b < NB; ++b)
+              if (b < nbk) Zs[(size_t)(kb + b) * ldz + i] = x[b];
+          }
+          __syncthreads();
+        }
+      }
+    }
   }
   // ---- phase 5: back-transformation U = Q D z --------------------------------
   // Each warp owns two columns held in registers (8 entries per lane each);
   // reflectors are staged through shared memory in chunks of rc rows, placed
   // after the shared-memory copy of z.
   constexpr int PER = 8;  // n <= 256 -> 8 elements per lane
-  const size_t zbytes = zsm ? (((size_t)keep * n * sizeof(R) + 15) / 16) * 16 : 0;
+  const size_t zbytes = zsm ? zs_bytes + cb_bytes : 0;
   const int rc = min(32, (int)((HeevSmem<R>::kBytes - zbytes) / ((size_t)n * sizeof(cpx<R>))));
   cpx<R> y0[PER], y1[PER];
   cpx<R>* vst = reinterpret_cast<cpx<R>*>(heev_smem + zbytes);
