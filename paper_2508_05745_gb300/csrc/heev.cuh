@@ -257,74 +257,156 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
   for (int r = warp; r < M0; r += nwarp)
     for (int c = lane; c <= r; c += 32) Lp[pidx(r, c)] = G[(int64_t)(j0 + r) * n + (j0 + c)];
   __syncthreads();
+  // The rank-2 update of each step is applied lazily: Lp holds the trailing
+  // block without the update of the previous step, whose v and y (so that
+  // w = 2 y - 2 (v^dagger y) v) sit in ping-pong buffers indexed by local row.
+  // A step reads its column with that correction, then one row pass (warp
+  // per row, lanes over columns) writes the corrected entries back and forms
+  // the lower-triangle half of y = A v, and one tile pass (32 x 32 tiles,
+  // lane per column) adds the strictly-upper half; four barriers per step.
+  __shared__ cpx<R> sy2[256];
+  __shared__ R redn[32], reds[32];
+  for (int i = threadIdx.x; i < M0; i += blockDim.x) {
+    sv[i] = mk<R>(0, 0); sw[i] = mk<R>(0, 0);
+    sph[i] = mk<R>(0, 0); sy2[i] = mk<R>(0, 0);
+  }
+  __syncthreads();
+  R ssP = 0;
+  int pb = 0;   // buffers of the previous step
   for (int j = j0; j + 2 < n; ++j) {
     const int jl = j - j0;     // local index of column j
     const int m = n - j - 1;   // trailing size; local rows jl+1 .. M0-1
+    const int qb = pb ^ 1;
+    const cpx<R>* vP = pb ? sw : sv;
+    const cpx<R>* yP = pb ? sy2 : sph;
+    cpx<R>* vN = qb ? sw : sv;
+    cpx<R>* yN = qb ? sy2 : sph;
+    auto wprev = [&](int X) { return (R)2 * yP[X] - ((R)2 * ssP) * vP[X]; };
+    const cpx<R> vPj = vP[jl], wPj = wprev(jl);
+    // column jl below the diagonal (one entry per thread; m < blockDim.x)
+    const int i = threadIdx.x;
+    cpx<R> x = mk<R>(0, 0);
     R part = 0;
-    for (int i = threadIdx.x; i < m; i += blockDim.x) {
-      cpx<R> x = Lp[pidx(jl + 1 + i, jl)];
-      sv[i] = x;
-      if (i > 0) part += norm2(x);
+    if (i < m) {
+      const int Rr = jl + 1 + i;
+      x = Lp[pidx(Rr, jl)] - vP[Rr] * conj(wPj) - wprev(Rr) * conj(vPj);
+      if (i > 0) part = norm2(x);
     }
-    R sig = block_sum(part, red);
-    cpx<R> x0 = sv[0];
-    R ax0 = sqrt(norm2(x0));
-    R nrm = sqrt(sig + ax0 * ax0);
-    const bool reflect = sig > (R)0;
-    cpx<R> alpha = x0;
-    if (reflect) {
+    const cpx<R> x0 = Lp[pidx(jl + 1, jl)] - vP[jl + 1] * conj(wPj) - wprev(jl + 1) * conj(vPj);
+    part = warp_sum(part);
+    if (lane == 0) redn[warp] = part;
+    __syncthreads();
+    R sig = 0;
+    for (int w2 = 0; w2 < nwarp; ++w2) sig += redn[w2];
+    const R ax0 = sqrt(norm2(x0));
+    const R nrm = sqrt(sig + ax0 * ax0);
+    cpx<R> alpha = x0, vi = mk<R>(0, 0);
+    if (sig > (R)0) {
       cpx<R> ph = (ax0 > 0) ? mk<R>(x0.re / ax0, x0.im / ax0) : mk<R>(1, 0);
       alpha = mk<R>(-nrm * ph.re, -nrm * ph.im);
-      R inv = (R)1 / sqrt(sig + (ax0 + nrm) * (ax0 + nrm));
-      __syncthreads();
-      for (int i = threadIdx.x; i < m; i += blockDim.x) sv[i] = (i == 0) ? (x0 - alpha) * inv : sv[i] * inv;
+      const R inv = (R)1 / sqrt(sig + (ax0 + nrm) * (ax0 + nrm));
+      vi = (i == 0) ? (x0 - alpha) * inv : x * inv;
     }
-    __syncthreads();
+    if (i < m) {
+      vN[jl + 1 + i] = vi;
+      Hv[(int64_t)j * n + (j + 1 + i)] = vi;
+    }
+    if (i <= j) Hv[(int64_t)j * n + i] = mk<R>(0, 0);
     if (threadIdx.x == 0) {
-      sd[j] = Lp[pidx(jl, jl)].re;
+      sd[j] = Lp[pidx(jl, jl)].re - (R)2 * cdot(wPj, vPj).re;
       sec[j] = alpha;
     }
-    for (int i = threadIdx.x; i < n; i += blockDim.x)
-      Hv[(int64_t)j * n + i] = (i > j && reflect) ? sv[i - j - 1] : mk<R>(0, 0);
-    if (!reflect) continue;
-    // y = G_sub v, Hermitian from the lower triangle: rows (r >= c) then the
-    // strictly-upper part as conj of columns
-    for (int r = warp; r < m; r += nwarp) {
-      const cpx<R>* row = Lp + pidx(jl + 1 + r, jl + 1);
-      cpx<R> acc = mk<R>(0, 0);
-      for (int c = lane; c <= r; c += 32) cfma(acc, row[c], sv[c]);
-      acc.re = warp_sum(acc.re);
-      acc.im = warp_sum(acc.im);
-      if (lane == 0) sw[r] = acc;
+    __syncthreads();
+    // row pass: apply the previous update to rows jl+1.. (c <= r), y_lower
+    R ssp = 0;
+    {
+      constexpr int PT = 8;                     // column slots per lane (m <= 255)
+      constexpr bool kCache = sizeof(R) == 4;   // column values kept in registers (c64)
+      cpx<R> vc[kCache ? PT : 1], wc[kCache ? PT : 1], nc[kCache ? PT : 1];
+      if (kCache) {
+#pragma unroll
+        for (int t = 0; t < (kCache ? PT : 1); ++t) {
+          const int c = lane + 32 * t;
+          const bool in = c < m;
+          const int C = jl + 1 + c;
+          vc[t] = in ? vP[C] : mk<R>(0, 0);
+          wc[t] = in ? wprev(C) : mk<R>(0, 0);
+          nc[t] = in ? vN[C] : mk<R>(0, 0);
+        }
+      }
+      for (int r = warp; r < m; r += nwarp) {
+        const int Rr = jl + 1 + r;
+        const cpx<R> vr = vP[Rr], wr = wprev(Rr);
+        cpx<R>* row = Lp + pidx(Rr, jl + 1);
+        cpx<R> acc = mk<R>(0, 0);
+#pragma unroll
+        for (int t = 0; t < PT; ++t) {
+          if (32 * t <= r) {
+            const int c = lane + 32 * t;
+            if (c <= r) {
+              cpx<R> cv, cw, cn;
+              if (kCache) {
+                cv = vc[kCache ? t : 0]; cw = wc[kCache ? t : 0]; cn = nc[kCache ? t : 0];
+              } else {
+                const int C = jl + 1 + c;
+                cv = vP[C]; cw = wprev(C); cn = vN[C];
+              }
+              const cpx<R> aa = row[c] - vr * conj(cw) - wr * conj(cv);
+              row[c] = aa;
+              cfma(acc, aa, cn);
+            }
+          }
+        }
+        acc.re = warp_sum(acc.re);
+        acc.im = warp_sum(acc.im);
+        if (lane == 0) {
+          yN[Rr] = acc;
+          ssp += cdot(vN[Rr], acc).re;
+        }
+      }
     }
     __syncthreads();
-    for (int c = warp; c < m; c += nwarp) {
-      cpx<R> acc = mk<R>(0, 0);
-      for (int r = c + 1 + lane; r < m; r += 32) cfmac(acc, Lp[pidx(jl + 1 + r, jl + 1 + c)], sv[r]);
-      acc.re = warp_sum(acc.re);
-      acc.im = warp_sum(acc.im);
-      if (lane == 0) sw[c] += acc;
+    // tile pass: y[c] += sum_{r > c} conj(A[r][c]) v[r], lanes over columns
+    {
+      const int nbk = (m + 31) >> 5;
+      const int ntl = nbk * (nbk + 1) / 2;
+      for (int tl = warp; tl < ntl; tl += nwarp) {
+        int I = 0;
+        while ((I + 1) * (I + 2) / 2 <= tl) ++I;
+        const int J = tl - I * (I + 1) / 2;
+        const int c = 32 * J + lane;
+        const int C = jl + 1 + c;
+        cpx<R> acc = mk<R>(0, 0);
+        const int r1 = min(32 * I + 32, m);
+        for (int r = 32 * I; r < r1; ++r)
+          if (r > c) cfmac(acc, Lp[pidx(jl + 1 + r, C)], vN[jl + 1 + r]);
+        if (c < m) {
+          atomicAdd(&yN[C].re, acc.re);
+          atomicAdd(&yN[C].im, acc.im);
+          ssp += cdot(vN[C], acc).re;
+        }
+      }
     }
+    ssp = warp_sum(ssp);
+    if (lane == 0) reds[warp] = ssp;
     __syncthreads();
-    R sp = 0;
-    for (int i = threadIdx.x; i < m; i += blockDim.x) sp += cdot(sv[i], sw[i]).re;
-    R ss = block_sum(sp, red);
-    for (int i = threadIdx.x; i < m; i += blockDim.x) sw[i] = (R)2 * sw[i] - ((R)2 * ss) * sv[i];
-    __syncthreads();
-    for (int r = warp; r < m; r += nwarp) {
-      cpx<R>* row = Lp + pidx(jl + 1 + r, jl + 1);
-      const cpx<R> vr = sv[r], wr = sw[r];
-      for (int c = lane; c <= r; c += 32) row[c] = row[c] - vr * conj(sw[c]) - wr * conj(sv[c]);
-    }
-    __syncthreads();
+    R ss = 0;
+    for (int w2 = 0; w2 < nwarp; ++w2) ss += reds[w2];
+    ssP = ss;
+    pb = qb;
   }
   if (threadIdx.x == 0) {
+    // the last two rows, with the pending update of the last step
+    const cpx<R>* vP = pb ? sw : sv;
+    const cpx<R>* yP = pb ? sy2 : sph;
+    auto wprev = [&](int X) { return (R)2 * yP[X] - ((R)2 * ssP) * vP[X]; };
+    auto aeff = [&](int X, int Y) { return Lp[pidx(X, Y)] - vP[X] * conj(wprev(Y)) - wprev(X) * conj(vP[Y]); };
     const int a = n - 2 - j0, b = n - 1 - j0;   // local indices of the last two rows
     if (n >= 2) {
-      sd[n - 2] = Lp[pidx(a, a)].re;
-      sec[n - 2] = Lp[pidx(b, a)];
+      sd[n - 2] = aeff(a, a).re;
+      sec[n - 2] = aeff(b, a);
     }
-    sd[n - 1] = Lp[pidx(b, b)].re;
+    sd[n - 1] = aeff(b, b).re;
     // phase normalization: delta_{j+1} = delta_j e_j / |e_j|
     cpx<R> dl = mk<R>(1, 0);
     sph[0] = dl;
@@ -626,56 +708,93 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
     }
   }
   // ---- phase 5: back-transformation U = Q D z --------------------------------
-  // Each warp owns two columns held in registers (8 entries per lane each);
-  // reflectors are staged through shared memory in chunks of rc rows, placed
-  // after the shared-memory copy of z.
+  // Each warp owns NCOL columns held in registers (PER entries per lane each);
+  // reflectors are staged through shared memory in chunks of rc rows (row
+  // stride 32 * nper, zero-padded), placed after the shared-memory copy of z.
+  // Reflector j is zero in rows <= j, so 32-row groups below it are skipped.
+  // The NCOL complex dot products of a reflector are summed over the warp by
+  // one reduce-scatter / broadcast butterfly.
   constexpr int PER = 8;  // n <= 256 -> 8 elements per lane
+  constexpr int NCOL = sizeof(R) == 4 ? 4 : 2;
+  constexpr int NV = 2 * NCOL;
+  const int nper = (n + 31) >> 5;
+  const int ldv = 32 * nper;
   const size_t zbytes = zsm ? zs_bytes + cb_bytes : 0;
-  const int rc = min(32, (int)((HeevSmem<R>::kBytes - zbytes) / ((size_t)n * sizeof(cpx<R>))));
-  cpx<R> y0[PER], y1[PER];
+  const int rc = min(32, (int)((HeevSmem<R>::kBytes - zbytes) / ((size_t)ldv * sizeof(cpx<R>))));
+  cpx<R> y[NCOL][PER];
   cpx<R>* vst = reinterpret_cast<cpx<R>*>(heev_smem + zbytes);
-  const int npairs = (keep + 1) / 2;
-  const int passes = (npairs + nwarp - 1) / nwarp;
+  const int ngroups = (keep + NCOL - 1) / NCOL;
+  const int passes = (ngroups + nwarp - 1) / nwarp;
   for (int pass = 0; pass < passes; ++pass) {
-    const int pr = warp + pass * nwarp;
-    const int k0c = 2 * pr, k1c = 2 * pr + 1;
-    const bool act0 = k0c < keep, act1 = k1c < keep;
+    const int k0 = NCOL * (warp + pass * nwarp);
+    const bool act = k0 < keep;
 #pragma unroll
-    for (int a = 0; a < PER; ++a) {
-      const int i = lane + 32 * a;
-      y0[a] = (i < n && act0) ? sph[i] * Z(k0c, i) : mk<R>(0, 0);
-      y1[a] = (i < n && act1) ? sph[i] * Z(k1c, i) : mk<R>(0, 0);
-    }
+    for (int c = 0; c < NCOL; ++c)
+#pragma unroll
+      for (int a = 0; a < PER; ++a) {
+        const int i = lane + 32 * a;
+        y[c][a] = (i < n && k0 + c < keep) ? sph[i] * Z(k0 + c, i) : mk<R>(0, 0);
+      }
     __syncthreads();
     for (int jtop = n - 3; jtop >= 0; jtop -= rc) {
       const int jlo = max(0, jtop - rc + 1);
-      for (int e = threadIdx.x; e < (jtop - jlo + 1) * n; e += blockDim.x) {
-        const int rr = e / n, i = e % n;
-        vst[rr * n + i] = Hv[(int64_t)(jlo + rr) * n + i];
-      }
+      for (int rr = warp; rr <= jtop - jlo; rr += nwarp)
+        for (int i = lane; i < ldv; i += 32)
+          vst[rr * ldv + i] = (i < n) ? Hv[(int64_t)(jlo + rr) * n + i] : mk<R>(0, 0);
       __syncthreads();
-      if (act0 || act1) {
+      if (act) {
         for (int j = jtop; j >= jlo; --j) {
-          const cpx<R>* v = vst + (j - jlo) * n;
-          cpx<R> d0 = mk<R>(0, 0), d1 = mk<R>(0, 0);
+          const cpx<R>* v = vst + (j - jlo) * ldv;
+          const int a0 = (j + 1) >> 5;   // groups a < a0 hold rows <= j only
+          R d[NV];
+#pragma unroll
+          for (int e = 0; e < NV; ++e) d[e] = 0;
+          cpx<R> vr[PER];
 #pragma unroll
           for (int a = 0; a < PER; ++a) {
-            const int i = lane + 32 * a;
-            if (i > j && i < n) {
-              cfmac(d0, v[i], y0[a]);
-              cfmac(d1, v[i], y1[a]);
+            vr[a] = (a >= a0 && a < nper) ? v[lane + 32 * a] : mk<R>(0, 0);
+            if (a >= a0 && a < nper) {
+#pragma unroll
+              for (int c = 0; c < NCOL; ++c) {
+                // d_c += conj(v_i) y_c[i]
+                d[2 * c] = fma(vr[a].re, y[c][a].re, fma(vr[a].im, y[c][a].im, d[2 * c]));
+                d[2 * c + 1] = fma(vr[a].re, y[c][a].im, fma(-vr[a].im, y[c][a].re, d[2 * c + 1]));
+              }
             }
           }
-          d0.re = warp_sum(d0.re); d0.im = warp_sum(d0.im);
-          d1.re = warp_sum(d1.re); d1.im = warp_sum(d1.im);
-          d0 = (R)2 * d0;
-          d1 = (R)2 * d1;
+          // reduce-scatter: after log2(NV) halving rounds lane holds the
+          // partial of value idx(lane); then full sums over the other lanes
+          constexpr int LG = NV == 8 ? 3 : (NV == 4 ? 2 : 1);
+#pragma unroll
+          for (int r = 0; r < LG; ++r) {
+            const int s = 16 >> r;
+            const int h = NV >> (r + 1);
+            const bool up = (lane & s) != 0;
+#pragma unroll
+            for (int k = 0; k < h; ++k) {
+              const R send = up ? d[k] : d[k + h];
+              const R keepv = up ? d[k + h] : d[k];
+              d[k] = keepv + __shfl_xor_sync(0xffffffffu, send, s);
+            }
+          }
+          R tot = d[0];
+#pragma unroll
+          for (int r = LG; r < 5; ++r) tot += __shfl_xor_sync(0xffffffffu, tot, 16 >> r);
+          R dd[NV];
+#pragma unroll
+          for (int e = 0; e < NV; ++e) {
+            // lane holding value e: bits (4, 3, ...) of the lane spell e from the top
+            int src = 0;
+#pragma unroll
+            for (int r = 0; r < LG; ++r)
+              if (e & (1 << (LG - 1 - r))) src |= 16 >> r;
+            dd[e] = (R)2 * __shfl_sync(0xffffffffu, tot, src);
+          }
 #pragma unroll
           for (int a = 0; a < PER; ++a) {
-            const int i = lane + 32 * a;
-            if (i > j && i < n) {
-              y0[a] -= v[i] * d0;
-              y1[a] -= v[i] * d1;
+            if (a >= a0 && a < nper) {
+#pragma unroll
+              for (int c = 0; c < NCOL; ++c) y[c][a] -= vr[a] * mk<R>(dd[2 * c], dd[2 * c + 1]);
             }
           }
         }
@@ -686,8 +805,9 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
     for (int a = 0; a < PER; ++a) {
       const int i = lane + 32 * a;
       if (i < n) {
-        if (act0) U[(int64_t)k0c * n + i] = y0[a];
-        if (act1) U[(int64_t)k1c * n + i] = y1[a];
+#pragma unroll
+        for (int c = 0; c < NCOL; ++c)
+          if (k0 + c < keep) U[(int64_t)(k0 + c) * n + i] = y[c][a];
       }
     }
   }
