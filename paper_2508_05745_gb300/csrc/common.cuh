@@ -84,6 +84,50 @@ __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
+// Sums NV (2, 4 or 8) per-lane values over the warp at once: log2(NV)
+// halving rounds of a reduce-scatter butterfly, then plain rounds over the
+// remaining lane bits.  Returns the total of value scatter_index(lane) (the
+// lane's bits 4, 3, 2 spell it from the most significant bit down); d is
+// clobbered.  Costs NV + 4 - log2(NV) shuffles instead of 5 NV.
+template <int NV>
+struct Scatter {
+  static constexpr int LG = NV == 8 ? 3 : (NV == 4 ? 2 : 1);
+  __device__ __forceinline__ static int index(int lane) {
+    int e = 0;
+#pragma unroll
+    for (int r = 0; r < LG; ++r) e = (e << 1) | ((lane >> (4 - r)) & 1);
+    return e;
+  }
+  // first lane that holds the total of value e
+  __device__ __forceinline__ static int source(int e) {
+    int src = 0;
+#pragma unroll
+    for (int r = 0; r < LG; ++r)
+      if (e & (1 << (LG - 1 - r))) src |= 16 >> r;
+    return src;
+  }
+};
+template <int NV, class T>
+__device__ __forceinline__ T warp_reduce_scatter(T (&d)[NV], int lane) {
+  constexpr int LG = Scatter<NV>::LG;
+#pragma unroll
+  for (int r = 0; r < LG; ++r) {
+    const int s = 16 >> r;
+    const int h = NV >> (r + 1);
+    const bool up = (lane & s) != 0;
+#pragma unroll
+    for (int k = 0; k < h; ++k) {
+      const T send = up ? d[k] : d[k + h];
+      const T keepv = up ? d[k + h] : d[k];
+      d[k] = keepv + __shfl_xor_sync(0xffffffffu, send, s);
+    }
+  }
+  T tot = d[0];
+#pragma unroll
+  for (int r = LG; r < 5; ++r) tot += __shfl_xor_sync(0xffffffffu, tot, 16 >> r);
+  return tot;
+}
+
 // Sum over the block; every thread receives the result.  `scratch` holds at
 // least blockDim.x/32 values.
 template <class T>

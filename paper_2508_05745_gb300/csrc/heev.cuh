@@ -43,7 +43,8 @@ __device__ __forceinline__ int sturm_greater(const R* d, const R* e2, int n, R x
   if (fabs(q) < pivmin) q = -pivmin;
   neg += (q < 0);
   for (int i = 1; i < n; ++i) {
-    q = (d[i] - x) - e2[i - 1] / q;
+    // c64: fast reciprocal-based divide (|q| >= pivmin keeps it in range)
+    q = (d[i] - x) - (sizeof(R) == 4 ? (R)__fdividef((float)e2[i - 1], (float)q) : e2[i - 1] / q);
     if (fabs(q) < pivmin) q = -pivmin;
     neg += (q < 0);
   }
@@ -106,11 +107,14 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
   // one tiled rank-2 j0 update brings the trailing block G[j0:, j0:] up to
   // date; its lower triangle is then packed into shared memory and the
   // remaining steps stay on chip.  V and W (j0 x n each, row k = step k) live
-  // in ws2, which receives the eigenvectors only at the end.
+  // in shared memory when they fit, else in ws2 (which receives the
+  // eigenvectors only at the end).
   int j0 = 0;
   while ((n - j0) * (n - j0 + 1) / 2 > HeevSmem<R>::kCap) ++j0;
-  cpx<R>* Vp = U;
-  cpx<R>* Wp = U + (int64_t)j0 * n;
+  // V and W sit in shared memory (unused until the packing) when they fit
+  const bool vw_sm = 2 * (size_t)j0 * n * sizeof(cpx<R>) <= (size_t)HeevSmem<R>::kBytes;
+  cpx<R>* Vp = vw_sm ? Lp : U;
+  cpx<R>* Wp = Vp + (int64_t)j0 * n;
   for (int j = 0; j < j0 && j + 2 < n; ++j) {
     const int m = n - j - 1;
     // column j of G_eff below the diagonal, and its diagonal entry
@@ -164,14 +168,35 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
       acc.im = warp_sum(acc.im);
       if (lane == 0) cc[kk] = acc;
     }
-    // y = G_sub v from the original (read-only) G, one warp per row
-    for (int r = warp; r < m; r += nwarp) {
-      const cpx<R>* row = G + (int64_t)(j + 1 + r) * n + (j + 1);
-      cpx<R> acc = mk<R>(0, 0);
-      for (int c = lane; c < m; c += 32) cfma(acc, row[c], sv[c]);
-      acc.re = warp_sum(acc.re);
-      acc.im = warp_sum(acc.im);
-      if (lane == 0) sw[r] = acc;
+    // y = G_sub v from the original (read-only) G: four rows per warp in
+    // flight, their eight partial sums reduced by one butterfly
+    for (int r0 = 4 * warp; r0 < m; r0 += 4 * nwarp) {
+      const int nq = min(4, m - r0);
+      const cpx<R>* row = G + (int64_t)(j + 1 + r0) * n + (j + 1);
+      cpx<R> acc[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[q] = mk<R>(0, 0);
+      for (int c = lane; c < m; c += 32) {
+        const cpx<R> x = sv[c];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (q < nq) cfma(acc[q], row[(int64_t)q * n + c], x);
+      }
+      R d[8];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        d[2 * q] = acc[q].re;
+        d[2 * q + 1] = acc[q].im;
+      }
+      const R tot = warp_reduce_scatter<8>(d, lane);
+      if ((lane & 3) == 0) {
+        const int e = Scatter<8>::index(lane);
+        const int r = r0 + (e >> 1);
+        if (r < m) {
+          if (e & 1) sw[r].im = tot;
+          else sw[r].re = tot;
+        }
+      }
     }
     __syncthreads();
     // y -= sum_k v_k (w_k^dagger v) + w_k (v_k^dagger v)
@@ -195,18 +220,22 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
     // (lower triangle only).  V and W are staged in shared memory in chunks
     // of kch steps; 64 x 64 output tiles, each of the 512 threads (32 x 16)
     // owns rows ty + 16 r and columns tx + 32 c of a tile.
+    // (With V and W already in shared memory they are used in place.)
     const int mt = n - j0;
-    const int kch = min(j0, (int)(HeevSmem<R>::kBytes / (2 * (size_t)mt * sizeof(cpx<R>))));
-    cpx<R>* Vs = Lp;
-    cpx<R>* Ws = Lp + (int64_t)kch * mt;
+    const int kch = vw_sm ? j0 : min(j0, (int)(HeevSmem<R>::kBytes / (2 * (size_t)mt * sizeof(cpx<R>))));
+    const int ldk = vw_sm ? n : mt;
+    const cpx<R>* Vs = vw_sm ? Vp + j0 : Lp;
+    const cpx<R>* Ws = vw_sm ? Wp + j0 : Lp + (int64_t)kch * mt;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     const int ntile = (mt + 63) / 64;
     for (int k0 = 0; k0 < j0; k0 += kch) {
       const int kc = min(kch, j0 - k0);
-      for (int e = threadIdx.x; e < kc * mt; e += blockDim.x) {
-        const int kk = e / mt, i = e - kk * mt;
-        Vs[e] = Vp[(int64_t)(k0 + kk) * n + j0 + i];
-        Ws[e] = Wp[(int64_t)(k0 + kk) * n + j0 + i];
+      if (!vw_sm) {
+        for (int e = threadIdx.x; e < kc * mt; e += blockDim.x) {
+          const int kk = e / mt, i = e - kk * mt;
+          Lp[e] = Vp[(int64_t)(k0 + kk) * n + j0 + i];
+          Lp[(int64_t)kch * mt + e] = Wp[(int64_t)(k0 + kk) * n + j0 + i];
+        }
       }
       __syncthreads();
       for (int ti = 0; ti < ntile; ++ti)
@@ -221,14 +250,14 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
               const int i = ti * 64 + ty + 16 * r;
-              va[r] = i < mt ? Vs[kk * mt + i] : mk<R>(0, 0);
-              wa[r] = i < mt ? Ws[kk * mt + i] : mk<R>(0, 0);
+              va[r] = i < mt ? Vs[kk * ldk + i] : mk<R>(0, 0);
+              wa[r] = i < mt ? Ws[kk * ldk + i] : mk<R>(0, 0);
             }
 #pragma unroll
             for (int c = 0; c < 2; ++c) {
               const int i = tc * 64 + tx + 32 * c;
-              vb[c] = i < mt ? Vs[kk * mt + i] : mk<R>(0, 0);
-              wb[c] = i < mt ? Ws[kk * mt + i] : mk<R>(0, 0);
+              vb[c] = i < mt ? Vs[kk * ldk + i] : mk<R>(0, 0);
+              wb[c] = i < mt ? Ws[kk * ldk + i] : mk<R>(0, 0);
             }
 #pragma unroll
             for (int r = 0; r < 4; ++r)
@@ -260,10 +289,9 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
   // The rank-2 update of each step is applied lazily: Lp holds the trailing
   // block without the update of the previous step, whose v and y (so that
   // w = 2 y - 2 (v^dagger y) v) sit in ping-pong buffers indexed by local row.
-  // A step reads its column with that correction, then one row pass (warp
-  // per row, lanes over columns) writes the corrected entries back and forms
-  // the lower-triangle half of y = A v, and one tile pass (32 x 32 tiles,
-  // lane per column) adds the strictly-upper half; four barriers per step.
+  // A step reads its column with that correction, then a row pass writes the
+  // corrected entries back and forms the lower-triangle half of y = A v, and
+  // a tile pass adds the strictly-upper half; four barriers per step.
   __shared__ cpx<R> sy2[256];
   __shared__ R redn[32], reds[32];
   for (int i = threadIdx.x; i < M0; i += blockDim.x) {
@@ -309,6 +337,7 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
     }
     if (i < m) {
       vN[jl + 1 + i] = vi;
+      yN[jl + 1 + i] = mk<R>(0, 0);
       Hv[(int64_t)j * n + (j + 1 + i)] = vi;
     }
     if (i <= j) Hv[(int64_t)j * n + i] = mk<R>(0, 0);
@@ -317,74 +346,69 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
       sec[j] = alpha;
     }
     __syncthreads();
-    // row pass: apply the previous update to rows jl+1.. (c <= r), y_lower
+    // Both passes run over 32 x 16 half-tiles of the trailing triangle,
+    // aligned to multiples of 32 in local row/column index.
+    // Row pass (lane = row): applies the previous update to A[r][c], c <= r,
+    // writes it back and accumulates y_lower in registers.  A half-warp reads
+    // 16 rows starting at a multiple of 16, whose triangular offsets
+    // r (r + 1) / 2 are distinct mod 16, so the reads are conflict-free.
+    // Tile pass (lane = column): y[c] += conj(A[r][c]) v[r] for r > c, over
+    // contiguous entries.  Each half-tile ends in one atomic add per lane.
+    const int tb0 = (jl + 1) >> 5;
+    const int ntb = ((M0 - 1) >> 5) - tb0 + 1;
+    const int nun = ntb * (ntb + 1);            // 2 halves per tile
     R ssp = 0;
-    {
-      constexpr int PT = 8;                     // column slots per lane (m <= 255)
-      constexpr bool kCache = sizeof(R) == 4;   // column values kept in registers (c64)
-      cpx<R> vc[kCache ? PT : 1], wc[kCache ? PT : 1], nc[kCache ? PT : 1];
-      if (kCache) {
-#pragma unroll
-        for (int t = 0; t < (kCache ? PT : 1); ++t) {
-          const int c = lane + 32 * t;
-          const bool in = c < m;
-          const int C = jl + 1 + c;
-          vc[t] = in ? vP[C] : mk<R>(0, 0);
-          wc[t] = in ? wprev(C) : mk<R>(0, 0);
-          nc[t] = in ? vN[C] : mk<R>(0, 0);
+    for (int u = warp; u < nun; u += nwarp) {
+      const int tl = u >> 1, hf = u & 1;
+      int I = 0;
+      while ((I + 1) * (I + 2) / 2 <= tl) ++I;
+      const int J = tl - I * (I + 1) / 2;
+      const int Rr = 32 * (tb0 + I) + lane;
+      const bool rin = Rr > jl && Rr < M0;
+      const int cbeg = max(32 * (tb0 + J) + 16 * hf, jl + 1);
+      const int cend = min(min(32 * (tb0 + J) + 16 * hf + 16, M0), 32 * (tb0 + I) + 32);
+      cpx<R> vr = mk<R>(0, 0), wr = mk<R>(0, 0);
+      if (rin) {
+        vr = vP[Rr];
+        wr = wprev(Rr);
+      }
+      cpx<R>* rowp = Lp + (rin ? pidx(Rr, 0) : 0);
+      cpx<R> acc = mk<R>(0, 0);
+#pragma unroll 4
+      for (int C = cbeg; C < cend; ++C) {
+        const cpx<R> cv = vP[C], cw = wprev(C), cn = vN[C];
+        if (rin && C <= Rr) {
+          const cpx<R> aa = rowp[C] - vr * conj(cw) - wr * conj(cv);
+          rowp[C] = aa;
+          cfma(acc, aa, cn);
         }
       }
-      for (int r = warp; r < m; r += nwarp) {
-        const int Rr = jl + 1 + r;
-        const cpx<R> vr = vP[Rr], wr = wprev(Rr);
-        cpx<R>* row = Lp + pidx(Rr, jl + 1);
-        cpx<R> acc = mk<R>(0, 0);
-#pragma unroll
-        for (int t = 0; t < PT; ++t) {
-          if (32 * t <= r) {
-            const int c = lane + 32 * t;
-            if (c <= r) {
-              cpx<R> cv, cw, cn;
-              if (kCache) {
-                cv = vc[kCache ? t : 0]; cw = wc[kCache ? t : 0]; cn = nc[kCache ? t : 0];
-              } else {
-                const int C = jl + 1 + c;
-                cv = vP[C]; cw = wprev(C); cn = vN[C];
-              }
-              const cpx<R> aa = row[c] - vr * conj(cw) - wr * conj(cv);
-              row[c] = aa;
-              cfma(acc, aa, cn);
-            }
-          }
-        }
-        acc.re = warp_sum(acc.re);
-        acc.im = warp_sum(acc.im);
-        if (lane == 0) {
-          yN[Rr] = acc;
-          ssp += cdot(vN[Rr], acc).re;
-        }
+      if (rin && cbeg <= Rr && cbeg < cend) {
+        atomicAdd(&yN[Rr].re, acc.re);
+        atomicAdd(&yN[Rr].im, acc.im);
+        ssp += cdot(vN[Rr], acc).re;
       }
     }
     __syncthreads();
-    // tile pass: y[c] += sum_{r > c} conj(A[r][c]) v[r], lanes over columns
-    {
-      const int nbk = (m + 31) >> 5;
-      const int ntl = nbk * (nbk + 1) / 2;
-      for (int tl = warp; tl < ntl; tl += nwarp) {
-        int I = 0;
-        while ((I + 1) * (I + 2) / 2 <= tl) ++I;
-        const int J = tl - I * (I + 1) / 2;
-        const int c = 32 * J + lane;
-        const int C = jl + 1 + c;
-        cpx<R> acc = mk<R>(0, 0);
-        const int r1 = min(32 * I + 32, m);
-        for (int r = 32 * I; r < r1; ++r)
-          if (r > c) cfmac(acc, Lp[pidx(jl + 1 + r, C)], vN[jl + 1 + r]);
-        if (c < m) {
-          atomicAdd(&yN[C].re, acc.re);
-          atomicAdd(&yN[C].im, acc.im);
-          ssp += cdot(vN[C], acc).re;
-        }
+    for (int u = warp; u < nun; u += nwarp) {
+      const int tl = u >> 1, hf = u & 1;
+      int I = 0;
+      while ((I + 1) * (I + 2) / 2 <= tl) ++I;
+      const int J = tl - I * (I + 1) / 2;
+      const int C = 32 * (tb0 + J) + lane;
+      const bool cin = C > jl && C < M0;
+      const int rbeg = max(32 * (tb0 + I) + 16 * hf, jl + 1);
+      const int rend = min(32 * (tb0 + I) + 16 * hf + 16, M0);
+      cpx<R> acc = mk<R>(0, 0);
+#pragma unroll 4
+      for (int Rr = rbeg; Rr < rend; ++Rr) {
+        const cpx<R> vrr = vN[Rr];
+        if (cin && Rr > C) cfmac(acc, Lp[pidx(Rr, C)], vrr);
+      }
+      if (cin && rend - 1 > C) {
+        atomicAdd(&yN[C].re, acc.re);
+        atomicAdd(&yN[C].im, acc.im);
+        ssp += cdot(vN[C], acc).re;
       }
     }
     ssp = warp_sum(ssp);
@@ -442,16 +466,38 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
   __syncthreads();
   const int keep = s_keep;
   double* ev = s.evals + t * (2 * s.chi);
-  for (int k = threadIdx.x; k < keep; k += blockDim.x) {
-    // k-th largest: smallest x with sturm_greater(x) <= k
-    R lo = gl, hi = gu;
-    for (int it = 0; it < 200; ++it) {
-      R mid = (R)0.5 * (lo + hi);
-      if (hi - lo <= eps * (fabs(lo) + fabs(hi)) + (R)1e-3 * eps * tnorm + pivmin || mid <= lo || mid >= hi) break;
-      if (sturm_greater<R>(sd, se2, n, mid, pivmin) > k) lo = mid;
-      else hi = mid;
+  {
+    // Multisection: G lanes of a warp share eigenvalue k and evaluate the
+    // Sturm count at G interior points of its interval, which shrinks by
+    // G + 1 per round (G = 4 when 128 eigenvalues are kept on 512 threads).
+    int G = 1;
+    while (G < 32 && keep * (2 * G) <= (int)blockDim.x) G *= 2;
+    const int per_warp = 32 / G;
+    const int gi = lane & (G - 1);
+    const unsigned gmask = (G == 32) ? 0xffffffffu : ((1u << G) - 1u);
+    for (int kb = 0; kb < keep; kb += nwarp * per_warp) {
+      const int k = kb + warp * per_warp + lane / G;
+      R lo = gl, hi = gu;
+      bool done = k >= keep;
+      for (int it = 0; it < 200; ++it) {
+        const R h = (hi - lo) / (R)(G + 1);
+        if (hi - lo <= eps * (fabs(lo) + fabs(hi)) + (R)1e-3 * eps * tnorm + pivmin || !(lo + h > lo) ||
+            !(hi - h < hi))
+          done = true;
+        if (__all_sync(0xffffffffu, done)) break;
+        const R x = lo + h * (R)(gi + 1);
+        const bool above = !done && sturm_greater<R>(sd, se2, n, x, pivmin) > k;
+        const unsigned grp = (__ballot_sync(0xffffffffu, above) >> (lane & ~(G - 1))) & gmask;
+        const int pcount = __popc(grp);   // interior points below eigenvalue k
+        if (!done) {
+          const R nlo = (pcount > 0) ? lo + h * (R)pcount : lo;
+          const R nhi = (pcount < G) ? lo + h * (R)(pcount + 1) : hi;
+          lo = nlo;
+          hi = nhi;
+        }
+      }
+      if (k < keep && gi == 0) ev[k] = (double)((R)0.5 * (lo + hi));
     }
-    ev[k] = (double)((R)0.5 * (lo + hi));
   }
   if (threadIdx.x == 0) {
     s.kept[t] = keep;
@@ -762,34 +808,10 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
               }
             }
           }
-          // reduce-scatter: after log2(NV) halving rounds lane holds the
-          // partial of value idx(lane); then full sums over the other lanes
-          constexpr int LG = NV == 8 ? 3 : (NV == 4 ? 2 : 1);
-#pragma unroll
-          for (int r = 0; r < LG; ++r) {
-            const int s = 16 >> r;
-            const int h = NV >> (r + 1);
-            const bool up = (lane & s) != 0;
-#pragma unroll
-            for (int k = 0; k < h; ++k) {
-              const R send = up ? d[k] : d[k + h];
-              const R keepv = up ? d[k + h] : d[k];
-              d[k] = keepv + __shfl_xor_sync(0xffffffffu, send, s);
-            }
-          }
-          R tot = d[0];
-#pragma unroll
-          for (int r = LG; r < 5; ++r) tot += __shfl_xor_sync(0xffffffffu, tot, 16 >> r);
+          const R tot = warp_reduce_scatter<NV>(d, lane);
           R dd[NV];
 #pragma unroll
-          for (int e = 0; e < NV; ++e) {
-            // lane holding value e: bits (4, 3, ...) of the lane spell e from the top
-            int src = 0;
-#pragma unroll
-            for (int r = 0; r < LG; ++r)
-              if (e & (1 << (LG - 1 - r))) src |= 16 >> r;
-            dd[e] = (R)2 * __shfl_sync(0xffffffffu, tot, src);
-          }
+          for (int e = 0; e < NV; ++e) dd[e] = (R)2 * __shfl_sync(0xffffffffu, tot, Scatter<NV>::source(e));
 #pragma unroll
           for (int a = 0; a < PER; ++a) {
             if (a >= a0 && a < nper) {
