@@ -35,20 +35,48 @@ __device__ __forceinline__ void cta_gemm(int M, int N, int K, FA loadA, FB loadB
       for (int r = 0; r < 4; ++r)
 #pragma unroll
         for (int c = 0; c < 4; ++c) acc[r][c] = mk<R>(0, 0);
-      for (int k0 = 0; k0 < K; k0 += kGemmBK) {
-        for (int e = tid; e < kGemmBM * kGemmBK; e += kGemmThreads) {
+      // the next K slab is loaded into registers while the current one is
+      // multiplied out of shared memory
+      constexpr int LA = kGemmBM * kGemmBK / kGemmThreads, LB = kGemmBK * kGemmBN / kGemmThreads;
+      cpx<R> ra[LA], rb[LB];
+      auto fetch = [&](int k0) {
+#pragma unroll
+        for (int q = 0; q < LA; ++q) {
+          const int e = tid + q * kGemmThreads;
           int i, k;
           if (A_KFAST) { i = e / kGemmBK; k = e % kGemmBK; }
           else { k = e / kGemmBM; i = e % kGemmBM; }
-          sm.a[k][i] = (i0 + i < M && k0 + k < K) ? loadA(i0 + i, k0 + k) : mk<R>(0, 0);
+          ra[q] = (i0 + i < M && k0 + k < K) ? loadA(i0 + i, k0 + k) : mk<R>(0, 0);
         }
-        for (int e = tid; e < kGemmBK * kGemmBN; e += kGemmThreads) {
+#pragma unroll
+        for (int q = 0; q < LB; ++q) {
+          const int e = tid + q * kGemmThreads;
           int k, j;
           if (B_KFAST) { j = e / kGemmBK; k = e % kGemmBK; }
           else { k = e / kGemmBN; j = e % kGemmBN; }
-          sm.b[k][j] = (j0 + j < N && k0 + k < K) ? loadB(k0 + k, j0 + j) : mk<R>(0, 0);
+          rb[q] = (j0 + j < N && k0 + k < K) ? loadB(k0 + k, j0 + j) : mk<R>(0, 0);
+        }
+      };
+      if (K > 0) fetch(0);
+      for (int k0 = 0; k0 < K; k0 += kGemmBK) {
+#pragma unroll
+        for (int q = 0; q < LA; ++q) {
+          const int e = tid + q * kGemmThreads;
+          int i, k;
+          if (A_KFAST) { i = e / kGemmBK; k = e % kGemmBK; }
+          else { k = e / kGemmBM; i = e % kGemmBM; }
+          sm.a[k][i] = ra[q];
+        }
+#pragma unroll
+        for (int q = 0; q < LB; ++q) {
+          const int e = tid + q * kGemmThreads;
+          int k, j;
+          if (B_KFAST) { j = e / kGemmBK; k = e % kGemmBK; }
+          else { k = e / kGemmBN; j = e % kGemmBN; }
+          sm.b[k][j] = rb[q];
         }
         __syncthreads();
+        if (k0 + kGemmBK < K) fetch(k0 + kGemmBK);
 #pragma unroll
         for (int k = 0; k < kGemmBK; ++k) {
           cpx<R> av[4], bv[4];
