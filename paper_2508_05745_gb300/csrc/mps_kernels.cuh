@@ -324,29 +324,51 @@ __global__ void __launch_bounds__(kGemmThreads) k_contract(SimView<R> s, int q) 
       },
       [&](int i, int j, cpx<R> v) { th[(int64_t)i * ld + j] = v; }, sm);
   __syncthreads();
-  double acc[16][2];
+  // rho12 is Hermitian: the 10 entries i <= j are formed.  Products in the
+  // storage precision, partial sums over 8 entries of Theta in that
+  // precision, accumulated in FP64 (FP64 throughput is ~1/64 of FP32 here).
+  double acc[10][2];
 #pragma unroll
-  for (int i = 0; i < 16; ++i) acc[i][0] = acc[i][1] = 0.0;
-  for (int e = threadIdx.x; e < dl * dr; e += blockDim.x) {
-    const int a = e / dr, b = e % dr;
-    zd v[4];
-    v[0] = cast<double>(th[(int64_t)(2 * a) * ld + b]);
-    v[1] = cast<double>(th[(int64_t)(2 * a) * ld + dr + b]);
-    v[2] = cast<double>(th[(int64_t)(2 * a + 1) * ld + b]);
-    v[3] = cast<double>(th[(int64_t)(2 * a + 1) * ld + dr + b]);
+  for (int p = 0; p < 10; ++p) acc[p][0] = acc[p][1] = 0.0;
+  const int nel = dl * dr;
+  for (int e0 = threadIdx.x; e0 < nel; e0 += 8 * blockDim.x) {
+    R part[10][2];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int p = 0; p < 10; ++p) part[p][0] = part[p][1] = 0;
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + u * blockDim.x;
+      if (e >= nel) break;
+      const int a = e / dr, b = e - a * dr;
+      cpx<R> v[4];
+      v[0] = th[(int64_t)(2 * a) * ld + b];
+      v[1] = th[(int64_t)(2 * a) * ld + dr + b];
+      v[2] = th[(int64_t)(2 * a + 1) * ld + b];
+      v[3] = th[(int64_t)(2 * a + 1) * ld + dr + b];
+      int p = 0;
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        acc[i * 4 + j][0] += v[i].re * v[j].re + v[i].im * v[j].im;
-        acc[i * 4 + j][1] += v[i].im * v[j].re - v[i].re * v[j].im;
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = i; j < 4; ++j, ++p) {
+          part[p][0] += v[i].re * v[j].re + v[i].im * v[j].im;
+          part[p][1] += v[i].im * v[j].re - v[i].re * v[j].im;
+        }
+    }
+#pragma unroll
+    for (int p = 0; p < 10; ++p) {
+      acc[p][0] += (double)part[p][0];
+      acc[p][1] += (double)part[p][1];
+    }
+  }
+  int p = 0;
+  for (int i = 0; i < 4; ++i)
+    for (int j = i; j < 4; ++j, ++p) {
+      double re = block_sum(acc[p][0], red);
+      double im = block_sum(acc[p][1], red);
+      if (threadIdx.x == 0) {
+        s.rho12[t * 16 + i * 4 + j] = mk(re, im);
+        if (j != i) s.rho12[t * 16 + j * 4 + i] = mk(re, -im);
       }
-  }
-  for (int i = 0; i < 16; ++i) {
-    double re = block_sum(acc[i][0], red);
-    double im = block_sum(acc[i][1], red);
-    if (threadIdx.x == 0) s.rho12[t * 16 + i] = mk(re, im);
-  }
+    }
 }
 
 // ---- apply T to Theta and build the Gram matrix ------------------------------
@@ -361,27 +383,30 @@ __global__ void __launch_bounds__(kGemmThreads) k_apply_gram(SimView<R> s, int q
   const int dl = bd[q], dr = bd[q + 2];
   cpx<R>* th = s.ws0 + t * s.ws_stride;
   cpx<R>* G = s.ws1 + t * s.ws_stride;
-  __shared__ zd T[16];
-  if (threadIdx.x < 16) T[threadIdx.x] = s.top[t * 16 + threadIdx.x];
+  // T (FP64 from the unraveling) is applied in the storage precision
+  __shared__ cpx<R> T[16];
+  if (threadIdx.x < 16) T[threadIdx.x] = cast<R>(s.top[t * 16 + threadIdx.x]);
   __syncthreads();
   const int64_t ld = 2 * dr;
   for (int e = threadIdx.x; e < dl * dr; e += blockDim.x) {
-    const int a = e / dr, b = e % dr;
-    zd v[4];
-    v[0] = cast<double>(th[(int64_t)(2 * a) * ld + b]);
-    v[1] = cast<double>(th[(int64_t)(2 * a) * ld + dr + b]);
-    v[2] = cast<double>(th[(int64_t)(2 * a + 1) * ld + b]);
-    v[3] = cast<double>(th[(int64_t)(2 * a + 1) * ld + dr + b]);
-    zd w[4];
+    const int a = e / dr, b = e - a * dr;
+    cpx<R> v[4];
+    v[0] = th[(int64_t)(2 * a) * ld + b];
+    v[1] = th[(int64_t)(2 * a) * ld + dr + b];
+    v[2] = th[(int64_t)(2 * a + 1) * ld + b];
+    v[3] = th[(int64_t)(2 * a + 1) * ld + dr + b];
+    cpx<R> w[4];
+#pragma unroll
     for (int i = 0; i < 4; ++i) {
-      zd acc = mk(0.0, 0.0);
+      cpx<R> acc = mk<R>(0, 0);
+#pragma unroll
       for (int k = 0; k < 4; ++k) cfma(acc, T[i * 4 + k], v[k]);
       w[i] = acc;
     }
-    th[(int64_t)(2 * a) * ld + b] = cast<R>(w[0]);
-    th[(int64_t)(2 * a) * ld + dr + b] = cast<R>(w[1]);
-    th[(int64_t)(2 * a + 1) * ld + b] = cast<R>(w[2]);
-    th[(int64_t)(2 * a + 1) * ld + dr + b] = cast<R>(w[3]);
+    th[(int64_t)(2 * a) * ld + b] = w[0];
+    th[(int64_t)(2 * a) * ld + dr + b] = w[1];
+    th[(int64_t)(2 * a + 1) * ld + b] = w[2];
+    th[(int64_t)(2 * a + 1) * ld + dr + b] = w[3];
   }
   __syncthreads();
   const int ng = side == 0 ? 2 * dl : 2 * dr;
