@@ -60,53 +60,78 @@ __device__ __forceinline__ void spin_flip(const zd* w, zd* out) {
   out[3] = -conj(w[0]);
 }
 
-// Cyclic Jacobi for a real symmetric n x n matrix (row-major, n <= 8).
+// Cyclic Jacobi for a real symmetric N x N matrix (row-major, N <= 8).
 // Returns eigenvalues in w (descending) and eigenvectors as columns of v.
-__device__ inline void jacobi_sym(double* a, double* v, double* w, int n) {
-  for (int i = 0; i < n; ++i)
-    for (int j = 0; j < n; ++j) v[i * n + j] = (i == j) ? 1.0 : 0.0;
+// The size is a template parameter so that the row/column updates unroll
+// into independent loads and FMAs (the matrices live in local memory).
+template <int N>
+__device__ inline void jacobi_sym_n(double* a, double* v, double* w) {
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+#pragma unroll
+    for (int j = 0; j < N; ++j) v[i * N + j] = (i == j) ? 1.0 : 0.0;
   double tot = 0.0;
-  for (int i = 0; i < n * n; ++i) tot += a[i] * a[i];
+#pragma unroll
+  for (int i = 0; i < N * N; ++i) tot += a[i] * a[i];
   const double thresh = 1e-17 * sqrt(tot);  // rotate only |a_pq| above this
   for (int sweep = 0; sweep < 60; ++sweep) {
     bool rotated = false;
-    for (int p = 0; p < n - 1; ++p)
-      for (int q = p + 1; q < n; ++q) {
-        double apq = a[p * n + q];
+    for (int p = 0; p < N - 1; ++p)
+      for (int q = p + 1; q < N; ++q) {
+        double apq = a[p * N + q];
         if (fabs(apq) <= thresh) continue;
         rotated = true;
-        double zeta = (a[q * n + q] - a[p * n + p]) / (2.0 * apq);
+        double zeta = (a[q * N + q] - a[p * N + p]) / (2.0 * apq);
         double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
         double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
-        for (int k = 0; k < n; ++k) {  // columns p, q
-          double akp = a[k * n + p], akq = a[k * n + q];
-          a[k * n + p] = c * akp - s * akq;
-          a[k * n + q] = s * akp + c * akq;
+#pragma unroll
+        for (int k = 0; k < N; ++k) {  // columns p, q
+          double akp = a[k * N + p], akq = a[k * N + q];
+          a[k * N + p] = c * akp - s * akq;
+          a[k * N + q] = s * akp + c * akq;
         }
-        for (int k = 0; k < n; ++k) {  // rows p, q
-          double apk = a[p * n + k], aqk = a[q * n + k];
-          a[p * n + k] = c * apk - s * aqk;
-          a[q * n + k] = s * apk + c * aqk;
+#pragma unroll
+        for (int k = 0; k < N; ++k) {  // rows p, q
+          double apk = a[p * N + k], aqk = a[q * N + k];
+          a[p * N + k] = c * apk - s * aqk;
+          a[q * N + k] = s * apk + c * aqk;
         }
-        for (int k = 0; k < n; ++k) {
-          double vkp = v[k * n + p], vkq = v[k * n + q];
-          v[k * n + p] = c * vkp - s * vkq;
-          v[k * n + q] = s * vkp + c * vkq;
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+          double vkp = v[k * N + p], vkq = v[k * N + q];
+          v[k * N + p] = c * vkp - s * vkq;
+          v[k * N + q] = s * vkp + c * vkq;
         }
       }
     if (!rotated) break;
   }
-  for (int i = 0; i < n; ++i) w[i] = a[i * n + i];
-  for (int i = 0; i < n - 1; ++i) {  // selection sort, descending
+#pragma unroll
+  for (int i = 0; i < N; ++i) w[i] = a[i * N + i];
+  for (int i = 0; i < N - 1; ++i) {  // selection sort, descending
     int best = i;
-    for (int j = i + 1; j < n; ++j)
+    for (int j = i + 1; j < N; ++j)
       if (w[j] > w[best]) best = j;
     if (best != i) {
       double t = w[i]; w[i] = w[best]; w[best] = t;
-      for (int k = 0; k < n; ++k) {
-        double u = v[k * n + i]; v[k * n + i] = v[k * n + best]; v[k * n + best] = u;
+#pragma unroll
+      for (int k = 0; k < N; ++k) {
+        double u = v[k * N + i]; v[k * N + i] = v[k * N + best]; v[k * N + best] = u;
       }
     }
+  }
+}
+
+// n = 2 rank (2, 4, 6, 8) for the Takagi embedding, 4 for M_R.
+__device__ inline void jacobi_sym(double* a, double* v, double* w, int n) {
+  switch (n) {
+    case 1: jacobi_sym_n<1>(a, v, w); break;
+    case 2: jacobi_sym_n<2>(a, v, w); break;
+    case 3: jacobi_sym_n<3>(a, v, w); break;
+    case 4: jacobi_sym_n<4>(a, v, w); break;
+    case 5: jacobi_sym_n<5>(a, v, w); break;
+    case 6: jacobi_sym_n<6>(a, v, w); break;
+    case 7: jacobi_sym_n<7>(a, v, w); break;
+    default: jacobi_sym_n<8>(a, v, w); break;
   }
 }
 
@@ -309,7 +334,9 @@ __device__ __noinline__ bool optimal_unraveling(const zd* rho, const zd* kin, in
   for (int i = 0; i < 16; ++i) fnorm2 += norm2(f[i]);
   for (int sweep = 0; sweep < 40; ++sweep) {
     bool rotated = false;
+#pragma unroll
     for (int p = 0; p < 3; ++p)
+#pragma unroll
       for (int q = p + 1; q < 4; ++q) {
         double al = 0.0, be = 0.0;
         zd g = mk(0.0, 0.0);
