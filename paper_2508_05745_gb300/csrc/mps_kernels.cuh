@@ -106,6 +106,44 @@ __device__ void qr_build_t(QrSmem<R>& sm, int pm, int pb) {
   __syncthreads();
 }
 
+// W[a][c] = sum_i conj(V[a][i]) Y[row0 + i][colbase + c] for a < pb, c < ncc
+// (<= 128): V is the panel in shared memory, Y column-major in global memory.
+// A skinny product (pb <= 16 rows), so instead of 64 x 64 GEMM tiles: slabs
+// of 16 rows of Y are staged in the GEMM scratch (XOR-swizzled so that both
+// the column-wise store and the row-wise read are conflict-free), and thread
+// (c, h) accumulates rows a in [h NB / 2, (h + 1) NB / 2) of column c.
+template <class R>
+__device__ void qr_vdag_y(QrSmem<R>& sm, const cpx<R>* Y, int ldy, int row0, int colbase, int pm, int pb,
+                          int ncc) {
+  constexpr int NB = QrSmem<R>::NB;
+  constexpr int HA = NB / 2;
+  static_assert(sizeof(GemmSmem<R>) >= 16 * 128 * sizeof(cpx<R>), "staging does not fit");
+  cpx<R>* ys = reinterpret_cast<cpx<R>*>(&sm.g);
+  const int c = threadIdx.x & 127, h = threadIdx.x >> 7;   // 256 threads
+  cpx<R> acc[HA];
+#pragma unroll
+  for (int a = 0; a < HA; ++a) acc[a] = mk<R>(0, 0);
+  for (int i0 = 0; i0 < pm; i0 += 16) {
+    for (int e = threadIdx.x; e < 16 * 128; e += blockDim.x) {
+      const int ii = e & 15, cc = e >> 4;
+      ys[ii * 128 + (cc ^ ii)] =
+          (i0 + ii < pm && cc < ncc) ? Y[(int64_t)(colbase + cc) * ldy + row0 + i0 + ii] : mk<R>(0, 0);
+    }
+    __syncthreads();
+    const int ni = min(16, pm - i0);
+    for (int ii = 0; ii < ni; ++ii) {
+      const cpx<R> y = ys[ii * 128 + (c ^ ii)];
+      const cpx<R>* vrow = sm.vs + (h * HA) * pm + i0 + ii;
+#pragma unroll
+      for (int a = 0; a < HA; ++a) cfmac(acc[a], vrow[a * pm], y);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int a = 0; a < HA; ++a)
+    if (h * HA + a < pb && c < ncc) sm.w[(h * HA + a) * 128 + c] = acc[a];
+}
+
 // Q_sub (rows p0.., kq columns) <- (I - V T V^dagger) Q_sub, or with T^dagger
 // when adjoint (the factorization's trailing update on X).
 template <class R>
@@ -115,10 +153,7 @@ __device__ void qr_apply_block(QrSmem<R>& sm, cpx<R>* Y, int ldy, int row0, int 
   for (int c0 = 0; c0 < nc; c0 += 128) {
     const int ncc = min(128, nc - c0);
     // W = V^dagger Y  (pb x ncc)
-    cta_gemm<R, false, false>(
-        pb, ncc, pm, [&](int a, int i) { return conj(sm.vs[a * pm + i]); },
-        [&](int i, int c) { return Y[(int64_t)(col0 + c0 + c) * ldy + row0 + i]; },
-        [&](int a, int c, cpx<R> v) { sm.w[a * 128 + c] = v; }, sm.g);
+    qr_vdag_y(sm, Y, ldy, row0, col0 + c0, pm, pb, ncc);
     __syncthreads();
     // W <- T W  or  T^dagger W  (in place by rows, top-down for T^dagger? use a copy)
     for (int e = threadIdx.x; e < ncc; e += blockDim.x) {
@@ -215,14 +250,16 @@ __device__ void householder_qr(cpx<R>* X, cpx<R>* V, cpx<R>* Qm, int m, int n, i
     }
     __syncthreads();
     qr_build_t(sm, pm, pb);
-    qr_apply_block(sm, Qm, m, p0, 0, pm, pb, kq, false);
+    // columns j < p0 are still e_j here (the later reflectors touch rows >= p0
+    // only), so this block changes columns p0.. alone
+    qr_apply_block(sm, Qm, m, p0, p0, pm, pb, kq - p0, false);
   }
 }
 
 // Move the centre from site k to k+1 (dir = +1, QR of A_k as (2 dl) x dr) or
 // to k-1 (dir = -1, LQ of A_k as dl x (2 dr)).
 template <class R>
-__global__ void __launch_bounds__(kGemmThreads) k_move_center(SimView<R> s, int k, int dir) {
+__global__ void __launch_bounds__(kGemmThreads, sizeof(R) == 4 ? 2 : 1) k_move_center(SimView<R> s, int k, int dir) {
   const int64_t t = blockIdx.x;
   if (t >= s.B) return;
   extern __shared__ __align__(16) unsigned char move_smem[];
