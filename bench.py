@@ -130,17 +130,30 @@ def run_arm(L, torch, w, sizes, precision, args, pre, warm, steps, profile_step=
     """Create one Simulation per system size, pre-evolve, warm up, time `steps`
     layers.  Returns dict with timing, per-kernel profile and the sims."""
     cutoff = 1e-12 if precision == "mixed" else 1e-20
+    # One CUDA stream per system size: the handles are independent, so their
+    # kernels may overlap on the GPU.  The timed region is bracketed on the
+    # launching stream, which every handle's stream joins before the stop event.
     sims = {}
     for n, b in sizes.items():
         if b == 0:
             continue
         sims[n] = L.Simulation(n, args.chi, b, seed=args.seed, precision=precision, cutoff=cutoff,
-                               log_capacity=w["circuits"][n].n_gates)
+                               log_capacity=w["circuits"][n].n_gates, stream=torch.cuda.Stream())
     stream = torch.cuda.current_stream()
 
     def step(l):
         for n, s in sims.items():
             s.apply_layer(w["circuits"][n].layers[l])
+
+    def fork(ev):
+        for s in sims.values():
+            s.stream.wait_event(ev)
+
+    def join():
+        for s in sims.values():
+            e = torch.cuda.Event()
+            e.record(s.stream)
+            stream.wait_event(e)
 
     for l in range(pre + warm):
         step(l)
@@ -148,8 +161,10 @@ def run_arm(L, torch, w, sizes, precision, args, pre, warm, steps, profile_step=
     t0 = l0 = pre + warm
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
+    fork(ev0)
     for l in range(t0, t0 + steps):
         step(l)
+    join()
     ev1.record(stream)
     torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1)
@@ -167,6 +182,7 @@ def run_arm(L, torch, w, sizes, precision, args, pre, warm, steps, profile_step=
                 layer = w["circuits"][n].layers[l]
                 s.apply_layer(layer)
                 h2d += layer.gates.nbytes + layer.kraus.nbytes + layer.left_qubits.nbytes
+            for s in sims.values():
                 g_last = s.gates_applied - 1
                 s.sample_branch(g_last, 1)
                 d2h += 4 * s.B
@@ -176,10 +192,21 @@ def run_arm(L, torch, w, sizes, precision, args, pre, warm, steps, profile_step=
         out.update(e2e_value=upd / el, h2d=h2d // steps, d2h=d2h // steps)
         out["next_layer"] = l1 + steps
     if profile_step:
+        # per-kernel CUDA events; the handles run one after another here so
+        # that no kernel's duration includes another handle's work
         l2 = out["next_layer"]
+        torch.cuda.synchronize()
+        work = {}
+        for n, s in sims.items():
+            _, bonds = s.export_mps(0)
+            for k, v in layer_work(w["circuits"][n].layers[l2].left_qubits, bonds, args.chi).items():
+                work[k] = work.get(k, 0.0) + v * s.B
+        out["profile_work"] = work
         for s in sims.values():
             s.profile(True)
-        step(l2)
+        for n, s in sims.items():
+            s.apply_layer(w["circuits"][n].layers[l2])
+            torch.cuda.synchronize()
         prof = {}
         for s in sims.values():
             for k, (kms, cnt) in s.profile(False, collect=True).items():
@@ -332,7 +359,7 @@ def main():
     prof = mixed["profile"]
     dom = max(prof.items(), key=lambda kv: kv[1][0])
     total_prof = sum(v[0] for v in prof.values())
-    rl = roofline(prof, mixed["profile_updates"], args)
+    rl = roofline(prof, mixed["profile_work"], args)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -363,14 +390,61 @@ def gpu_launches(prof, steps, prof_updates, updates):
     return int(launches * steps)
 
 
-# Algorithmic work per bond update at uniform bond dimension chi, in complex
-# multiply-adds (1 CMAC = 8 real flops): contraction (2chi x chi)(chi x 2chi);
-# Hermitian Gram of a 2chi x 2chi matrix (one triangle); eigensolve:
-# tridiagonalization (4/3) n^3 plus back-transformation n^2 chi with n = 2chi;
-# split: projection U^dagger Theta plus the residual GEMM; centre move:
-# Householder QR of 2chi x chi, Q formation and the triangular merge.
-CMAC_PER_UPDATE = {"contract": 4.0, "gram": 4.0, "eig": 32.0 / 3.0 + 4.0, "split": 8.0,
-                   "move": 2 * (4.0 - 2.0 / 3.0) + 1.0}
+# Algorithmic work, in complex multiply-adds (1 CMAC = 8 real flops), of one
+# layer for one trajectory, per kernel kind, from the bond dimensions b[] of
+# the state before the layer (each split is assumed to grow the bond to
+# min(chi, 2 dl, 2 dr)).  Gate on (q, q+1) with dl, dm, dr = b[q], b[q+1],
+# b[q+2]; n_g = 2 d_s is the Gram side chosen by the next gate, d_o the other:
+#   contract  (2 dl x dm)(dm x 2 dr):                 4 dl dm dr
+#   gram      one triangle of n_g x n_g, K = 2 d_o:   n_g^2 d_o
+#   eig       Hermitian tridiagonalization (2/3) n_g^3, back-transformation
+#             of keep vectors n_g^2 keep
+#   split     U^dagger Theta and the residual:        4 keep n_g d_o
+#   move      per centre move, Householder QR of m x n (m n^2 - n^3 / 3),
+#             explicit Q (m r^2 - r^3 / 3), triangular merge into the
+#             neighbour (r n d_next, half of the r x n by n x 2 d_next product)
+def _qr_work(m, n, d_next):
+    r = min(m, n)
+    return (m * n * n - n ** 3 / 3.0) + (m * r * r - r ** 3 / 3.0) + r * n * d_next
+
+
+def layer_work(left_qubits, bonds, chi):
+    b = [int(x) for x in bonds]
+    nq = len(b) - 1
+    w = {"contract": 0.0, "gram": 0.0, "eig": 0.0, "split": 0.0, "move": 0.0}
+    qs = [int(q) for q in left_qubits]
+    for i, q in enumerate(qs):
+        if i > 0:
+            p = qs[i - 1]
+            if q > p:   # centre at p+1 moves right to q
+                for k in range(p + 1, q):
+                    w["move"] += _qr_work(2 * b[k], b[k + 1], b[min(k + 2, nq)])
+            else:       # centre at p moves left to q+1
+                for k in range(p, q + 1, -1):
+                    w["move"] += _qr_work(2 * b[k + 1], b[k], b[max(k - 1, 0)])
+        dl, dm, dr = b[q], b[q + 1], b[q + 2]
+        right = (qs[i + 1] > q) if i + 1 < len(qs) else (i == 0 or qs[i - 1] < q)
+        ds, do = (dl, dr) if right else (dr, dl)
+        ng = 2 * ds
+        keep = min(chi, 2 * dl, 2 * dr)
+        w["contract"] += 4.0 * dl * dm * dr
+        w["gram"] += ng * ng * do
+        w["eig"] += (2.0 / 3.0) * ng ** 3 + ng * ng * keep
+        w["split"] += 4.0 * keep * ng * do
+        b[q + 1] = keep
+    return w
+
+
+# DRAM bytes (read + write) of one ncu capture of the kernel as it is now
+# (profiles/<kernel>_chi128_n48_b152.md); remove an entry when its kernel changes.
+NCU_TRAFFIC = {
+    "eig": {"bytes": 236.5e6,
+            "note": "one k_heev launch at the n_Gram=256 gate (gate 12 of layer 8), 152 trajectories: 1.55 MB per "
+                    "trajectory against ~1.5 MB of algorithmic bytes (G read, reflectors written and read back, U "
+                    "written); bench launches mix gate sizes, so this is the full-size launch, not the average"},
+    "move": {"bytes": 340.1e6,
+             "note": "one k_move_center launch (256 x 128 QR), 152 trajectories: 2.24 MB per trajectory"},
+}
 
 
 def fp32_peak_tflops():
@@ -382,26 +456,29 @@ def fp32_peak_tflops():
     return 152 * 128 * 2 * sm_max * 1e6 / 1e12
 
 
-def roofline(prof, prof_updates, args, fp64=False):
-    """Per kernel kind: achieved TFLOP/s on the algorithmic work of one profiled
-    step (units = bond updates of that step, chi = chi_max) over the summed
-    CUDA-event time of its launches; the dominant kind is reported."""
-    chi = args.chi
+def roofline(prof, work, args, fp64=False):
+    """Per kernel kind: achieved TFLOP/s = algorithmic flops of the profiled
+    layer (layer_work over every trajectory, from the actual bond dimensions)
+    / the summed CUDA-event time of that kind's launches; the dominant kind is
+    reported."""
     peak = fp32_peak_tflops() / (64.0 if fp64 else 1.0)
     rows = {}
     for kind, (ms, cnt) in prof.items():
-        if kind not in CMAC_PER_UPDATE or ms <= 0:
+        if kind not in work or ms <= 0:
             continue
-        flops = CMAC_PER_UPDATE[kind] * 8.0 * chi ** 3 * prof_updates
+        flops = 8.0 * work[kind]
         ach = flops / (ms / 1000.0) / 1e12
-        rows[kind] = {"ms": ms, "launches": cnt, "avg_launch_ms": ms / max(cnt, 1), "achieved_tflops": ach,
-                      "frac": ach / peak}
+        rows[kind] = {"ms": ms, "launches": cnt, "avg_launch_ms": ms / max(cnt, 1), "gflop": flops / 1e9,
+                      "achieved_tflops": ach, "frac": ach / peak}
     dom = max(prof.items(), key=lambda kv: kv[1][0])[0]
     r = rows.get(dom, {})
+    cap = NCU_TRAFFIC.get(dom)
     return {"kernel": dom, "bound": "alu", "achieved": r.get("achieved_tflops"), "peak": peak, "unit": "TFLOP/s",
-            "frac": r.get("frac"), "traffic": None, "avg_launch_ms": r.get("avg_launch_ms"),
-            "peak_note": "FP32 SIMT peak derived from 152 SMs x 128 lanes x 2 x max SM clock (MEASURED_PEAKS sm_max_mhz)",
-            "work_note": "algorithmic CMAC per bond update at chi_max: " + json.dumps(CMAC_PER_UPDATE),
+            "frac": r.get("frac"), "traffic": cap["bytes"] if cap else None,
+            "traffic_note": cap["note"] if cap else None, "avg_launch_ms": r.get("avg_launch_ms"),
+            "peak_note": "FP32 SIMT peak derived from 152 SMs x 128 lanes x 2 x max SM clock (MEASURED_PEAKS sm_max_mhz); of derived",
+            "work_note": "algorithmic complex multiply-adds of the profiled layer from the bond dimensions "
+                         "before it (bench.py layer_work), 8 flops each",
             "kernels": rows}
 
 

@@ -84,14 +84,14 @@ __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
-// Sums NV (2, 4 or 8) per-lane values over the warp at once: log2(NV)
+// Sums NV (2, 4, 8, 16 or 32) per-lane values over the warp at once: log2(NV)
 // halving rounds of a reduce-scatter butterfly, then plain rounds over the
-// remaining lane bits.  Returns the total of value scatter_index(lane) (the
-// lane's bits 4, 3, 2 spell it from the most significant bit down); d is
-// clobbered.  Costs NV + 4 - log2(NV) shuffles instead of 5 NV.
+// remaining lane bits.  Returns the total of value Scatter<NV>::index(lane)
+// (the lane's top log2(NV) bits, 4 first, spell it from its most significant
+// bit down; for NV = 32 that is the lane itself); d is clobbered.  Costs NV + 4 - log2(NV) shuffles instead of 5 NV.
 template <int NV>
 struct Scatter {
-  static constexpr int LG = NV == 8 ? 3 : (NV == 4 ? 2 : 1);
+  static constexpr int LG = NV == 32 ? 5 : (NV == 16 ? 4 : (NV == 8 ? 3 : (NV == 4 ? 2 : 1)));
   __device__ __forceinline__ static int index(int lane) {
     int e = 0;
 #pragma unroll

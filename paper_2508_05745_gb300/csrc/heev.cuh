@@ -289,9 +289,9 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
   // The rank-2 update of each step is applied lazily: Lp holds the trailing
   // block without the update of the previous step, whose v and y (so that
   // w = 2 y - 2 (v^dagger y) v) sit in ping-pong buffers indexed by local row.
-  // A step reads its column with that correction, then a row pass writes the
-  // corrected entries back and forms the lower-triangle half of y = A v, and
-  // a tile pass adds the strictly-upper half; four barriers per step.
+  // A step reads its column with that correction and forms v; then one pass
+  // over the trailing triangle writes the corrected entries back and forms
+  // y = A v (both halves); three barriers per step.
   __shared__ cpx<R> sy2[256];
   __shared__ R redn[32], reds[32];
   for (int i = threadIdx.x; i < M0; i += blockDim.x) {
@@ -313,11 +313,12 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
     const cpx<R> vPj = vP[jl], wPj = wprev(jl);
     // column jl below the diagonal (one entry per thread; m < blockDim.x)
     const int i = threadIdx.x;
-    cpx<R> x = mk<R>(0, 0);
+    cpx<R> x = mk<R>(0, 0), wi = mk<R>(0, 0);
     R part = 0;
     if (i < m) {
       const int Rr = jl + 1 + i;
-      x = Lp[pidx(Rr, jl)] - vP[Rr] * conj(wPj) - wprev(Rr) * conj(vPj);
+      wi = wprev(Rr);
+      x = Lp[pidx(Rr, jl)] - vP[Rr] * conj(wPj) - wi * conj(vPj);
       if (i > 0) part = norm2(x);
     }
     const cpx<R> x0 = Lp[pidx(jl + 1, jl)] - vP[jl + 1] * conj(wPj) - wprev(jl + 1) * conj(vPj);
@@ -335,9 +336,12 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
       const R inv = (R)1 / sqrt(sig + (ax0 + nrm) * (ax0 + nrm));
       vi = (i == 0) ? (x0 - alpha) * inv : x * inv;
     }
+    // every thread has read y of the previous step: it now becomes w
+    cpx<R>* wP = const_cast<cpx<R>*>(yP);
     if (i < m) {
       vN[jl + 1 + i] = vi;
       yN[jl + 1 + i] = mk<R>(0, 0);
+      wP[jl + 1 + i] = wi;
       Hv[(int64_t)j * n + (j + 1 + i)] = vi;
     }
     if (i <= j) Hv[(int64_t)j * n + i] = mk<R>(0, 0);
@@ -346,14 +350,14 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
       sec[j] = alpha;
     }
     __syncthreads();
-    // Both passes run over 32 x 16 half-tiles of the trailing triangle,
-    // aligned to multiples of 32 in local row/column index.
-    // Row pass (lane = row): applies the previous update to A[r][c], c <= r,
-    // writes it back and accumulates y_lower in registers.  A half-warp reads
-    // 16 rows starting at a multiple of 16, whose triangular offsets
-    // r (r + 1) / 2 are distinct mod 16, so the reads are conflict-free.
-    // Tile pass (lane = column): y[c] += conj(A[r][c]) v[r] for r > c, over
-    // contiguous entries.  Each half-tile ends in one atomic add per lane.
+    // One pass over 32 x 16 half-tiles of the trailing triangle (aligned to
+    // multiples of 32 in local index), lane = row r.  It applies the previous
+    // update to A[r][c], c <= r, writes it back, accumulates the lower half
+    // y[r] += A[r][c] v[c] in a register and the strictly-upper half
+    // conj(A[r][c]) v[r] per column in 16 registers, which one reduce-scatter
+    // butterfly sums over the rows (lane 2 c + {0, 1} ends with column c).
+    // A half-warp reads 16 rows starting at a multiple of 16, whose
+    // triangular offsets r (r + 1) / 2 are distinct mod 16: conflict-free.
     const int tb0 = (jl + 1) >> 5;
     const int ntb = ((M0 - 1) >> 5) - tb0 + 1;
     const int nun = ntb * (ntb + 1);            // 2 halves per tile
@@ -365,50 +369,49 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
       const int J = tl - I * (I + 1) / 2;
       const int Rr = 32 * (tb0 + I) + lane;
       const bool rin = Rr > jl && Rr < M0;
-      const int cbeg = max(32 * (tb0 + J) + 16 * hf, jl + 1);
-      const int cend = min(min(32 * (tb0 + J) + 16 * hf + 16, M0), 32 * (tb0 + I) + 32);
-      cpx<R> vr = mk<R>(0, 0), wr = mk<R>(0, 0);
+      const int cb = 32 * (tb0 + J) + 16 * hf;
+      cpx<R> vr = mk<R>(0, 0), wr = mk<R>(0, 0), nr = mk<R>(0, 0);
       if (rin) {
         vr = vP[Rr];
-        wr = wprev(Rr);
+        wr = wP[Rr];
+        nr = vN[Rr];
       }
       cpx<R>* rowp = Lp + (rin ? pidx(Rr, 0) : 0);
       cpx<R> acc = mk<R>(0, 0);
-#pragma unroll 4
-      for (int C = cbeg; C < cend; ++C) {
-        const cpx<R> cv = vP[C], cw = wprev(C), cn = vN[C];
-        if (rin && C <= Rr) {
-          const cpx<R> aa = rowp[C] - vr * conj(cw) - wr * conj(cv);
-          rowp[C] = aa;
-          cfma(acc, aa, cn);
+      bool any = false;
+      R d[32];
+#pragma unroll
+      for (int cc = 0; cc < 16; ++cc) {
+        const int C = cb + cc;
+        cpx<R> qv = mk<R>(0, 0);
+        if (C > jl && C < M0) {
+          const cpx<R> cv = vP[C], cw = wP[C], cn = vN[C];
+          if (rin && C <= Rr) {
+            const cpx<R> aa = rowp[C] - vr * conj(cw) - wr * conj(cv);
+            rowp[C] = aa;
+            cfma(acc, aa, cn);
+            any = true;
+            if (C < Rr) cfmac(qv, aa, nr);
+          }
         }
+        d[2 * cc] = qv.re;
+        d[2 * cc + 1] = qv.im;
       }
-      if (rin && cbeg <= Rr && cbeg < cend) {
+      if (any) {
         atomicAdd(&yN[Rr].re, acc.re);
         atomicAdd(&yN[Rr].im, acc.im);
-        ssp += cdot(vN[Rr], acc).re;
+        ssp += cdot(nr, acc).re;
       }
-    }
-    __syncthreads();
-    for (int u = warp; u < nun; u += nwarp) {
-      const int tl = u >> 1, hf = u & 1;
-      int I = 0;
-      while ((I + 1) * (I + 2) / 2 <= tl) ++I;
-      const int J = tl - I * (I + 1) / 2;
-      const int C = 32 * (tb0 + J) + lane;
-      const bool cin = C > jl && C < M0;
-      const int rbeg = max(32 * (tb0 + I) + 16 * hf, jl + 1);
-      const int rend = min(32 * (tb0 + I) + 16 * hf + 16, M0);
-      cpx<R> acc = mk<R>(0, 0);
-#pragma unroll 4
-      for (int Rr = rbeg; Rr < rend; ++Rr) {
-        const cpx<R> vrr = vN[Rr];
-        if (cin && Rr > C) cfmac(acc, Lp[pidx(Rr, C)], vrr);
-      }
-      if (cin && rend - 1 > C) {
-        atomicAdd(&yN[C].re, acc.re);
-        atomicAdd(&yN[C].im, acc.im);
-        ssp += cdot(vN[C], acc).re;
+      const R tot = warp_reduce_scatter<32>(d, lane);
+      const int Cc = cb + (lane >> 1);
+      if (Cc > jl && Cc < M0) {
+        if (lane & 1) {
+          atomicAdd(&yN[Cc].im, tot);
+          ssp += vN[Cc].im * tot;
+        } else {
+          atomicAdd(&yN[Cc].re, tot);
+          ssp += vN[Cc].re * tot;
+        }
       }
     }
     ssp = warp_sum(ssp);
