@@ -27,7 +27,7 @@ from typing import List
 import numpy as np
 
 from . import philox
-from .unravel import optimal_unraveling, unraveling_entropy, von_neumann_entropy
+from .unravel import haar_optimal, optimal_unraveling, unraveling_entropy, von_neumann_entropy
 
 Z = np.diag([1.0, -1.0]).astype(np.complex128)
 
@@ -56,8 +56,15 @@ def sample_index(p: np.ndarray, u: float) -> int:
 
 
 def _choose_kraus(rho_t, kraus, mode):
+    """Kraus set sampled at a noise site: as given, the state's locally
+    entanglement-optimal remix (Sec. IV.B), or the fixed Haar-optimal remix
+    (the Bell state's optimal set, Sec. V.B)."""
     if mode == "given":
         return np.asarray(kraus, np.complex128)
+    if mode == "haar_optimal":
+        return haar_optimal(kraus)
+    if mode != "optimal":
+        raise ValueError(f"unknown unraveling mode {mode!r}")
     return optimal_unraveling(rho_t, kraus)[0]
 
 

@@ -327,6 +327,36 @@ def optimal_unraveling(rho_a: np.ndarray, kraus: np.ndarray):
     return kout, w
 
 
+def haar_optimal(kraus: np.ndarray) -> np.ndarray:
+    """The "Haar Optimal" fixed unraveling (Sec. V.B, near-optimal fixed
+    unraveling for random circuits): the locally entanglement-optimal Kraus set
+    of the Bell state, computed once and used at every site.  The Bell state's
+    target has reduced state I/2, whose effective state is Phi+ (rule R1's
+    degenerate case picks the computational basis).  By the least-unitary
+    corollary (Sec. V.B) the same set minimizes the average unitarity."""
+    return optimal_unraveling(0.5 * np.eye(2, dtype=np.complex128), kraus)[0]
+
+
+def unitarity(k: np.ndarray) -> float:
+    """Unitarity of an operator (Eq. def:operator_unitarity): Shannon entropy,
+    in bits, of its squared singular values normalized by the squared
+    Frobenius norm.  1 for a unitary 2x2 operator, 0 for rank 1; a zero
+    operator has no weight and returns 0."""
+    k = np.asarray(k, dtype=np.complex128)
+    f2 = float(np.sum(np.abs(k) ** 2))
+    if f2 <= 0.0:
+        return 0.0
+    q = np.linalg.svd(k, compute_uv=False) ** 2 / f2
+    q = q[q > 0.0]
+    return float(-np.sum(q * np.log2(q)))
+
+
+def unitarity_av(kraus: np.ndarray) -> float:
+    """Average unitarity of a Kraus set (least-unitary corollary, Sec. V.B):
+    (1/d) sum_i ||K_i||_F^2 unitarity(K_i), d = 2."""
+    return float(sum(np.sum(np.abs(k) ** 2) * unitarity(k) for k in np.asarray(kraus)) / 2.0)
+
+
 def branch_weights(kraus: np.ndarray, rho_a: np.ndarray) -> np.ndarray:
     """p_i = Tr(K_i rho_a K_i^dagger) (Eq. Kraus_to_ensemble)."""
     return np.array([np.trace(k @ rho_a @ k.conj().T).real for k in kraus])

@@ -84,6 +84,26 @@ def dephasing_kraus(p: float) -> np.ndarray:
     return np.stack([math.sqrt(1.0 - 0.5 * p) * PAULI_I, math.sqrt(0.5 * p) * PAULI_Z])
 
 
+def projective_dephasing_kraus(p: float) -> np.ndarray:
+    """"Projective" unraveling of the dephasing channel (appendix on common
+    unravelings): {sqrt(1-p) I, sqrt(p) |0><0|, sqrt(p) |1><1|}."""
+    p0 = np.array([[1.0, 0.0], [0.0, 0.0]], dtype=np.complex128)
+    p1 = np.array([[0.0, 0.0], [0.0, 1.0]], dtype=np.complex128)
+    return np.stack([math.sqrt(1.0 - p) * PAULI_I, math.sqrt(p) * p0, math.sqrt(p) * p1])
+
+
+def projective_depolarizing_kraus(p: float) -> np.ndarray:
+    """"Projective" unraveling of the depolarizing channel (appendix on common
+    unravelings): {sqrt(1-p) I, sqrt(p/2) |a><b| for a, b in {0, 1}} (five
+    operators, |0><0|, |0><1|, |1><0|, |1><1| in that order)."""
+    ops = [math.sqrt(1.0 - p) * PAULI_I]
+    for a, b in ((0, 0), (0, 1), (1, 0), (1, 1)):
+        e = np.zeros((2, 2), dtype=np.complex128)
+        e[a, b] = 1.0
+        ops.append(math.sqrt(0.5 * p) * e)
+    return np.stack(ops)
+
+
 def compose_kraus(second: np.ndarray, first: np.ndarray) -> np.ndarray:
     """Kraus set of the channel 'first, then second': {S_a F_b}."""
     return np.stack([s @ f for s in second for f in first])

@@ -16,19 +16,35 @@ def small():
     return I.workload_small_exact(seed=0)
 
 
-def test_dense_and_mps_agree_without_truncation(small):
+@pytest.mark.parametrize("mode", ["optimal", "haar_optimal"])
+def test_dense_and_mps_agree_without_truncation(small, mode):
     """chi >= 2^{n/2}: the MPS trajectory equals the state-vector trajectory
-    on the same Philox stream (two independent implementations of Alg. 1)."""
+    on the same Philox stream (two independent implementations of Alg. 1),
+    for the adaptive and the fixed Haar-optimal unraveling."""
     c = small["circuit"]
     for tr in range(6):
-        d = T.dense_trajectory(c, tr, 0)
-        m = T.mps_trajectory(c, tr, 0, 16, keep_dense=True)
+        d = T.dense_trajectory(c, tr, 0, mode=mode)
+        m = T.mps_trajectory(c, tr, 0, 16, keep_dense=True, mode=mode)
         assert d.branch == m.branch
         assert abs(abs(np.vdot(d.state, m.state)) - 1.0) < 1e-12
         assert np.allclose(d.p_branch, m.p_branch, atol=1e-12)
         assert np.allclose(d.z, m.z, atol=1e-12) and np.allclose(d.zz, m.zz, atol=1e-12)
         assert abs(d.s_half - m.s_half) < 1e-11
         assert max(m.discarded) < 1e-20 and m.eps_bound == 0.0
+
+
+def test_haar_optimal_trajectories_reproduce_density_matrix(small):
+    """A fixed unraveling is unbiased too: the Haar-optimal mode's trajectory
+    means over 128 trajectories match exact density-matrix evolution (all 15
+    z-scores below 4)."""
+    c = small["circuit"]
+    rho = T.density_evolution(c)
+    zr, zzr = T.density_observables(rho, c.n_qubits)
+    recs = [T.dense_trajectory(c, tr, 0, mode="haar_optimal") for tr in range(128)]
+    mz, sz = T.trajectory_statistics([r.z for r in recs])
+    mzz, szz = T.trajectory_statistics([r.zz for r in recs])
+    z = np.concatenate([(mz - zr) / sz, (mzz - zzr) / szz])
+    assert np.max(np.abs(z)) < 4.0, z
 
 
 @pytest.mark.slow

@@ -304,3 +304,104 @@ def test_haar_sampler_two_design_purity(rng):
         vals.append(np.trace(r @ r).real)
     vals = np.array(vals)
     assert abs(vals.mean() - 4 / 5) < 4 * vals.std() / math.sqrt(vals.size)
+
+
+# --- fixed unravelings: Haar Optimal, least unitary (Sec. V.B) ------------------
+
+HADAMARD = np.array([[1, 1], [1, -1]], dtype=np.complex128) / math.sqrt(2)
+
+
+def remix(kraus, u):
+    """K'_i = sum_j U_ij K_j (Eq. unitarity_kraus, as the table applies it)."""
+    return np.einsum('ij,jab->iab', u, np.asarray(kraus, dtype=np.complex128))
+
+
+# Haar Optimal sets of the paper's table of unravelings: the Orthogonal set
+# rotated by H (dephasing, amplitude damping) or H (x) H (depolarizing).
+TABLE_HAAR_OPTIMAL = {
+    "dephasing": (lambda p: remix(I.dephasing_kraus(p), HADAMARD),
+                  lambda p: U.binary_entropy((1 + math.sqrt((2 - p) * p)) / 2)),
+    "amplitude_damping": (lambda g: remix(I.amplitude_damping_kraus(g), HADAMARD),
+                          lambda g: U.binary_entropy((1 + math.sqrt(g)) / 2)),
+    "depolarizing": (lambda p: remix(I.depolarizing_kraus(p), np.kron(HADAMARD, HADAMARD)),
+                     lambda p: U.binary_entropy((2 + math.sqrt(3) * math.sqrt((4 - 3 * p) * p)) / 4)),
+}
+ORTHOGONAL = {"dephasing": I.dephasing_kraus, "amplitude_damping": I.amplitude_damping_kraus,
+              "depolarizing": I.depolarizing_kraus}
+
+
+def test_unitarity_closed_forms():
+    """Eq. def:operator_unitarity: 1 for a unitary, 0 for rank 1, the binary
+    entropy of the normalized squared singular values otherwise."""
+    assert abs(U.unitarity(np.eye(2)) - 1.0) < 1e-15
+    assert abs(U.unitarity(0.3 * I.PAULI_Y) - 1.0) < 1e-15
+    assert abs(U.unitarity(np.diag([1.0, 0.0])) - 0.0) < 1e-15
+    assert U.unitarity(np.zeros((2, 2))) == 0.0
+    g = 0.37
+    k0 = I.amplitude_damping_kraus(g)[0]
+    q = 1.0 / (2.0 - g)
+    assert abs(U.unitarity(k0) - U.binary_entropy(q) / math.log(2)) < 1e-14
+
+
+def test_average_unitarity_is_bell_entropy_in_bits(rng):
+    """For any Kraus set, (1/2) sum ||K||_F^2 unitarity(K) equals E_av of the
+    Bell state (reduced state I/2) in bits: (K (x) I)|Phi+> has Schmidt
+    coefficients sigma(K) / ||K||_F and branch weight ||K||_F^2 / 2."""
+    for trial in range(20):
+        r = int(rng.integers(1, 6))
+        v = np.linalg.qr(rng.standard_normal((2 * r, 2)) + 1j * rng.standard_normal((2 * r, 2)))[0]
+        kraus = v.reshape(r, 2, 2)                      # random channel: isometry blocks
+        assert np.allclose(sum(k.conj().T @ k for k in kraus), np.eye(2))
+        e_bell = U.unraveling_entropy(kraus, np.eye(2) / 2)
+        assert abs(U.unitarity_av(kraus) - e_bell / math.log(2)) < 1e-12
+
+
+@pytest.mark.parametrize("name", list(TABLE_HAAR_OPTIMAL))
+@pytest.mark.parametrize("param", [0.01, 0.2, 0.5])
+def test_haar_optimal_matches_the_table(name, param):
+    """haar_optimal (the Bell state's optimal remix) and the paper's table set
+    both reach the closed-form E_oF of the Choi state at the Bell input, and
+    have the same (minimal) average unitarity."""
+    table_set, closed = TABLE_HAAR_OPTIMAL[name]
+    k_orth = ORTHOGONAL[name](param)
+    k_ho = U.haar_optimal(k_orth)
+    k_tab = table_set(param)
+    half = np.eye(2) / 2
+    assert abs(U.unraveling_entropy(k_ho, half) - closed(param)) < 1e-9
+    assert abs(U.unraveling_entropy(k_tab, half) - closed(param)) < 1e-9
+    assert abs(U.unitarity_av(k_ho) - U.unitarity_av(k_tab)) < 1e-9
+    # the channel is unchanged
+    rho = rand_rho(np.random.default_rng(7))
+    out = lambda ks: sum(k @ rho @ k.conj().T for k in ks)
+    assert np.allclose(out(k_ho), out(k_orth), atol=1e-13)
+
+
+@pytest.mark.parametrize("name", ["dephasing", "depolarizing", "amplitude_damping", "ad_then_dephasing"])
+def test_haar_optimal_is_least_unitary(name, rng):
+    """Least-unitary corollary: no remix of the Kraus set has a smaller
+    average unitarity than the Haar-optimal one (brute force over Haar
+    unitaries of the padded set)."""
+    kraus = CHANNELS[name][0]
+    r = max(len(kraus), 4)
+    kpad = np.zeros((r, 2, 2), dtype=np.complex128)
+    kpad[:len(kraus)] = kraus
+    best = U.unitarity_av(U.haar_optimal(kraus))
+    for trial in range(300):
+        assert U.unitarity_av(remix(kpad, I.haar_unitary(rng, r))) >= best - 1e-12
+    # Orthogonal and Projective fixed sets are not below it either
+    assert U.unitarity_av(kraus) >= best - 1e-12
+
+
+@pytest.mark.parametrize("p", [0.05, 0.4])
+def test_projective_sets(p):
+    """The Projective sets of the appendix on common unravelings are valid
+    Kraus sets of the same channels, and at the Bell input they sit above the
+    optimum (dephasing: E_av = (1 - p) ln 2, the identity branch alone)."""
+    rho = rand_rho(np.random.default_rng(3))
+    half = np.eye(2) / 2
+    for proj, orth in ((I.projective_dephasing_kraus(p), I.dephasing_kraus(p)),
+                       (I.projective_depolarizing_kraus(p), I.depolarizing_kraus(p))):
+        assert np.allclose(sum(k.conj().T @ k for k in proj), np.eye(2))
+        assert np.allclose(sum(k @ rho @ k.conj().T for k in proj), sum(k @ rho @ k.conj().T for k in orth))
+        assert U.unraveling_entropy(proj, half) >= U.unraveling_entropy(U.haar_optimal(orth), half) - 1e-12
+    assert abs(U.unraveling_entropy(I.projective_dephasing_kraus(p), half) - (1 - p) * math.log(2)) < 1e-12
