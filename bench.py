@@ -43,7 +43,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="lemps", choices=["lemps", "reference"])
-    ap.add_argument("--traj", type=int, default=2048, help="mixed-precision trajectories in the batch")
+    ap.add_argument("--traj", type=int, default=4096, help="mixed-precision trajectories in the batch (one wave)")
     ap.add_argument("--fp64-traj", type=int, default=128, help="FP64 comparator trajectories")
     ap.add_argument("--pre-layers", type=int, default=10, help="untimed layers before warm-up")
     ap.add_argument("--depth", type=int, default=32)

@@ -55,9 +55,19 @@ typedef enum {
 } lemps_precision;
 
 typedef enum {
-  LEMPS_UNRAVEL_OPTIMAL = 0, /* remix each noise site's Kraus set into the
-                                locally entanglement-optimal one (Sec. IV.B) */
-  LEMPS_UNRAVEL_GIVEN = 1    /* sample the Kraus set as given */
+  LEMPS_UNRAVEL_OPTIMAL = 0,  /* remix each noise site's Kraus set into the
+                                 locally entanglement-optimal one (Sec. IV.B) */
+  LEMPS_UNRAVEL_GIVEN = 1,    /* sample the Kraus set as given (fixed
+                                 unravelings such as Orthogonal or Projective,
+                                 Sec. V.A and the appendix on common unravelings) */
+  LEMPS_UNRAVEL_HAAR_OPT = 2  /* "Haar Optimal" fixed unraveling (Sec. V.B,
+                                 near-optimal fixed unraveling for random
+                                 circuits): the Kraus set is remixed once into
+                                 the locally entanglement-optimal set for the
+                                 Bell state (reduced state I/2), which by the
+                                 least-unitary corollary is also the decomposition
+                                 of least average unitarity, and then sampled as
+                                 given at every site */
 } lemps_unravel;
 
 /* Device allocator hook (PyTorch's caching allocator from Python).  NULL
@@ -86,7 +96,10 @@ typedef struct {
   int32_t n_gates;            /* gates of this layer, applied in list order */
   const int32_t* left_qubit;  /* host [n_gates]; gate k acts on (q, q+1), pairs disjoint */
   const double* gates;        /* host [n_gates][4][4] complex */
-  int32_t n_kraus;            /* 1..4 operators of the single-qubit noise channel */
+  int32_t n_kraus;            /* operators of the single-qubit noise channel: 1..4
+                                 for the optimal and Haar-optimal modes, 1..8 for
+                                 LEMPS_UNRAVEL_GIVEN (e.g. the 5-operator
+                                 Projective depolarizing set) */
   const double* kraus;        /* host [n_kraus][2][2] complex, sum K^dagger K = I */
   double coin_p;              /* the channel acts on both gated qubits with this
                                  probability per gate (1 = always) */

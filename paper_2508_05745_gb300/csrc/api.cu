@@ -59,6 +59,8 @@ struct lemps_sim {
   int64_t log_cap = 0;
   zd* layer_buf = nullptr;   // gates + kraus of the current layer
   int64_t layer_cap = 0;     // complex numbers
+  zd* haar = nullptr;        // Haar-optimal mode: [0, 4) rho = I/2, [4, 20) remixed set, [20] E_av
+  std::vector<double> haar_key;  // Kraus set (host) whose remix haar holds
   double* obs = nullptr;     // measure scratch: z [B][n], zz [B][n-1], s_half [B], eps_bound [B]
   double* stats = nullptr;   // reductions
   int64_t gates_done = 0;
@@ -199,6 +201,25 @@ lemps_status apply_layer_t(lemps_sim* h, const lemps_layer* L) {
   zd* kraus_d = h->layer_buf + 16 * (int64_t)ng;
   if (cudaMemcpyAsync(kraus_d, L->kraus, sizeof(zd) * 4 * L->n_kraus, cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
     return check_cuda(h, "apply_layer copy");
+  const zd* kset_d = kraus_d;
+  int kset_r = L->n_kraus;
+  int kmode = h->cfg.unravel_mode;
+  if (kmode == LEMPS_UNRAVEL_HAAR_OPT) {
+    // Remix the channel's Kraus set once for the Bell state (reduced state
+    // I/2); every site then samples the remixed set as given.  The remix is
+    // recomputed only when the layer's Kraus set changes.
+    std::vector<double> key(L->kraus, L->kraus + 8 * L->n_kraus);
+    if (key != h->haar_key) {
+      h->timed(LEMPS_K_UNRAVEL, [&] {
+        launch_unravel_batch(h->haar, kraus_d, L->n_kraus, 1, h->haar + 4, reinterpret_cast<double*>(h->haar + 20),
+                             h->stream);
+      });
+      h->haar_key.swap(key);
+    }
+    kset_d = h->haar + 4;
+    kset_r = 4;
+    kmode = LEMPS_UNRAVEL_GIVEN;
+  }
   const unsigned grid_t = (unsigned)((h->B + kThreads - 1) / kThreads);
   SimView<R> sv = h->view<R>();
   for (int g = 0; g < ng; ++g) {
@@ -208,10 +229,10 @@ lemps_status apply_layer_t(lemps_sim* h, const lemps_layer* L) {
     h->timed(LEMPS_K_CONTRACT, [&] { k_contract<R><<<(unsigned)h->B, kThreads, 0, h->stream>>>(sv, q); });
     LayerDev ld;
     ld.gates = h->layer_buf;
-    ld.kraus = kraus_d;
-    ld.r = L->n_kraus;
+    ld.kraus = kset_d;
+    ld.r = kset_r;
     ld.coin_p = L->coin_p;
-    ld.mode = h->cfg.unravel_mode;
+    ld.mode = kmode;
     ld.seed = h->cfg.seed;
     ld.traj_offset = h->cfg.traj_offset;
     ld.gate_global = h->gates_done + g;
@@ -337,7 +358,8 @@ lemps_status sim_create(const lemps_config* cfg, lemps_handle* out) {
   if (cfg->chi_max < 1 || cfg->chi_max > 128) return fail(LEMPS_EINVAL, "sim_create: chi_max must be in 1..128");
   if (cfg->n_traj < 1) return fail(LEMPS_EINVAL, "sim_create: n_traj must be positive");
   if (cfg->precision != LEMPS_FP64 && cfg->precision != LEMPS_MIXED) return fail(LEMPS_EINVAL, "sim_create: bad precision");
-  if (cfg->unravel_mode != LEMPS_UNRAVEL_OPTIMAL && cfg->unravel_mode != LEMPS_UNRAVEL_GIVEN)
+  if (cfg->unravel_mode != LEMPS_UNRAVEL_OPTIMAL && cfg->unravel_mode != LEMPS_UNRAVEL_GIVEN &&
+      cfg->unravel_mode != LEMPS_UNRAVEL_HAAR_OPT)
     return fail(LEMPS_EINVAL, "sim_create: bad unravel_mode");
   if (!(cfg->trunc_cutoff >= 0.0) || !(cfg->eps_max >= 2.0)) return fail(LEMPS_EINVAL, "sim_create: bad cutoff or eps_max");
   if ((cfg->alloc == nullptr) != (cfg->free == nullptr)) return fail(LEMPS_EINVAL, "sim_create: alloc and free go together");
@@ -364,7 +386,7 @@ lemps_status sim_create(const lemps_config* cfg, lemps_handle* out) {
   }
   h->ws_stride = (int64_t)(2 * h->chi) * (2 * h->chi);
   h->log_cap = cfg->log_capacity > 0 ? cfg->log_capacity : 0;
-  h->layer_cap = (int64_t)(n / 2 + 1) * 16 + 16;
+  h->layer_cap = (int64_t)(n / 2 + 1) * 16 + 4 * kMaxKraus;
   bool ok = true;
   auto A = [&](size_t bytes) {
     void* p = h->dalloc(bytes);
@@ -387,6 +409,7 @@ lemps_status sim_create(const lemps_config* cfg, lemps_handle* out) {
   h->trace = (double*)A(sizeof(double) * h->B);
   h->blog = (int8_t*)A(std::max<int64_t>(1, h->log_cap * 2 * h->B));
   h->layer_buf = (zd*)A(sizeof(zd) * h->layer_cap);
+  h->haar = (zd*)A(sizeof(zd) * 21);
   h->obs = (double*)A(sizeof(double) * h->B * (2 * n + 1));
   h->stats = (double*)A(sizeof(double) * (4 * n + 4));
   if (!ok) {
@@ -398,6 +421,11 @@ lemps_status sim_create(const lemps_config* cfg, lemps_handle* out) {
   if (h->log_cap > 0) cudaMemsetAsync(h->blog, 0xff, h->log_cap * 2 * h->B, h->stream);
   cudaMemcpyAsync(h->site_off, h->off_h.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice, h->stream);
   cudaMemcpyAsync(h->cap, h->cap_h.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice, h->stream);
+  {
+    // the Bell state's reduced state, input of the Haar-optimal remix
+    static const zd kHalfIdentity[4] = {{0.5, 0.0}, {0.0, 0.0}, {0.0, 0.0}, {0.5, 0.0}};
+    cudaMemcpyAsync(h->haar, kHalfIdentity, sizeof(kHalfIdentity), cudaMemcpyHostToDevice, h->stream);
+  }
   if (h->prec == LEMPS_FP64) k_init_state<double><<<(unsigned)h->B, 64, 0, h->stream>>>(h->view<double>());
   else k_init_state<float><<<(unsigned)h->B, 64, 0, h->stream>>>(h->view<float>());
   lemps_status st = check_cuda(h, "sim_create");
@@ -417,7 +445,9 @@ lemps_status apply_layer(lemps_handle h, const lemps_layer* layer) {
   if (h->sticky) return fail(LEMPS_ECUDA, "apply_layer: handle has a sticky CUDA error");
   if (layer->n_gates < 0 || (layer->n_gates > 0 && (!layer->left_qubit || !layer->gates)) || !layer->kraus)
     return fail(LEMPS_EINVAL, "apply_layer: bad layer arrays");
-  if (layer->n_kraus < 1 || layer->n_kraus > 4) return fail(LEMPS_EINVAL, "apply_layer: n_kraus must be 1..4");
+  const int max_kraus = (h->cfg.unravel_mode == LEMPS_UNRAVEL_GIVEN) ? kMaxKraus : 4;
+  if (layer->n_kraus < 1 || layer->n_kraus > max_kraus)
+    return fail(LEMPS_EINVAL, "apply_layer: n_kraus must be 1..4 (1..8 in the given mode)");
   if (!(layer->coin_p >= 0.0 && layer->coin_p <= 1.0)) return fail(LEMPS_EINVAL, "apply_layer: coin_p outside [0,1]");
   std::vector<char> used(h->n, 0);
   for (int g = 0; g < layer->n_gates; ++g) {

@@ -8,12 +8,15 @@
 
 namespace lemps {
 
+// Operators of a Kraus set sampled as given (the optimal remix takes at most 4).
+constexpr int kMaxKraus = 8;
+
 struct LayerDev {
   const zd* gates;     // [n_gates][16]
   const zd* kraus;     // [r][4]
   int32_t r;
   double coin_p;
-  int32_t mode;        // 0 optimal, 1 given
+  int32_t mode;        // 0 optimal, 1 given (the Haar-optimal mode arrives here as given)
   uint64_t seed;
   int64_t traj_offset;
   int64_t gate_global;  // global index of this gate

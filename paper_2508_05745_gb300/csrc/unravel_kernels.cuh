@@ -31,7 +31,7 @@ __device__ inline void conj4(const zd* m, const zd* rho, zd* out) {
 // (trace 1), sample with u, return the applied single-qubit operator
 // K_i / sqrt(p_i) in op.  Returns the branch index or -2 on numerical failure.
 __device__ __noinline__ int noise_site(const zd* rho_t, const LayerDev& L, double u, zd* op, double* p_out) {
-  zd kset[16];
+  zd kset[4 * kMaxKraus];
   int r = 4;
   if (L.mode == 0) {
     if (!unr::optimal_unraveling(rho_t, L.kraus, L.r, kset)) return -2;
@@ -39,9 +39,9 @@ __device__ __noinline__ int noise_site(const zd* rho_t, const LayerDev& L, doubl
     r = L.r;
     for (int i = 0; i < 4 * r; ++i) kset[i] = L.kraus[i];
   }
-  double p[4];
+  double p[kMaxKraus];
   unr::branch_weights(kset, r, rho_t, p);
-  double cs[4], acc = 0.0;
+  double cs[kMaxKraus], acc = 0.0;
   for (int k = 0; k < r; ++k) {
     if (!isfinite(p[k])) return -2;
     acc += p[k];

@@ -17,7 +17,9 @@ from . import build as _build
 
 LEMPS_OK, LEMPS_EINVAL, LEMPS_ENOMEM, LEMPS_ECUDA, LEMPS_ENUMERIC, LEMPS_ESTATE = range(6)
 LEMPS_FP64, LEMPS_MIXED = 0, 1
-LEMPS_UNRAVEL_OPTIMAL, LEMPS_UNRAVEL_GIVEN = 0, 1
+LEMPS_UNRAVEL_OPTIMAL, LEMPS_UNRAVEL_GIVEN, LEMPS_UNRAVEL_HAAR_OPT = 0, 1, 2
+UNRAVEL_MODES = {"optimal": LEMPS_UNRAVEL_OPTIMAL, "given": LEMPS_UNRAVEL_GIVEN,
+                 "haar_optimal": LEMPS_UNRAVEL_HAAR_OPT}
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -130,7 +132,9 @@ class Simulation:
         cfg.n_qubits, cfg.chi_max, cfg.trunc_cutoff = self.n, self.chi, float(cutoff)
         cfg.n_traj, cfg.traj_offset, cfg.seed = self.B, int(traj_offset), int(seed)
         cfg.precision = LEMPS_FP64 if precision == "fp64" else LEMPS_MIXED
-        cfg.unravel_mode = LEMPS_UNRAVEL_OPTIMAL if unravel == "optimal" else LEMPS_UNRAVEL_GIVEN
+        if unravel not in UNRAVEL_MODES:
+            raise ValueError(f"unravel must be one of {sorted(UNRAVEL_MODES)}")
+        cfg.unravel_mode = UNRAVEL_MODES[unravel]
         cfg.log_capacity = int(log_capacity)
         cfg.eps_max = float(eps_max)
         cfg.cuda_stream = self.stream.cuda_stream

@@ -204,6 +204,49 @@ def test_given_unraveling_mode(L):
         assert np.allclose(res["z"][t], ref.z, atol=1e-10)
 
 
+@pytest.mark.parametrize("kraus", [I.depolarizing_kraus(0.05), I.amplitude_damping_kraus(0.2),
+                                   I.dephasing_kraus(0.3)], ids=["depolarizing", "amp_damping", "dephasing"])
+def test_haar_optimal_mode(L, kraus):
+    """Fixed Haar-optimal unraveling (Sec. V.B): the library remixes the Kraus
+    set once for the Bell state and samples it as given; per trajectory equal
+    to the oracle's dense trajectory in the same mode (FP64)."""
+    circ = I.random_brickwork(6, 6, kraus, seed=5)
+    sim, res, br = run_gpu(L, circ, 8, 8, seed=3, unravel="haar_optimal")
+    sim.destroy()
+    for t in range(8):
+        ref = T.dense_trajectory(circ, t, 3, mode="haar_optimal")
+        assert list(br[t]) == ref.branch
+        assert np.allclose(res["z"][t], ref.z, atol=1e-10)
+        assert np.allclose(res["zz"][t], ref.zz, atol=1e-10)
+        assert abs(res["s_half"][t] - ref.s_half) < 1e-10
+
+
+def test_projective_depolarizing_given_mode(L):
+    """The five-operator Projective depolarizing set (appendix on common
+    unravelings) sampled as given, per trajectory against the oracle."""
+    circ = I.random_brickwork(6, 6, I.projective_depolarizing_kraus(0.1), seed=6)
+    sim, res, br = run_gpu(L, circ, 8, 8, seed=2, unravel="given")
+    sim.destroy()
+    for t in range(8):
+        ref = T.dense_trajectory(circ, t, 2, mode="given")
+        assert list(br[t]) == ref.branch
+        assert np.allclose(res["z"][t], ref.z, atol=1e-10)
+        assert abs(res["s_half"][t] - ref.s_half) < 1e-10
+
+
+def test_fixed_mode_inputs_are_validated(L):
+    """More than four operators only in the given mode; unknown mode names fail."""
+    five = I.Layer(np.array([0], np.int32), np.eye(4, dtype=complex)[None], I.projective_depolarizing_kraus(0.1))
+    for mode in ("optimal", "haar_optimal"):
+        sim = L.Simulation(4, 4, 2, unravel=mode)
+        with pytest.raises(L.LempsError) as e:
+            sim.apply_layer(five)
+        assert e.value.status == L.LEMPS_EINVAL
+        sim.destroy()
+    with pytest.raises(ValueError):
+        L.Simulation(4, 4, 2, unravel="projective")
+
+
 def test_traj_offset_shards_reproduce_the_full_run(L):
     """Trajectory ids key the Philox counter, so two shards reproduce one run."""
     circ = I.random_brickwork(6, 4, I.depolarizing_kraus(0.05), seed=8)
