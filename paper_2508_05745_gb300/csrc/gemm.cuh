@@ -16,10 +16,14 @@ namespace lemps {
 
 constexpr int kGemmBM = 64, kGemmBN = 64, kGemmBK = 16, kGemmThreads = 256;
 
+// Rows are padded by one element: a tile loaded with k fastest (A_KFAST /
+// B_KFAST) stores 16 consecutive k of one column per half-warp, which would hit
+// one bank group at a stride of 64 elements; at 65 they fall on distinct banks.
+// The multiply reads (fixed k, consecutive i or j) stay conflict-free.
 template <class R>
 struct GemmSmem {
-  cpx<R> a[kGemmBK][kGemmBM];
-  cpx<R> b[kGemmBK][kGemmBN];
+  cpx<R> a[kGemmBK][kGemmBM + 1];
+  cpx<R> b[kGemmBK][kGemmBN + 1];
 };
 
 template <class R, bool A_KFAST, bool B_KFAST, class FA, class FB, class FC>

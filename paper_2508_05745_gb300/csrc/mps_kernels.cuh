@@ -397,7 +397,9 @@ __global__ void __launch_bounds__(kGemmThreads) k_contract(SimView<R> s, int q) 
     }
   }
   int p = 0;
+#pragma unroll
   for (int i = 0; i < 4; ++i)
+#pragma unroll
     for (int j = i; j < 4; ++j, ++p) {
       double re = block_sum(acc[p][0], red);
       double im = block_sum(acc[p][1], red);
