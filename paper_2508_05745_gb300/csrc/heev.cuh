@@ -350,26 +350,30 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
       sec[j] = alpha;
     }
     __syncthreads();
-    // One pass over 32 x 16 half-tiles of the trailing triangle (aligned to
-    // multiples of 32 in local index), lane = row r.  It applies the previous
-    // update to A[r][c], c <= r, writes it back, accumulates the lower half
-    // y[r] += A[r][c] v[c] in a register and the strictly-upper half
-    // conj(A[r][c]) v[r] per column in 16 registers, which one reduce-scatter
-    // butterfly sums over the rows (lane 2 c + {0, 1} ends with column c).
-    // A half-warp reads 16 rows starting at a multiple of 16, whose
-    // triangular offsets r (r + 1) / 2 are distinct mod 16: conflict-free.
+    // One pass over 32 x QW slices of the trailing triangle's 32 x 32 tiles
+    // (aligned to multiples of 32 in local index), lane = row r.  It applies
+    // the previous update to A[r][c], c <= r, writes it back, accumulates the
+    // lower half y[r] += A[r][c] v[c] in a register and the strictly-upper half
+    // conj(A[r][c]) v[r] per column in QW registers, which one reduce-scatter
+    // butterfly sums over the rows.  A half-warp reads 16 rows starting at a
+    // multiple of 16, whose triangular offsets r (r + 1) / 2 are distinct
+    // mod 16: conflict-free.  QW = 16 (half-tiles): narrower slices balance the
+    // warps better but cost more in per-slice butterflies and atomics, and
+    // measured slower (QW = 8: 9.0 vs 8.5 ms per chi=128 launch).
+    constexpr int QW = 16, NQ = 32 / QW, NVQ = 2 * QW;
+    constexpr int LGQ = Scatter<NVQ>::LG;
     const int tb0 = (jl + 1) >> 5;
     const int ntb = ((M0 - 1) >> 5) - tb0 + 1;
-    const int nun = ntb * (ntb + 1);            // 2 halves per tile
+    const int nun = ntb * (ntb + 1) / 2 * NQ;
     R ssp = 0;
     for (int u = warp; u < nun; u += nwarp) {
-      const int tl = u >> 1, hf = u & 1;
+      const int tl = u / NQ, hf = u % NQ;
       int I = 0;
       while ((I + 1) * (I + 2) / 2 <= tl) ++I;
       const int J = tl - I * (I + 1) / 2;
       const int Rr = 32 * (tb0 + I) + lane;
       const bool rin = Rr > jl && Rr < M0;
-      const int cb = 32 * (tb0 + J) + 16 * hf;
+      const int cb = 32 * (tb0 + J) + QW * hf;
       cpx<R> vr = mk<R>(0, 0), wr = mk<R>(0, 0), nr = mk<R>(0, 0);
       if (rin) {
         vr = vP[Rr];
@@ -379,9 +383,9 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
       cpx<R>* rowp = Lp + (rin ? pidx(Rr, 0) : 0);
       cpx<R> acc = mk<R>(0, 0);
       bool any = false;
-      R d[32];
+      R d[NVQ];
 #pragma unroll
-      for (int cc = 0; cc < 16; ++cc) {
+      for (int cc = 0; cc < QW; ++cc) {
         const int C = cb + cc;
         cpx<R> qv = mk<R>(0, 0);
         if (C > jl && C < M0) {
@@ -402,10 +406,11 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
         atomicAdd(&yN[Rr].im, acc.im);
         ssp += cdot(nr, acc).re;
       }
-      const R tot = warp_reduce_scatter<32>(d, lane);
-      const int Cc = cb + (lane >> 1);
-      if (Cc > jl && Cc < M0) {
-        if (lane & 1) {
+      const R tot = warp_reduce_scatter<NVQ>(d, lane);
+      const int e = Scatter<NVQ>::index(lane);   // value 2 c + {re, im} of column cb + c
+      const int Cc = cb + (e >> 1);
+      if ((lane & ((1 << (5 - LGQ)) - 1)) == 0 && Cc > jl && Cc < M0) {
+        if (e & 1) {
           atomicAdd(&yN[Cc].im, tot);
           ssp += vN[Cc].im * tot;
         } else {

@@ -144,6 +144,50 @@ __device__ void qr_vdag_y(QrSmem<R>& sm, const cpx<R>* Y, int ldy, int row0, int
     if (h * HA + a < pb && c < ncc) sm.w[(h * HA + a) * 128 + c] = acc[a];
 }
 
+// Y[row0 + i][colbase + c] -= sum_a V[a][i] W[a][c] for i < pm, c < ncc (<=
+// 128): V (the panel) and W in shared memory, Y column-major in global
+// memory.  A warp owns 64 rows x 8 columns: lane l holds rows l and l + 32 of
+// the 8 columns in registers, so every global load and store covers 32
+// consecutive rows of one column; V is read conflict-free, W by broadcast.
+template <class R>
+__device__ void qr_update_y(QrSmem<R>& sm, cpx<R>* Y, int ldy, int row0, int colbase, int pm, int pb, int ncc) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  const int nrb = (pm + 63) >> 6, ncb = (ncc + 7) >> 3;
+  for (int u = warp; u < nrb * ncb; u += nwarp) {
+    const int rb = u % nrb, c0 = (u / nrb) * 8;
+    const int i0 = rb * 64 + lane, i1 = i0 + 32;
+    const bool in0 = i0 < pm, in1 = i1 < pm;
+    cpx<R> y0[8], y1[8];
+#pragma unroll
+    for (int cc = 0; cc < 8; ++cc) {
+      const bool cin = c0 + cc < ncc;
+      cpx<R>* col = Y + (int64_t)(colbase + c0 + cc) * ldy + row0;
+      y0[cc] = (cin && in0) ? col[i0] : mk<R>(0, 0);
+      y1[cc] = (cin && in1) ? col[i1] : mk<R>(0, 0);
+    }
+#pragma unroll 4
+    for (int a = 0; a < pb; ++a) {
+      const cpx<R> v0 = in0 ? sm.vs[a * pm + i0] : mk<R>(0, 0);
+      const cpx<R> v1 = in1 ? sm.vs[a * pm + i1] : mk<R>(0, 0);
+      const cpx<R>* wr = sm.w + a * 128 + c0;
+#pragma unroll
+      for (int cc = 0; cc < 8; ++cc) {
+        const cpx<R> w = wr[cc];
+        y0[cc] -= v0 * w;
+        y1[cc] -= v1 * w;
+      }
+    }
+#pragma unroll
+    for (int cc = 0; cc < 8; ++cc) {
+      if (c0 + cc < ncc) {
+        cpx<R>* col = Y + (int64_t)(colbase + c0 + cc) * ldy + row0;
+        if (in0) col[i0] = y0[cc];
+        if (in1) col[i1] = y1[cc];
+      }
+    }
+  }
+}
+
 // Q_sub (rows p0.., kq columns) <- (I - V T V^dagger) Q_sub, or with T^dagger
 // when adjoint (the factorization's trailing update on X).
 template <class R>
@@ -170,13 +214,7 @@ __device__ void qr_apply_block(QrSmem<R>& sm, cpx<R>* Y, int ldy, int row0, int 
     }
     __syncthreads();
     // Y -= V W
-    cta_gemm<R, false, false>(
-        pm, ncc, pb, [&](int i, int a) { return sm.vs[a * pm + i]; }, [&](int a, int c) { return sm.w[a * 128 + c]; },
-        [&](int i, int c, cpx<R> v) {
-          cpx<R>& y = Y[(int64_t)(col0 + c0 + c) * ldy + row0 + i];
-          y = y - v;
-        },
-        sm.g);
+    qr_update_y(sm, Y, ldy, row0, col0 + c0, pm, pb, ncc);
     __syncthreads();
   }
 }
