@@ -226,10 +226,8 @@ __device__ void householder_qr(cpx<R>* X, cpx<R>* V, cpx<R>* Qm, int m, int n, i
   const int kmin = min(m, n);
   for (int p0 = 0; p0 < kmin; p0 += NB) {
     const int pb = min(NB, kmin - p0), pm = m - p0;
-    for (int e = threadIdx.x; e < pb * pm; e += blockDim.x) {
-      const int jj = e / pm, i = e % pm;
-      sm.p[e] = X[(int64_t)(p0 + jj) * m + p0 + i];
-    }
+    for (int jj = warp; jj < pb; jj += nwarp)
+      for (int i = lane; i < pm; i += 32) sm.p[jj * pm + i] = X[(int64_t)(p0 + jj) * m + p0 + i];
     __syncthreads();
     for (int jj = 0; jj < pb; ++jj) {
       R part = 0;
@@ -259,13 +257,10 @@ __device__ void householder_qr(cpx<R>* X, cpx<R>* V, cpx<R>* Qm, int m, int n, i
       }
       __syncthreads();
     }
-    for (int e = threadIdx.x; e < pb * pm; e += blockDim.x) {
-      const int jj = e / pm, i = e % pm;
-      X[(int64_t)(p0 + jj) * m + p0 + i] = sm.p[e];
-    }
-    for (int e = threadIdx.x; e < pb * m; e += blockDim.x) {
-      const int jj = e / m, i = e % m;
-      V[(int64_t)(p0 + jj) * m + i] = (i >= p0) ? sm.vs[jj * pm + (i - p0)] : mk<R>(0, 0);
+    for (int jj = warp; jj < pb; jj += nwarp) {
+      for (int i = lane; i < pm; i += 32) X[(int64_t)(p0 + jj) * m + p0 + i] = sm.p[jj * pm + i];
+      for (int i = lane; i < m; i += 32)
+        V[(int64_t)(p0 + jj) * m + i] = (i >= p0) ? sm.vs[jj * pm + (i - p0)] : mk<R>(0, 0);
     }
     __syncthreads();
     if (p0 + pb < n) {
@@ -274,18 +269,14 @@ __device__ void householder_qr(cpx<R>* X, cpx<R>* V, cpx<R>* Qm, int m, int n, i
     }
   }
   // Q = H_0 ... H_{kmin-1} [I; 0]
-  for (int64_t e = threadIdx.x; e < (int64_t)m * kq; e += blockDim.x) {
-    const int c = (int)(e / m), i = (int)(e % m);
-    Qm[e] = mk<R>(i == c ? 1 : 0, 0);
-  }
+  for (int c = warp; c < kq; c += nwarp)
+    for (int i = lane; i < m; i += 32) Qm[(int64_t)c * m + i] = mk<R>(i == c ? 1 : 0, 0);
   __syncthreads();
   const int npanel = (kmin + NB - 1) / NB;
   for (int pi = npanel - 1; pi >= 0; --pi) {
     const int p0 = pi * NB, pb = min(NB, kmin - p0), pm = m - p0;
-    for (int e = threadIdx.x; e < pb * pm; e += blockDim.x) {
-      const int jj = e / pm, i = e % pm;
-      sm.vs[e] = V[(int64_t)(p0 + jj) * m + p0 + i];
-    }
+    for (int jj = warp; jj < pb; jj += nwarp)
+      for (int i = lane; i < pm; i += 32) sm.vs[jj * pm + i] = V[(int64_t)(p0 + jj) * m + p0 + i];
     __syncthreads();
     qr_build_t(sm, pm, pb);
     // columns j < p0 are still e_j here (the later reflectors touch rows >= p0
@@ -311,12 +302,13 @@ __global__ void __launch_bounds__(kGemmThreads, sizeof(R) == 4 ? 2 : 1) k_move_c
   cpx<R>* V = s.ws1 + t * s.ws_stride;
   cpx<R>* Qm = s.ws2 + t * s.ws_stride;
   cpx<R>* Tm = s.ws3 + t * s.ws_stride;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  // element copies run as (warp, lane) loops, lanes along the site tensor's
+  // contiguous index, with no per-element division
   if (dir > 0) {
     const int m = 2 * dl, n = dr, r = min(m, n);
-    for (int64_t e = threadIdx.x; e < (int64_t)m * n; e += blockDim.x) {
-      int c = (int)(e / m), i = (int)(e % m);
-      X[e] = A[(int64_t)i * capr + c];
-    }
+    for (int i = warp; i < m; i += nwarp)
+      for (int c = lane; c < n; c += 32) X[(int64_t)c * m + i] = A[(int64_t)i * capr + c];
     __syncthreads();
     householder_qr(X, V, Qm, m, n, r, qs);
     // A_{k+1} <- R A_{k+1}: A_{k+1} is dr x (2 d2), R is r x dr (upper part of X)
@@ -330,25 +322,23 @@ __global__ void __launch_bounds__(kGemmThreads, sizeof(R) == 4 ? 2 : 1) k_move_c
         },
         [&](int i, int cc, cpx<R> v) { Tm[(int64_t)i * 2 * d2 + cc] = v; }, sm);
     __syncthreads();
-    for (int64_t e = threadIdx.x; e < (int64_t)r * 2 * d2; e += blockDim.x) {
-      int i = (int)(e / (2 * d2)), cc = (int)(e % (2 * d2));
-      int ss = cc / d2, b = cc % d2;
-      B[(int64_t)(i * 2 + ss) * cap2 + b] = Tm[e];
-    }
+    for (int i = warp; i < r; i += nwarp)
+      for (int cc = lane; cc < 2 * d2; cc += 32) {
+        const int ss = cc >= d2, b = cc - ss * d2;
+        B[(int64_t)(i * 2 + ss) * cap2 + b] = Tm[(int64_t)i * 2 * d2 + cc];
+      }
     // A_k <- Q (m x r) reshaped (dl, 2, r)
-    for (int64_t e = threadIdx.x; e < (int64_t)m * r; e += blockDim.x) {
-      int c = (int)(e / m), i = (int)(e % m);
-      A[(int64_t)i * capr + c] = Qm[e];
-    }
+    for (int i = warp; i < m; i += nwarp)
+      for (int c = lane; c < r; c += 32) A[(int64_t)i * capr + c] = Qm[(int64_t)c * m + i];
     if (threadIdx.x == 0) bd[k + 1] = r;
   } else {
     // X = A_k^dagger: (2 dr) x dl, column-major, X[c][i] = conj(A[i][c])
     const int m = 2 * dr, n = dl, r = min(m, n);
-    for (int64_t e = threadIdx.x; e < (int64_t)m * n; e += blockDim.x) {
-      int c = (int)(e / m), i = (int)(e % m);  // row c of A, column i of A (= (s, b))
-      int ss = i / dr, b = i % dr;
-      X[e] = conj(A[(int64_t)(c * 2 + ss) * capr + b]);
-    }
+    for (int c = warp; c < n; c += nwarp)   // row c of A, column i of A (= (s, b))
+      for (int i = lane; i < m; i += 32) {
+        const int ss = i >= dr, b = i - ss * dr;
+        X[(int64_t)c * m + i] = conj(A[(int64_t)(c * 2 + ss) * capr + b]);
+      }
     __syncthreads();
     householder_qr(X, V, Qm, m, n, r, qs);
     // A_k = L Q with L = R'^dagger (dl x r), Q = Q'^dagger (r x 2dr).
@@ -360,16 +350,14 @@ __global__ void __launch_bounds__(kGemmThreads, sizeof(R) == 4 ? 2 : 1) k_move_c
         [&](int l, int j) { return l >= j ? conj(X[(int64_t)l * m + j]) : mk<R>(0, 0); },
         [&](int row, int j, cpx<R> v) { Tm[(int64_t)row * r + j] = v; }, sm);
     __syncthreads();
-    for (int64_t e = threadIdx.x; e < (int64_t)2 * d0 * r; e += blockDim.x) {
-      int row = (int)(e / r), j = (int)(e % r);
-      P[(int64_t)row * cap1 + j] = Tm[e];
-    }
+    for (int row = warp; row < 2 * d0; row += nwarp)
+      for (int j = lane; j < r; j += 32) P[(int64_t)row * cap1 + j] = Tm[(int64_t)row * r + j];
     // A_k <- Q'^dagger: A[j][ss][b] = conj(Q'[(ss, b)][j])
-    for (int64_t e = threadIdx.x; e < (int64_t)m * r; e += blockDim.x) {
-      int j = (int)(e / m), i = (int)(e % m);
-      int ss = i / dr, b = i % dr;
-      A[(int64_t)(j * 2 + ss) * capr + b] = conj(Qm[e]);
-    }
+    for (int j = warp; j < r; j += nwarp)
+      for (int i = lane; i < m; i += 32) {
+        const int ss = i >= dr, b = i - ss * dr;
+        A[(int64_t)(j * 2 + ss) * capr + b] = conj(Qm[(int64_t)j * m + i]);
+      }
     if (threadIdx.x == 0) bd[k] = r;
   }
 }
