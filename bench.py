@@ -438,12 +438,12 @@ def layer_work(left_qubits, bonds, chi):
 # DRAM bytes (read + write) of one ncu capture of the kernel as it is now
 # (profiles/<kernel>_chi128_n48_b152.md); remove an entry when its kernel changes.
 NCU_TRAFFIC = {
-    "eig": {"bytes": 236.5e6,
+    "eig": {"bytes": 236.2e6,
             "note": "one k_heev launch at the n_Gram=256 gate (gate 12 of layer 8), 152 trajectories: 1.55 MB per "
                     "trajectory against ~1.5 MB of algorithmic bytes (G read, reflectors written and read back, U "
                     "written); bench launches mix gate sizes, so this is the full-size launch, not the average"},
-    "move": {"bytes": 340.1e6,
-             "note": "one k_move_center launch (256 x 128 QR), 152 trajectories: 2.24 MB per trajectory"},
+    "move": {"bytes": 328.1e6,
+             "note": "one k_move_center launch (256 x 128 QR), 152 trajectories: 2.16 MB per trajectory"},
 }
 
 
