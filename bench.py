@@ -442,8 +442,6 @@ NCU_TRAFFIC = {
             "note": "one k_heev launch at the n_Gram=256 gate (gate 12 of layer 8), 152 trajectories: 1.55 MB per "
                     "trajectory against ~1.5 MB of algorithmic bytes (G read, reflectors written and read back, U "
                     "written); bench launches mix gate sizes, so this is the full-size launch, not the average"},
-    "move": {"bytes": 328.1e6,
-             "note": "one k_move_center launch (256 x 128 QR), 152 trajectories: 2.16 MB per trajectory"},
 }
 
 

@@ -109,28 +109,30 @@ __device__ void qr_build_t(QrSmem<R>& sm, int pm, int pb) {
 // W[a][c] = sum_i conj(V[a][i]) Y[row0 + i][colbase + c] for a < pb, c < ncc
 // (<= 128): V is the panel in shared memory, Y column-major in global memory.
 // A skinny product (pb <= 16 rows), so instead of 64 x 64 GEMM tiles: slabs
-// of 16 rows of Y are staged in the GEMM scratch (XOR-swizzled so that both
-// the column-wise store and the row-wise read are conflict-free), and thread
-// (c, h) accumulates rows a in [h NB / 2, (h + 1) NB / 2) of column c.
+// of SL rows of Y are staged in the panel buffer sm.p (free once the panel is
+// factored; SL = 32 in c64, 16 in c128), XOR-swizzled so that both the
+// column-wise store and the row-wise read are conflict-free, and thread (c, h)
+// accumulates rows a in [h NB / 2, (h + 1) NB / 2) of column c.
 template <class R>
 __device__ void qr_vdag_y(QrSmem<R>& sm, const cpx<R>* Y, int ldy, int row0, int colbase, int pm, int pb,
                           int ncc) {
   constexpr int NB = QrSmem<R>::NB;
   constexpr int HA = NB / 2;
-  static_assert(sizeof(GemmSmem<R>) >= 16 * 128 * sizeof(cpx<R>), "staging does not fit");
-  cpx<R>* ys = reinterpret_cast<cpx<R>*>(&sm.g);
+  constexpr int SL = NB * QrSmem<R>::MMAX / 128;   // staged rows per slab
+  static_assert(SL == 16 || SL == 32, "slab height");
+  cpx<R>* ys = sm.p;
   const int c = threadIdx.x & 127, h = threadIdx.x >> 7;   // 256 threads
   cpx<R> acc[HA];
 #pragma unroll
   for (int a = 0; a < HA; ++a) acc[a] = mk<R>(0, 0);
-  for (int i0 = 0; i0 < pm; i0 += 16) {
-    for (int e = threadIdx.x; e < 16 * 128; e += blockDim.x) {
-      const int ii = e & 15, cc = e >> 4;
+  for (int i0 = 0; i0 < pm; i0 += SL) {
+    for (int e = threadIdx.x; e < SL * 128; e += blockDim.x) {
+      const int ii = e & (SL - 1), cc = e / SL;
       ys[ii * 128 + (cc ^ ii)] =
           (i0 + ii < pm && cc < ncc) ? Y[(int64_t)(colbase + cc) * ldy + row0 + i0 + ii] : mk<R>(0, 0);
     }
     __syncthreads();
-    const int ni = min(16, pm - i0);
+    const int ni = min(SL, pm - i0);
     for (int ii = 0; ii < ni; ++ii) {
       const cpx<R> y = ys[ii * 128 + (c ^ ii)];
       const cpx<R>* vrow = sm.vs + (h * HA) * pm + i0 + ii;
@@ -229,10 +231,18 @@ __device__ void householder_qr(cpx<R>* X, cpx<R>* V, cpx<R>* Qm, int m, int n, i
     for (int jj = warp; jj < pb; jj += nwarp)
       for (int i = lane; i < pm; i += 32) sm.p[jj * pm + i] = X[(int64_t)(p0 + jj) * m + p0 + i];
     __syncthreads();
-    for (int jj = 0; jj < pb; ++jj) {
+    // tail norm of column 0 by a block reduction; the norm of each later
+    // column is formed by the warp that applies the previous reflector to it
+    __shared__ R s_nrm[2];
+    {
       R part = 0;
-      for (int i = jj + threadIdx.x; i < pm; i += blockDim.x) part += norm2(sm.p[jj * pm + i]);
-      R nrm2 = block_sum(part, sm.red);
+      for (int i = threadIdx.x; i < pm; i += blockDim.x) part += norm2(sm.p[i]);
+      part = block_sum(part, sm.red);
+      if (threadIdx.x == 0) s_nrm[0] = part;
+      __syncthreads();
+    }
+    for (int jj = 0; jj < pb; ++jj) {
+      const R nrm2 = s_nrm[jj & 1];
       R nrm = sqrt(nrm2);
       cpx<R> x0 = sm.p[jj * pm + jj];
       R ax0 = sqrt(norm2(x0));
@@ -253,7 +263,16 @@ __device__ void householder_qr(cpx<R>* X, cpx<R>* V, cpx<R>* Qm, int m, int n, i
         d.re = warp_sum(d.re);
         d.im = warp_sum(d.im);
         d = (R)2 * d;
-        for (int i = jj + lane; i < pm; i += 32) sm.p[c * pm + i] -= sm.vs[jj * pm + i] * d;
+        R nn = 0;
+        for (int i = jj + lane; i < pm; i += 32) {
+          const cpx<R> y = sm.p[c * pm + i] - sm.vs[jj * pm + i] * d;
+          sm.p[c * pm + i] = y;
+          if (i > jj) nn += norm2(y);
+        }
+        if (c == jj + 1) {
+          nn = warp_sum(nn);
+          if (lane == 0) s_nrm[(jj + 1) & 1] = nn;
+        }
       }
       __syncthreads();
     }
