@@ -102,16 +102,28 @@ def dense_observables(psi, n):
     return z, zz, float(-np.sum(lam * np.log(lam)))
 
 
-def dense_trajectory(circuit, traj: int, seed: int, mode: str = "optimal") -> TrajectoryRecord:
+def dense_trajectory(circuit, traj: int, seed: int, mode: str = "optimal",
+                     layering: str = "local") -> TrajectoryRecord:
+    """State-vector trajectory (Alg. 1).  layering "local": each gate is
+    followed by the noise on its two qubits, (Trunc N^{(x)2} U)^{(x) n/2};
+    "global": all gates of the layer, then the noise on every gated qubit in
+    gate order, Trunc^{(x) n-1} N^{(x) n} U^{(x) n/2} (Sec. III.A, layering
+    options).  Both draw the same Philox counters (gate, slot)."""
+    if layering not in ("local", "global"):
+        raise ValueError(f"unknown layering {layering!r}")
     n = circuit.n_qubits
     psi = np.zeros(2 ** n, dtype=np.complex128)
     psi[0] = 1.0
     rec = TrajectoryRecord([], [], [], [])
     g_glob = 0
     for layer in circuit.layers:
+        if layering == "global":
+            for q, gate in zip(layer.left_qubits, layer.gates):
+                psi = apply_2q(psi, gate, int(q), n)
         for q, gate in zip(layer.left_qubits, layer.gates):
             q = int(q)
-            psi = apply_2q(psi, gate, q, n)
+            if layering == "local":
+                psi = apply_2q(psi, gate, q, n)
             active = True
             if layer.coin_p < 1.0:
                 active = philox.uniform(seed, traj, g_glob, 2) < layer.coin_p
@@ -230,31 +242,69 @@ class MPS:
         return z, zz, s_half
 
 
+def _pair_tensor(m, q, gate=None):
+    """Two-site tensor of sites (q, q+1) with the centre moved onto the pair,
+    the gate (4x4 on the two physical indices) applied when given."""
+    if m.center < q:
+        m.move_center(q)
+    elif m.center > q + 1:
+        m.move_center(q + 1)
+    a, b = m.a[q], m.a[q + 1]
+    th = np.einsum('asm,mtb->astb', a, b)
+    if gate is not None:
+        th = np.einsum('uv,avb->aub', gate, th.reshape(a.shape[0], 4, b.shape[2]))
+    return th.reshape(a.shape[0], 2, 2, b.shape[2])
+
+
+def _split(m, q, th, cap, cutoff, rec):
+    """SVD split of the pair (Eq. MPS_truncation_error): keep
+    chi' = min(cap, #{s_k^2 > cutoff * sum s^2}) values, renormalize, centre on
+    q+1; returns the discarded weight."""
+    dl, dr = th.shape[0], th.shape[3]
+    u, s, vh = np.linalg.svd(th.reshape(dl * 2, 2 * dr), full_matrices=False)
+    w = s ** 2
+    tot = np.sum(w)
+    keep = int(min(cap, np.sum(w > cutoff * tot)))
+    keep = max(keep, 1)
+    eps = float(np.sum(w[keep:]) / tot)
+    rec.discarded.append(eps)
+    kept = math.sqrt(np.sum(w[:keep]))
+    m.a[q] = u[:, :keep].reshape(dl, 2, keep)
+    m.a[q + 1] = (s[:keep, None] * vh[:keep, :] / kept).reshape(keep, 2, dr)
+    m.center = q + 1
+    return eps
+
+
 def mps_trajectory(circuit, traj: int, seed: int, chi_max: int, cutoff: float = 1e-20,
                    mode: str = "optimal", eps_max: float = 4.0, keep_dense: bool = False,
-                   layer_callback=None):
-    """One MPS trajectory.  After gate (q, q+1) and its noise, the two-site
-    tensor is split by SVD keeping chi' = min(chi_max, #{s_k^2 > cutoff * sum s^2})
-    values; the discarded weight eps = sum_{k > chi'} s_k^2 / sum s^2 is
-    accumulated per layer and the state is renormalized.  layer_callback(l),
-    if given, is called after layer l (used to time the oracle per layer)."""
+                   layer_callback=None, layering: str = "local"):
+    """One MPS trajectory.  layering "local": after gate (q, q+1) and its
+    noise, the two-site tensor is split by SVD keeping chi' = min(chi_max,
+    #{s_k^2 > cutoff * sum s^2}) values.  "global" (Sec. III.A, layering
+    options): all gates of the layer are applied and split without the chi_max
+    cap, then the noise acts on every gated pair in gate order (re-split
+    without the cap), then every bond is truncated to chi_max by a left-to-right
+    sweep of two-site splits.  The discarded weights of a layer are summed into
+    its eps (Thm. 1) and the state is renormalized after each split.
+    layer_callback(l), if given, is called after layer l (used to time the
+    oracle per layer)."""
+    if layering not in ("local", "global"):
+        raise ValueError(f"unknown layering {layering!r}")
     n = circuit.n_qubits
     m = MPS(n)
     rec = TrajectoryRecord([], [], [], [])
     g_glob = 0
     eps_tot = 0.0
+    uncapped = 1 << 30
     for layer in circuit.layers:
         eps_layer = 0.0
+        if layering == "global":
+            for q, gate in zip(layer.left_qubits, layer.gates):
+                q = int(q)
+                eps_layer += _split(m, q, _pair_tensor(m, q, gate), uncapped, cutoff, rec)
         for q, gate in zip(layer.left_qubits, layer.gates):
             q = int(q)
-            if m.center < q:
-                m.move_center(q)
-            elif m.center > q + 1:
-                m.move_center(q + 1)
-            a, b = m.a[q], m.a[q + 1]
-            th = np.einsum('asm,mtb->astb', a, b)
-            th = np.einsum('uv,avb->aub', gate, th.reshape(a.shape[0], 4, b.shape[2]))
-            th = th.reshape(a.shape[0], 2, 2, b.shape[2])
+            th = _pair_tensor(m, q, gate if layering == "local" else None)
             active = True
             if layer.coin_p < 1.0:
                 active = philox.uniform(seed, traj, g_glob, 2) < layer.coin_p
@@ -276,20 +326,11 @@ def mps_trajectory(circuit, traj: int, seed: int, chi_max: int, cutoff: float = 
                     th = np.einsum('us,asxb->auxb', op, th)
                 else:
                     th = np.einsum('us,axsb->axub', op, th)
-            dl, dr = th.shape[0], th.shape[3]
-            u, s, vh = np.linalg.svd(th.reshape(dl * 2, 2 * dr), full_matrices=False)
-            w = s ** 2
-            tot = np.sum(w)
-            keep = int(min(chi_max, np.sum(w > cutoff * tot)))
-            keep = max(keep, 1)
-            eps = float(np.sum(w[keep:]) / tot)
-            eps_layer += eps
-            rec.discarded.append(eps)
-            kept = math.sqrt(np.sum(w[:keep]))
-            m.a[q] = u[:, :keep].reshape(dl, 2, keep)
-            m.a[q + 1] = (s[:keep, None] * vh[:keep, :] / kept).reshape(keep, 2, dr)
-            m.center = q + 1
+            eps_layer += _split(m, q, th, chi_max if layering == "local" else uncapped, cutoff, rec)
             g_glob += 1
+        if layering == "global":
+            for k in range(n - 1):
+                eps_layer += _split(m, k, _pair_tensor(m, k), chi_max, cutoff, rec)
         eps_tot += 4.0 * math.sqrt(2.0 * eps_layer)
         if layer_callback is not None:
             layer_callback(len(rec.discarded))

@@ -62,6 +62,69 @@ def test_trajectory_average_reproduces_density_matrix(small):
     assert np.max(np.abs(z)) < 4.0, z
 
 
+def test_global_layering_dense_and_mps_agree(small):
+    """Global layering (all gates, then all noise, then a truncation sweep,
+    Sec. III.A): the state-vector and MPS implementations agree per
+    trajectory when chi >= 2^{n/2}, on the same Philox counters."""
+    c = small["circuit"]
+    for tr in range(6):
+        d = T.dense_trajectory(c, tr, 0, layering="global")
+        m = T.mps_trajectory(c, tr, 0, 16, keep_dense=True, layering="global")
+        assert d.branch == m.branch
+        assert abs(abs(np.vdot(d.state, m.state)) - 1.0) < 1e-12
+        assert np.allclose(d.z, m.z, atol=1e-12) and np.allclose(d.zz, m.zz, atol=1e-12)
+        assert abs(d.s_half - m.s_half) < 1e-11
+        assert max(m.discarded) < 1e-20
+
+
+def test_global_layering_is_the_same_channel(small):
+    """Both layerings realize the same channel (the noise on one pair commutes
+    with the gates on the other, disjoint pairs of a layer): the global
+    layering's trajectory means over 128 trajectories match the exact
+    density-matrix evolution (all 15 z-scores below 4).  Without truncation
+    the two layerings give the same trajectory, branch for branch."""
+    c = small["circuit"]
+    rho = T.density_evolution(c)
+    zr, zzr = T.density_observables(rho, c.n_qubits)
+    recs = [T.dense_trajectory(c, tr, 0, layering="global") for tr in range(128)]
+    mz, sz = T.trajectory_statistics([r.z for r in recs])
+    mzz, szz = T.trajectory_statistics([r.zz for r in recs])
+    z = np.concatenate([(mz - zr) / sz, (mzz - zzr) / szz])
+    assert np.max(np.abs(z)) < 4.0, z
+    for tr in range(4):
+        loc = T.dense_trajectory(c, tr, 0)
+        assert loc.branch == recs[tr].branch
+        assert abs(abs(np.vdot(loc.state, recs[tr].state)) - 1.0) < 1e-12
+
+
+def test_global_layering_discards_less():
+    """Truncating after the whole layer's noise discards less weight than
+    truncating after each gate (Sec. III.A, layering options): lower summed
+    discarded weight on average and in most of 24 trajectories, for three
+    noise strengths and bond caps (fixed seeds)."""
+    for p, chi in [(0.05, 4), (0.02, 6), (0.1, 4)]:
+        c = I.random_brickwork(10, 8, I.depolarizing_kraus(p), seed=4)
+        loc = np.array([sum(T.mps_trajectory(c, tr, 1, chi, cutoff=1e-14).discarded) for tr in range(24)])
+        glo = np.array([sum(T.mps_trajectory(c, tr, 1, chi, cutoff=1e-14, layering="global").discarded)
+                        for tr in range(24)])
+        assert glo.mean() < loc.mean()
+        assert np.mean(glo < loc) > 0.75
+
+
+def test_global_layering_truncates_every_bond():
+    """With chi_max below the exact rank, the sweep leaves every bond at most
+    chi_max, and the discarded weights enter the error bound."""
+    c = I.random_brickwork(10, 6, I.depolarizing_kraus(0.05), seed=4)
+    rec = T.mps_trajectory(c, 0, 1, 4, cutoff=1e-14, layering="global")
+    assert rec.eps_bound > 0.0 and max(rec.discarded) > 0.0
+    m_ref = T.mps_trajectory(c, 0, 1, 4, cutoff=1e-14, layering="global", keep_dense=True)
+    psi = m_ref.state
+    n = c.n_qubits
+    for k in range(1, n):
+        rank = np.linalg.matrix_rank(psi.reshape(2 ** k, -1), tol=1e-10)
+        assert rank <= 4
+
+
 def test_given_mode_with_identity_noise_is_unitary(small):
     c = copy.deepcopy(small["circuit"])
     for l in c.layers:
