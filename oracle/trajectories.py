@@ -107,7 +107,7 @@ def dense_trajectory(circuit, traj: int, seed: int, mode: str = "optimal",
     """State-vector trajectory (Alg. 1).  layering "local": each gate is
     followed by the noise on its two qubits, (Trunc N^{(x)2} U)^{(x) n/2};
     "global": all gates of the layer, then the noise on every gated qubit in
-    gate order, Trunc^{(x) n-1} N^{(x) n} U^{(x) n/2} (Sec. III.A, layering
+    gate order, Trunc^{(x) n-1} N^{(x) n} U^{(x) n/2} (Sec. IV.A, layering
     options).  Both draw the same Philox counters (gate, slot)."""
     if layering not in ("local", "global"):
         raise ValueError(f"unknown layering {layering!r}")
@@ -280,7 +280,7 @@ def mps_trajectory(circuit, traj: int, seed: int, chi_max: int, cutoff: float = 
                    layer_callback=None, layering: str = "local"):
     """One MPS trajectory.  layering "local": after gate (q, q+1) and its
     noise, the two-site tensor is split by SVD keeping chi' = min(chi_max,
-    #{s_k^2 > cutoff * sum s^2}) values.  "global" (Sec. III.A, layering
+    #{s_k^2 > cutoff * sum s^2}) values.  "global" (Sec. IV.A, layering
     options): all gates of the layer are applied and split without the chi_max
     cap, then the noise acts on every gated pair in gate order (re-split
     without the cap), then every bond is truncated to chi_max by a left-to-right

@@ -64,7 +64,7 @@ def test_trajectory_average_reproduces_density_matrix(small):
 
 def test_global_layering_dense_and_mps_agree(small):
     """Global layering (all gates, then all noise, then a truncation sweep,
-    Sec. III.A): the state-vector and MPS implementations agree per
+    Sec. IV.A): the state-vector and MPS implementations agree per
     trajectory when chi >= 2^{n/2}, on the same Philox counters."""
     c = small["circuit"]
     for tr in range(6):
@@ -99,7 +99,7 @@ def test_global_layering_is_the_same_channel(small):
 
 def test_global_layering_discards_less():
     """Truncating after the whole layer's noise discards less weight than
-    truncating after each gate (Sec. III.A, layering options): lower summed
+    truncating after each gate (Sec. IV.A, layering options): lower summed
     discarded weight on average and in most of 24 trajectories, for three
     noise strengths and bond caps (fixed seeds)."""
     for p, chi in [(0.05, 4), (0.02, 6), (0.1, 4)]:
