@@ -70,6 +70,18 @@ typedef enum {
                                  given at every site */
 } lemps_unravel;
 
+typedef enum {
+  LEMPS_LAYER_LOCAL = 0,  /* gate, its noise, truncation of its bond, gate by
+                             gate: (Trunc N^{(x)2} U)^{(x) n/2} (Sec. IV.A,
+                             layering options) */
+  LEMPS_LAYER_GLOBAL = 1  /* all gates of the layer, then the noise on every
+                             gated pair in gate order, then every bond
+                             truncated to chi_max by a left-to-right sweep:
+                             Trunc^{(x) n-1} N^{(x) n} U^{(x) n/2} (Sec. IV.A).
+                             Bonds reach 2 chi_max inside a layer, so chi_max
+                             is limited to 64; lower discarded weight */
+} lemps_layering;
+
 /* Device allocator hook (PyTorch's caching allocator from Python).  NULL
  * alloc means cudaMalloc / cudaFree. */
 typedef void* (*lemps_alloc_fn)(size_t bytes, void* stream, void* ctx);
@@ -90,6 +102,7 @@ typedef struct {
   lemps_alloc_fn alloc;
   lemps_free_fn free;
   void* alloc_ctx;
+  int32_t layering;       /* lemps_layering (0 = local) */
 } lemps_config;
 
 typedef struct {

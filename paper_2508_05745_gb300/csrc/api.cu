@@ -33,6 +33,7 @@ struct lemps_sim {
   int n = 0;
   int64_t B = 0;
   int chi = 0;
+  int cap_max = 0;           // bond capacity: chi (local layering) or 2 chi (global)
   int prec = 0;
   cudaStream_t stream = nullptr;
   bool sticky = false;
@@ -60,6 +61,7 @@ struct lemps_sim {
   zd* layer_buf = nullptr;   // gates + kraus of the current layer
   int64_t layer_cap = 0;     // complex numbers
   zd* haar = nullptr;        // Haar-optimal mode: [0, 4) rho = I/2, [4, 20) remixed set, [20] E_av
+  zd* eye4 = nullptr;        // 4x4 identity: the gate of the noise and truncation passes
   std::vector<double> haar_key;  // Kraus set (host) whose remix haar holds
   double* obs = nullptr;     // measure scratch: z [B][n], zz [B][n-1], s_half [B], eps_bound [B]
   double* stats = nullptr;   // reductions
@@ -122,7 +124,7 @@ struct lemps_sim {
     v.bond = bond;
     v.n = n;
     v.B = B;
-    v.chi = chi;
+    v.chi = cap_max;   // evals stride (2 cap_max per trajectory)
     v.ws0 = reinterpret_cast<cpx<R>*>(ws[0]);
     v.ws1 = reinterpret_cast<cpx<R>*>(ws[1]);
     v.ws2 = reinterpret_cast<cpx<R>*>(ws[2]);
@@ -222,36 +224,57 @@ lemps_status apply_layer_t(lemps_sim* h, const lemps_layer* L) {
   }
   const unsigned grid_t = (unsigned)((h->B + kThreads - 1) / kThreads);
   SimView<R> sv = h->view<R>();
-  for (int g = 0; g < ng; ++g) {
-    const int q = L->left_qubit[g];
+  // One pair step: centre onto (q, q+1), contraction, gate and noise sites
+  // (coin_p = 0: no noise, the gate alone), Gram on the side that leaves the
+  // centre next to the following pair, eigensolve keeping at most keep_max,
+  // split.  gate_global keys the Philox counters of the noise sites.
+  auto pair_step = [&](int q, const zd* gate, int gate_local, double coin_p, int64_t gate_global, bool log,
+                       int keep_max, int side) {
     if (h->center < q) move_center_to<R>(h, q);
     else if (h->center > q + 1) move_center_to<R>(h, q + 1);
     h->timed(LEMPS_K_CONTRACT, [&] { k_contract<R><<<(unsigned)h->B, kThreads, 0, h->stream>>>(sv, q); });
     LayerDev ld;
-    ld.gates = h->layer_buf;
+    ld.gates = gate;
     ld.kraus = kset_d;
     ld.r = kset_r;
-    ld.coin_p = L->coin_p;
+    ld.coin_p = coin_p;
     ld.mode = kmode;
     ld.seed = h->cfg.seed;
     ld.traj_offset = h->cfg.traj_offset;
-    ld.gate_global = h->gates_done + g;
-    ld.gate_local = g;
-    ld.blog = (ld.gate_global < h->log_cap) ? h->blog + ld.gate_global * 2 * h->B : nullptr;
+    ld.gate_global = gate_global;
+    ld.gate_local = gate_local;
+    ld.blog = (log && gate_global < h->log_cap) ? h->blog + gate_global * 2 * h->B : nullptr;
     GateState gs;
     gs.rho12 = h->rho12;
     gs.top = h->top;
     gs.status = h->status;
     gs.B = h->B;
     h->timed(LEMPS_K_UNRAVEL, [&] { launch_unravel_gate(gs, ld, h->stream); });
-    int side;
-    if (g + 1 < ng) side = (L->left_qubit[g + 1] > q) ? 0 : 1;
-    else if (g > 0) side = (q > L->left_qubit[g - 1]) ? 0 : 1;
-    else side = 0;
     h->timed(LEMPS_K_GRAM, [&] { k_apply_gram<R><<<(unsigned)h->B, kThreads, 0, h->stream>>>(sv, q, side); });
-    launch_heev<R>(h, q, side, h->cfg.trunc_cutoff, h->chi, 1);
+    launch_heev<R>(h, q, side, h->cfg.trunc_cutoff, keep_max, 1);
     h->timed(LEMPS_K_SPLIT, [&] { k_split<R><<<(unsigned)h->B, kThreads, 0, h->stream>>>(sv, q, side); });
     h->center = (side == 0) ? q + 1 : q;
+  };
+  // side 0 (centre to q+1) when the next pair lies to the right
+  auto side_of = [&](int g) {
+    const int q = L->left_qubit[g];
+    if (g + 1 < ng) return (L->left_qubit[g + 1] > q) ? 0 : 1;
+    if (g > 0) return (q > L->left_qubit[g - 1]) ? 0 : 1;
+    return 0;
+  };
+  if (h->cfg.layering == LEMPS_LAYER_GLOBAL) {
+    // all gates (no noise, bonds up to 2 chi), then the noise on every gated
+    // pair with the identity gate and the same Philox counters as the local
+    // layering, then a left-to-right truncation sweep over every bond
+    for (int g = 0; g < ng; ++g)
+      pair_step(L->left_qubit[g], h->layer_buf + 16 * (int64_t)g, 0, 0.0, h->gates_done + g, false, h->cap_max,
+                side_of(g));
+    for (int g = 0; g < ng; ++g)
+      pair_step(L->left_qubit[g], h->eye4, 0, L->coin_p, h->gates_done + g, true, h->cap_max, side_of(g));
+    for (int k = 0; k + 1 < h->n; ++k) pair_step(k, h->eye4, 0, 0.0, h->gates_done, false, h->chi, 0);
+  } else {
+    for (int g = 0; g < ng; ++g)
+      pair_step(L->left_qubit[g], h->layer_buf, g, L->coin_p, h->gates_done + g, true, h->chi, side_of(g));
   }
   h->timed(LEMPS_K_OTHER, [&] { k_layer_end<R><<<grid_t, kThreads, 0, h->stream>>>(sv); });
   h->gates_done += ng;
@@ -302,8 +325,8 @@ lemps_status measure_t(lemps_sim* h, lemps_measurement* m) {
     k_obs_from_rho12<<<grid_t, kThreads, 0, h->stream>>>(h->rho12, B, n, q, z, zz);
     if (q == hb - 1) {
       k_site_gram<R><<<(unsigned)B, kThreads, 0, h->stream>>>(sv, q);
-      launch_heev<R>(h, q, 2, 0.0, h->chi, 0);
-      k_entropy_from_evals<<<grid_t, kThreads, 0, h->stream>>>(h->evals, 2 * h->chi, h->bond, n + 1, q + 1, B, sh);
+      launch_heev<R>(h, q, 2, 0.0, h->cap_max, 0);
+      k_entropy_from_evals<<<grid_t, kThreads, 0, h->stream>>>(h->evals, 2 * h->cap_max, h->bond, n + 1, q + 1, B, sh);
     }
     launch_move<R>(h, q, +1);
     ++h->center;
@@ -362,12 +385,17 @@ lemps_status sim_create(const lemps_config* cfg, lemps_handle* out) {
       cfg->unravel_mode != LEMPS_UNRAVEL_HAAR_OPT)
     return fail(LEMPS_EINVAL, "sim_create: bad unravel_mode");
   if (!(cfg->trunc_cutoff >= 0.0) || !(cfg->eps_max >= 2.0)) return fail(LEMPS_EINVAL, "sim_create: bad cutoff or eps_max");
+  if (cfg->layering != LEMPS_LAYER_LOCAL && cfg->layering != LEMPS_LAYER_GLOBAL)
+    return fail(LEMPS_EINVAL, "sim_create: bad layering");
+  if (cfg->layering == LEMPS_LAYER_GLOBAL && cfg->chi_max > 64)
+    return fail(LEMPS_EINVAL, "sim_create: global layering holds bonds of 2 chi_max, so chi_max must be <= 64");
   if ((cfg->alloc == nullptr) != (cfg->free == nullptr)) return fail(LEMPS_EINVAL, "sim_create: alloc and free go together");
   lemps_sim* h = new lemps_sim();
   h->cfg = *cfg;
   h->n = cfg->n_qubits;
   h->B = cfg->n_traj;
   h->chi = cfg->chi_max;
+  h->cap_max = (cfg->layering == LEMPS_LAYER_GLOBAL) ? 2 * cfg->chi_max : cfg->chi_max;
   h->prec = cfg->precision;
   h->stream = (cudaStream_t)cfg->cuda_stream;
   h->elem = (h->prec == LEMPS_FP64) ? sizeof(zd) : sizeof(zf);
@@ -376,7 +404,7 @@ lemps_status sim_create(const lemps_config* cfg, lemps_handle* out) {
   for (int k = 0; k <= n; ++k) {
     int e = std::min(k, n - k);
     int64_t c = (e >= 30) ? (int64_t)1 << 30 : ((int64_t)1 << e);
-    h->cap_h[k] = (int32_t)std::min<int64_t>(c, h->chi);
+    h->cap_h[k] = (int32_t)std::min<int64_t>(c, h->cap_max);
   }
   h->off_h.resize(n);
   int64_t tot = 0;
@@ -384,7 +412,7 @@ lemps_status sim_create(const lemps_config* cfg, lemps_handle* out) {
     h->off_h[k] = tot;
     tot += (int64_t)h->cap_h[k] * 2 * h->cap_h[k + 1] * h->B;
   }
-  h->ws_stride = (int64_t)(2 * h->chi) * (2 * h->chi);
+  h->ws_stride = (int64_t)(2 * h->cap_max) * (2 * h->cap_max);
   h->log_cap = cfg->log_capacity > 0 ? cfg->log_capacity : 0;
   h->layer_cap = (int64_t)(n / 2 + 1) * 16 + 4 * kMaxKraus;
   bool ok = true;
@@ -398,7 +426,7 @@ lemps_status sim_create(const lemps_config* cfg, lemps_handle* out) {
   h->cap = (int32_t*)A(sizeof(int32_t) * (n + 1));
   h->bond = (int32_t*)A(sizeof(int32_t) * (n + 1) * h->B);
   for (int i = 0; i < 4; ++i) h->ws[i] = A(h->elem * h->ws_stride * h->B);
-  h->evals = (double*)A(sizeof(double) * 2 * h->chi * h->B);
+  h->evals = (double*)A(sizeof(double) * 2 * h->cap_max * h->B);
   h->rho12 = (zd*)A(sizeof(zd) * 16 * h->B);
   h->top = (zd*)A(sizeof(zd) * 16 * h->B);
   h->eps_layer = (double*)A(sizeof(double) * h->B);
@@ -410,6 +438,7 @@ lemps_status sim_create(const lemps_config* cfg, lemps_handle* out) {
   h->blog = (int8_t*)A(std::max<int64_t>(1, h->log_cap * 2 * h->B));
   h->layer_buf = (zd*)A(sizeof(zd) * h->layer_cap);
   h->haar = (zd*)A(sizeof(zd) * 21);
+  h->eye4 = (zd*)A(sizeof(zd) * 16);
   h->obs = (double*)A(sizeof(double) * h->B * (2 * n + 1));
   h->stats = (double*)A(sizeof(double) * (4 * n + 4));
   if (!ok) {
@@ -425,6 +454,9 @@ lemps_status sim_create(const lemps_config* cfg, lemps_handle* out) {
     // the Bell state's reduced state, input of the Haar-optimal remix
     static const zd kHalfIdentity[4] = {{0.5, 0.0}, {0.0, 0.0}, {0.0, 0.0}, {0.5, 0.0}};
     cudaMemcpyAsync(h->haar, kHalfIdentity, sizeof(kHalfIdentity), cudaMemcpyHostToDevice, h->stream);
+    static const zd kEye4[16] = {{1, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}, {1, 0}, {0, 0}, {0, 0},
+                                 {0, 0}, {0, 0}, {1, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}, {1, 0}};
+    cudaMemcpyAsync(h->eye4, kEye4, sizeof(kEye4), cudaMemcpyHostToDevice, h->stream);
   }
   if (h->prec == LEMPS_FP64) k_init_state<double><<<(unsigned)h->B, 64, 0, h->stream>>>(h->view<double>());
   else k_init_state<float><<<(unsigned)h->B, 64, 0, h->stream>>>(h->view<float>());

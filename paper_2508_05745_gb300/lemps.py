@@ -18,6 +18,8 @@ from . import build as _build
 LEMPS_OK, LEMPS_EINVAL, LEMPS_ENOMEM, LEMPS_ECUDA, LEMPS_ENUMERIC, LEMPS_ESTATE = range(6)
 LEMPS_FP64, LEMPS_MIXED = 0, 1
 LEMPS_UNRAVEL_OPTIMAL, LEMPS_UNRAVEL_GIVEN, LEMPS_UNRAVEL_HAAR_OPT = 0, 1, 2
+LEMPS_LAYER_LOCAL, LEMPS_LAYER_GLOBAL = 0, 1
+LAYERINGS = {"local": LEMPS_LAYER_LOCAL, "global": LEMPS_LAYER_GLOBAL}
 UNRAVEL_MODES = {"optimal": LEMPS_UNRAVEL_OPTIMAL, "given": LEMPS_UNRAVEL_GIVEN,
                  "haar_optimal": LEMPS_UNRAVEL_HAAR_OPT}
 
@@ -41,7 +43,7 @@ class Config(ctypes.Structure):
                 ("n_traj", ctypes.c_int64), ("traj_offset", ctypes.c_int64), ("seed", ctypes.c_uint64),
                 ("precision", ctypes.c_int32), ("unravel_mode", ctypes.c_int32), ("log_capacity", ctypes.c_int32),
                 ("eps_max", ctypes.c_double), ("cuda_stream", ctypes.c_void_p), ("alloc", ALLOC_FN),
-                ("free", FREE_FN), ("alloc_ctx", ctypes.c_void_p)]
+                ("free", FREE_FN), ("alloc_ctx", ctypes.c_void_p), ("layering", ctypes.c_int32)]
 
 
 class LayerStruct(ctypes.Structure):
@@ -120,7 +122,8 @@ class Simulation:
 
     def __init__(self, n_qubits: int, chi_max: int, n_traj: int, seed: int = 0, precision: str = "fp64",
                  unravel: str = "optimal", cutoff: Optional[float] = None, traj_offset: int = 0,
-                 log_capacity: int = 0, eps_max: float = 4.0, stream=None, torch_allocator: bool = True):
+                 log_capacity: int = 0, eps_max: float = 4.0, stream=None, torch_allocator: bool = True,
+                 layering: str = "local"):
         torch = _require_cuda()
         lib = load()
         self.n, self.chi, self.B = int(n_qubits), int(chi_max), int(n_traj)
@@ -135,6 +138,9 @@ class Simulation:
         if unravel not in UNRAVEL_MODES:
             raise ValueError(f"unravel must be one of {sorted(UNRAVEL_MODES)}")
         cfg.unravel_mode = UNRAVEL_MODES[unravel]
+        if layering not in LAYERINGS:
+            raise ValueError(f"layering must be one of {sorted(LAYERINGS)}")
+        cfg.layering = LAYERINGS[layering]
         cfg.log_capacity = int(log_capacity)
         cfg.eps_max = float(eps_max)
         cfg.cuda_stream = self.stream.cuda_stream

@@ -27,9 +27,10 @@ def L():
     return lemps
 
 
-def run_gpu(L, circ, chi, n_traj, seed, precision="fp64", unravel="optimal", cutoff=None, traj_offset=0):
+def run_gpu(L, circ, chi, n_traj, seed, precision="fp64", unravel="optimal", cutoff=None, traj_offset=0,
+            layering="local"):
     sim = L.Simulation(circ.n_qubits, chi, n_traj, seed=seed, precision=precision, unravel=unravel,
-                       cutoff=cutoff, log_capacity=circ.n_gates, traj_offset=traj_offset)
+                       cutoff=cutoff, log_capacity=circ.n_gates, traj_offset=traj_offset, layering=layering)
     sim.run(circ)
     res = sim.measure()
     branches = np.zeros((n_traj, 2 * circ.n_gates), dtype=np.int32)
@@ -245,6 +246,47 @@ def test_fixed_mode_inputs_are_validated(L):
         sim.destroy()
     with pytest.raises(ValueError):
         L.Simulation(4, 4, 2, unravel="projective")
+
+
+def test_global_layering_with_truncation(L):
+    """Global layering (all gates, all noise, then a truncation sweep; Sec.
+    IV.A) with chi_max below the exact rank: per trajectory equal to the
+    oracle's MPS trajectory in the same layering (FP64), error bound included."""
+    circ = I.random_brickwork(10, 6, I.depolarizing_kraus(0.05), seed=4)
+    sim, res, br = run_gpu(L, circ, 4, 8, seed=1, cutoff=1e-14, layering="global")
+    sim.destroy()
+    for t in range(8):
+        ref = T.mps_trajectory(circ, t, 1, 4, cutoff=1e-14, layering="global")
+        assert list(br[t]) == ref.branch
+        assert np.allclose(res["z"][t], ref.z, atol=1e-9)
+        assert np.allclose(res["zz"][t], ref.zz, atol=1e-9)
+        assert abs(res["s_half"][t] - ref.s_half) < 1e-9
+        assert abs(res["eps_bound"][t] - ref.eps_bound) < 1e-9
+    assert res["eps_bound"].max() > 0.0
+
+
+def test_global_layering_without_truncation(L):
+    """chi >= 2^{n/2}: the global layering equals the dense trajectory (and,
+    since the pairs of a layer are disjoint, the local layering)."""
+    circ = I.workload_small_exact(seed=0)["circuit"]
+    sim, res, br = run_gpu(L, circ, 16, 8, seed=0, layering="global")
+    sim.destroy()
+    _, loc, brl = run_gpu(L, circ, 16, 8, seed=0)
+    for t in range(8):
+        ref = T.dense_trajectory(circ, t, 0, layering="global")
+        assert list(br[t]) == ref.branch
+        assert np.allclose(res["z"][t], ref.z, atol=1e-10)
+        assert abs(res["s_half"][t] - ref.s_half) < 1e-10
+    assert np.array_equal(br, brl)
+    assert np.allclose(res["z"], loc["z"], atol=1e-10)
+
+
+def test_global_layering_limits(L):
+    with pytest.raises(L.LempsError) as e:
+        L.Simulation(8, 128, 2, layering="global")
+    assert e.value.status == L.LEMPS_EINVAL
+    with pytest.raises(ValueError):
+        L.Simulation(8, 16, 2, layering="sideways")
 
 
 def test_traj_offset_shards_reproduce_the_full_run(L):
