@@ -39,6 +39,7 @@ class TrajectoryRecord:
     e_av: List[float]          # E_av of the chosen unraveling at that site
     discarded: List[float]     # per gate discarded weight (MPS only)
     eps_bound: float = 0.0     # per-trajectory error bound (MPS only)
+    eps_layers: List[float] = dataclasses.field(default_factory=list)  # per layer 4 sqrt(2 sum eps) (MPS only)
     z: np.ndarray = None       # <Z_i>
     zz: np.ndarray = None      # <Z_i Z_{i+1}>
     s_half: float = 0.0        # entropy of bond n/2 (nats)
@@ -332,6 +333,7 @@ def mps_trajectory(circuit, traj: int, seed: int, chi_max: int, cutoff: float = 
             for k in range(n - 1):
                 eps_layer += _split(m, k, _pair_tensor(m, k), chi_max, cutoff, rec)
         eps_tot += 4.0 * math.sqrt(2.0 * eps_layer)
+        rec.eps_layers.append(4.0 * math.sqrt(2.0 * eps_layer))
         if layer_callback is not None:
             layer_callback(len(rec.discarded))
     rec.eps_bound = eps_tot if eps_tot <= eps_max - 2.0 else eps_max
@@ -355,3 +357,60 @@ def error_estimate(eps_bounds: np.ndarray, eps_max: float = 4.0, delta: float = 
     per-trajectory bounds, buffer = sqrt(eps_max^2 / (2N) ln(1/delta))."""
     nt = len(eps_bounds)
     return float(np.mean(eps_bounds)), math.sqrt(eps_max ** 2 / (2.0 * nt) * math.log(1.0 / delta))
+
+
+# --- concentration-improved error bound (Sec. III.C; appendix on concentration) ---
+
+def concentration_weight(kind: str, param: float, k: int, n: int) -> float:
+    """Weight of a layer k layers before the last one: alpha^k for a channel
+    contracting the trace distance by alpha < 1 per layer ("alpha"), or
+    min(sqrt(8 n) (1 - p)^k, 1) for local depolarizing noise of rate p by the
+    strong data-processing inequality ("depolarizing")."""
+    if kind == "alpha":
+        return param ** k
+    if kind == "depolarizing":
+        return min(math.sqrt(8.0 * n) * (1.0 - param) ** k, 1.0)
+    raise ValueError(f"unknown weighting {kind!r}")
+
+
+def concentrated_bound(eps_layers, kind: str, param: float, n: int, eps_max: float = 4.0) -> float:
+    """Per-trajectory concentration-improved bound sum_l w(L - l) eps_approx(l)
+    over the trajectory's layers l = 1..L, capped like the plain bound
+    (kept when <= eps_max - 2, else eps_max)."""
+    big_l = len(eps_layers)
+    e = sum(concentration_weight(kind, param, big_l - 1 - l, n) * x for l, x in enumerate(eps_layers))
+    return e if e <= eps_max - 2.0 else eps_max
+
+
+# --- output-distribution sampling (Lemma sampling_reduction) -------------------
+
+SAMPLE_COUNTER_BASE = 1 << 62   # Philox gate word of shot s: SAMPLE_COUNTER_BASE + s
+
+
+def sample_bitstring_dense(psi: np.ndarray, n: int, seed: int, traj: int, shot: int) -> np.ndarray:
+    """One computational-basis bitstring from |psi>, qubit 0 first, by
+    sequential conditionals: bit k is 0 when u_k (p0 + p1) < p0, with p_s the
+    weight of the prefix extended by s and u_k = Philox(seed; traj,
+    SAMPLE_COUNTER_BASE + shot, k).  Sampling every trajectory's final state
+    this way samples the unraveled mixed state (Lemma sampling_reduction)."""
+    t = psi.reshape([2] * n)
+    bits = np.zeros(n, dtype=np.uint8)
+    for k in range(n):
+        w = np.sum(np.abs(t) ** 2, axis=tuple(range(1, t.ndim)))
+        u = philox.uniform(seed, traj, SAMPLE_COUNTER_BASE + shot, k)
+        b = 0 if u * (w[0] + w[1]) < w[0] else 1
+        bits[k] = b
+        t = t[b]
+    return bits
+
+
+def bitstring_probability(psi: np.ndarray, n: int, bits) -> float:
+    """Product of the sequential conditionals of a bitstring (equals |<x|psi>|^2
+    for a normalized state)."""
+    t = psi.reshape([2] * n)
+    prob = 1.0
+    for k in range(n):
+        w = np.sum(np.abs(t) ** 2, axis=tuple(range(1, t.ndim)))
+        prob *= w[bits[k]] / (w[0] + w[1])
+        t = t[bits[k]]
+    return prob

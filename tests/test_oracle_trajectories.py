@@ -239,3 +239,63 @@ def test_gradient_descent_approaches_eof():
     best = U.unraveling_entropy(U.optimal_unraveling(rho, kr)[0], rho)
     assert costs[-1] <= costs[0] + 1e-12
     assert costs[-1] >= best - 1e-12
+
+
+# --- output-distribution sampling and the concentration-improved bound ---------
+
+def test_sequential_conditionals_give_born_probabilities(rng):
+    """The product of the sequential conditionals of every bitstring equals its
+    Born probability |<x|psi>|^2 (n = 5, random state)."""
+    n = 5
+    psi = rng.standard_normal(2 ** n) + 1j * rng.standard_normal(2 ** n)
+    psi /= np.linalg.norm(psi)
+    for x in range(2 ** n):
+        bits = [(x >> (n - 1 - k)) & 1 for k in range(n)]
+        assert abs(T.bitstring_probability(psi, n, bits) - abs(psi[x]) ** 2) < 1e-15
+
+
+def test_sampled_bitstrings_follow_born_rule(rng):
+    """20000 shots from a random 4-qubit state: total-variation distance to
+    |psi|^2 below 0.02 (the expected TV is about 0.01)."""
+    n = 4
+    psi = rng.standard_normal(2 ** n) + 1j * rng.standard_normal(2 ** n)
+    psi /= np.linalg.norm(psi)
+    counts = np.zeros(2 ** n)
+    for shot in range(20000):
+        b = T.sample_bitstring_dense(psi, n, 5, 0, shot)
+        counts[int("".join(map(str, b)), 2)] += 1
+    tv = 0.5 * np.sum(np.abs(counts / counts.sum() - np.abs(psi) ** 2))
+    assert tv < 0.02, tv
+
+
+def test_trajectory_samples_reproduce_the_noisy_distribution(small):
+    """Lemma sampling_reduction: one shot per trajectory samples the mixed
+    state; <Z_i> and <Z_i Z_i+1> estimated from 256 trajectories' bits match
+    the exact density matrix within 4 standard errors."""
+    c = small["circuit"]
+    n = c.n_qubits
+    rho = T.density_evolution(c)
+    zr, zzr = T.density_observables(rho, n)
+    bits = np.array([T.sample_bitstring_dense(T.dense_trajectory(c, tr, 0).state, n, 0, tr, 0)
+                     for tr in range(256)])
+    sgn = 1.0 - 2.0 * bits
+    mz, sz = T.trajectory_statistics(sgn)
+    mzz, szz = T.trajectory_statistics(sgn[:, :-1] * sgn[:, 1:])
+    z = np.concatenate([(mz - zr) / np.maximum(sz, 1e-3), (mzz - zzr) / np.maximum(szz, 1e-3)])
+    assert np.max(np.abs(z)) < 4.0, z
+
+
+def test_concentration_bound_definitions():
+    """alpha = 1 gives the plain bound of Thm. 1; weights <= 1 never raise it;
+    the depolarizing weight is 1 for recent layers and sqrt(8n)(1-p)^k once
+    that drops below 1."""
+    c = I.random_brickwork(10, 6, I.depolarizing_kraus(0.05), seed=4)
+    rec = T.mps_trajectory(c, 0, 1, 4, cutoff=1e-14)
+    assert len(rec.eps_layers) == 6
+    assert abs(T.concentrated_bound(rec.eps_layers, "alpha", 1.0, 10) - rec.eps_bound) < 1e-15
+    for a in (0.3, 0.7, 0.95):
+        assert T.concentrated_bound(rec.eps_layers, "alpha", a, 10) <= rec.eps_bound + 1e-15
+    assert T.concentrated_bound(rec.eps_layers, "alpha", 0.5, 10) < T.concentrated_bound(rec.eps_layers, "alpha", 0.9, 10)
+    assert T.concentration_weight("depolarizing", 0.3, 0, 10) == 1.0
+    k = 40
+    assert abs(T.concentration_weight("depolarizing", 0.3, k, 10) - math.sqrt(80.0) * 0.7 ** k) < 1e-18
