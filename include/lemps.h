@@ -168,6 +168,28 @@ lemps_status sample_branch(lemps_handle h, int64_t gate, int32_t slot, int32_t* 
  * Moves every trajectory's orthogonality centre; synchronizes the stream. */
 lemps_status measure(lemps_handle h, lemps_measurement* m);
 
+/* Output-distribution sampling (Lemma sampling_reduction; Corollary on output
+ * distribution sampling): draws n_shots (1..65535) computational-basis
+ * bitstrings from every trajectory's current MPS by sequential conditional
+ * sampling over the sites, qubit 0 first; over trajectories they sample the
+ * unraveled mixed state.  bits_out: host [n_traj][n_shots][n] bytes 0/1.
+ * Random numbers: Philox counter (trajectory id, 2^62 + shot, site, 0), a
+ * domain the noise sites never use.  Moves the orthogonality centre to site
+ * 0; keeps one device buffer of the largest request (through the handle's
+ * allocator); synchronizes the stream. */
+lemps_status sample_bitstrings(lemps_handle h, int32_t n_shots, uint8_t* bits_out);
+
+/* Concentration-improved error bound (Sec. III.C; appendix on concentration
+ * bounds): per trajectory sum_l w(L - l) eps_approx(l) over the L layers
+ * applied so far, eps_approx(l) = 4 sqrt(2 sum of the layer's discarded
+ * weights), with w(k) = alpha^k (kind 0, param = alpha in (0, 1]; alpha = 1
+ * gives the plain bound of Thm. 1) or min(sqrt(8 n) (1 - p)^k, 1) for local
+ * depolarizing noise of rate p (kind 1, param = p).  Capped like the plain
+ * bound (kept when <= eps_max - 2, else eps_max).  eps_out: host [n_traj],
+ * optional; eps_hat receives the mean.  The per-layer history holds 256
+ * layers: LEMPS_ESTATE after more.  Synchronizes the stream. */
+lemps_status eps_concentrated(lemps_handle h, int32_t kind, double param, double* eps_out, double* eps_hat);
+
 /* Copy trajectory `traj`'s MPS to the host: bond_dims [n+1]; tensors receives
  * site k as [d_k][2][d_{k+1}] complex, sites concatenated (caller sizes it for
  * n * 2 * chi_max^2 complex).  Inspection only; synchronizes the stream. */

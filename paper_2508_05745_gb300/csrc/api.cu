@@ -28,6 +28,9 @@ constexpr int kThreads = 256;
 
 }  // namespace
 
+// Layers whose error contributions are kept per trajectory for eps_concentrated.
+constexpr int kEpsHistLayers = 256;
+
 struct lemps_sim {
   lemps_config cfg;
   int n = 0;
@@ -62,6 +65,10 @@ struct lemps_sim {
   int64_t layer_cap = 0;     // complex numbers
   zd* haar = nullptr;        // Haar-optimal mode: [0, 4) rho = I/2, [4, 20) remixed set, [20] E_av
   zd* eye4 = nullptr;        // 4x4 identity: the gate of the noise and truncation passes
+  double* eps_hist = nullptr;  // [B][kEpsHistLayers] per-layer 4 sqrt(2 sum eps)
+  int layers_done = 0;
+  uint8_t* bits_buf = nullptr;  // sample_bitstrings output (largest request so far)
+  size_t bits_cap = 0;
   std::vector<double> haar_key;  // Kraus set (host) whose remix haar holds
   double* obs = nullptr;     // measure scratch: z [B][n], zz [B][n-1], s_half [B], eps_bound [B]
   double* stats = nullptr;   // reductions
@@ -276,7 +283,11 @@ lemps_status apply_layer_t(lemps_sim* h, const lemps_layer* L) {
     for (int g = 0; g < ng; ++g)
       pair_step(L->left_qubit[g], h->layer_buf, g, L->coin_p, h->gates_done + g, true, h->chi, side_of(g));
   }
-  h->timed(LEMPS_K_OTHER, [&] { k_layer_end<R><<<grid_t, kThreads, 0, h->stream>>>(sv); });
+  double* hist = (h->layers_done < kEpsHistLayers) ? h->eps_hist : nullptr;
+  h->timed(LEMPS_K_OTHER, [&] {
+    k_layer_end<R><<<grid_t, kThreads, 0, h->stream>>>(sv, hist, kEpsHistLayers, h->layers_done);
+  });
+  ++h->layers_done;
   h->gates_done += ng;
   return check_cuda(h, "apply_layer");
 }
@@ -439,6 +450,7 @@ lemps_status sim_create(const lemps_config* cfg, lemps_handle* out) {
   h->layer_buf = (zd*)A(sizeof(zd) * h->layer_cap);
   h->haar = (zd*)A(sizeof(zd) * 21);
   h->eye4 = (zd*)A(sizeof(zd) * 16);
+  h->eps_hist = (double*)A(sizeof(double) * kEpsHistLayers * h->B);
   h->obs = (double*)A(sizeof(double) * h->B * (2 * n + 1));
   h->stats = (double*)A(sizeof(double) * (4 * n + 4));
   if (!ok) {
@@ -530,6 +542,56 @@ lemps_status sample_branch(lemps_handle h, int64_t gate, int32_t slot, int32_t* 
       cudaStreamSynchronize(h->stream) != cudaSuccess)
     return check_cuda(h, "sample_branch");
   for (int64_t t = 0; t < h->B; ++t) branch_out[t] = tmp[t];
+  return LEMPS_OK;
+}
+
+lemps_status sample_bitstrings(lemps_handle h, int32_t n_shots, uint8_t* bits_out) {
+  if (!h || !bits_out || n_shots < 1 || n_shots > 65535) return fail(LEMPS_EINVAL, "sample_bitstrings: bad argument");
+  if (h->sticky) return fail(LEMPS_ECUDA, "sample_bitstrings: sticky CUDA error");
+  const size_t bytes = (size_t)h->B * (size_t)n_shots * (size_t)h->n;
+  if (bytes > h->bits_cap) {
+    uint8_t* p = (uint8_t*)h->dalloc(bytes);
+    if (!p) return fail(LEMPS_ENOMEM, "sample_bitstrings: device allocation failed");
+    h->bits_buf = p;
+    h->bits_cap = bytes;
+  }
+  const dim3 grid((unsigned)h->B, (unsigned)n_shots);
+  if (h->prec == LEMPS_FP64) {
+    move_center_to<double>(h, 0);
+    k_sample_bits<double><<<grid, 256, 0, h->stream>>>(h->view<double>(), n_shots, h->cfg.seed, h->cfg.traj_offset,
+                                                      h->bits_buf);
+  } else {
+    move_center_to<float>(h, 0);
+    k_sample_bits<float><<<grid, 256, 0, h->stream>>>(h->view<float>(), n_shots, h->cfg.seed, h->cfg.traj_offset,
+                                                     h->bits_buf);
+  }
+  if (cudaMemcpyAsync(bits_out, h->bits_buf, bytes, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
+    return check_cuda(h, "sample_bitstrings copy");
+  cudaStreamSynchronize(h->stream);
+  return check_cuda(h, "sample_bitstrings");
+}
+
+lemps_status eps_concentrated(lemps_handle h, int32_t kind, double param, double* eps_out, double* eps_hat) {
+  if (!h || !eps_hat) return fail(LEMPS_EINVAL, "eps_concentrated: null argument");
+  if (h->sticky) return fail(LEMPS_ECUDA, "eps_concentrated: sticky CUDA error");
+  if (kind == 0 ? !(param > 0.0 && param <= 1.0) : (kind == 1 ? !(param >= 0.0 && param <= 1.0) : true))
+    return fail(LEMPS_EINVAL, "eps_concentrated: kind 0 needs 0 < alpha <= 1, kind 1 needs 0 <= p <= 1");
+  if (h->layers_done > kEpsHistLayers)
+    return fail(LEMPS_ESTATE, "eps_concentrated: more than 256 layers since sim_create (history is full)");
+  double* out = h->obs;   // measure scratch, [B] at least
+  const unsigned grid_t = (unsigned)((h->B + kThreads - 1) / kThreads);
+  k_eps_weighted<<<grid_t, kThreads, 0, h->stream>>>(h->eps_hist, kEpsHistLayers, h->B, h->layers_done, kind, param,
+                                                     h->n, h->cfg.eps_max, out);
+  std::vector<double> host((size_t)h->B);
+  if (cudaMemcpyAsync(host.data(), out, sizeof(double) * h->B, cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
+    return check_cuda(h, "eps_concentrated copy");
+  cudaStreamSynchronize(h->stream);
+  lemps_status st = check_cuda(h, "eps_concentrated");
+  if (st != LEMPS_OK) return st;
+  double sum = 0.0;
+  for (double x : host) sum += x;
+  *eps_hat = sum / (double)h->B;
+  if (eps_out) std::memcpy(eps_out, host.data(), sizeof(double) * h->B);
   return LEMPS_OK;
 }
 

@@ -627,11 +627,77 @@ __global__ void __launch_bounds__(kGemmThreads) k_split(SimView<R> s, int q, int
 
 // ---- layer bookkeeping: eps_tot += 4 sqrt(2 sum_k eps_k) (App. B) -------------
 template <class R>
-__global__ void k_layer_end(SimView<R> s) {
+__global__ void k_layer_end(SimView<R> s, double* hist, int hist_stride, int layer) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= s.B) return;
-  s.eps_tot[t] += 4.0 * sqrt(2.0 * s.eps_layer[t]);
+  const double e = 4.0 * sqrt(2.0 * s.eps_layer[t]);
+  s.eps_tot[t] += e;
   s.eps_layer[t] = 0.0;
+  if (hist) hist[t * hist_stride + layer] = e;   // per-layer history (concentration bound)
+}
+
+// Concentration-improved bound (Sec. III.C; appendix on concentration):
+// out[t] = sum_l w(L - 1 - l) hist[t][l] over the L layers, w(k) = alpha^k
+// (kind 0, param alpha) or min(sqrt(8 n) (1 - p)^k, 1) (kind 1, param p),
+// capped like the plain bound (kept when <= eps_max - 2, else eps_max).
+__global__ void k_eps_weighted(const double* hist, int hist_stride, int64_t B, int L, int kind, double param,
+                               int n, double eps_max, double* out) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= B) return;
+  const double c = sqrt(8.0 * (double)n);
+  double e = 0.0;
+  for (int l = 0; l < L; ++l) {
+    const int k = L - 1 - l;
+    const double w = (kind == 0) ? pow(param, (double)k) : fmin(c * pow(1.0 - param, (double)k), 1.0);
+    e += w * hist[t * hist_stride + l];
+  }
+  out[t] = (e <= eps_max - 2.0) ? e : eps_max;
+}
+
+// Output-distribution sampling (Lemma sampling_reduction): with the centre on
+// site 0 (sites 1.. right-orthonormal), bit k of a shot is drawn from the
+// conditional weights p_s = ||v A_k[:, s, :]||^2 of the running row vector v
+// (v = [1] before site 0, then v <- v A_k[:, b, :] / sqrt(p_b)): bit 0 when
+// u (p0 + p1) < p0, u = Philox(seed; trajectory id, 2^62 + shot, k), a counter
+// domain the noise sites never use.  One CTA per (trajectory, shot); v and the
+// products in FP64.
+template <class R>
+__global__ void __launch_bounds__(256) k_sample_bits(SimView<R> s, int n_shots, uint64_t seed, int64_t traj_offset,
+                                                     uint8_t* out) {
+  const int64_t t = blockIdx.x;
+  const int shot = blockIdx.y;
+  if (t >= s.B) return;
+  __shared__ zd v[256], w0s[256], w1s[256];
+  __shared__ double red[32];
+  const int32_t* bd = s.bond + t * (s.n + 1);
+  if (threadIdx.x == 0) v[0] = mk(1.0, 0.0);
+  __syncthreads();
+  for (int k = 0; k < s.n; ++k) {
+    const int dl = bd[k], dr = bd[k + 1], capr = s.cap[k + 1];
+    const cpx<R>* A = site_ptr(s, k, t);
+    double part0 = 0.0, part1 = 0.0;
+    for (int b = threadIdx.x; b < dr; b += blockDim.x) {
+      zd w0 = mk(0.0, 0.0), w1 = mk(0.0, 0.0);
+      for (int a = 0; a < dl; ++a) {
+        const zd va = v[a];
+        cfma(w0, va, cast<double>(A[(int64_t)(a * 2) * capr + b]));
+        cfma(w1, va, cast<double>(A[(int64_t)(a * 2 + 1) * capr + b]));
+      }
+      w0s[b] = w0;
+      w1s[b] = w1;
+      part0 += norm2(w0);
+      part1 += norm2(w1);
+    }
+    const double p0 = block_sum(part0, red);
+    const double p1 = block_sum(part1, red);
+    const double u = philox_uniform(seed, (uint64_t)(traj_offset + t), (1ull << 62) + (uint64_t)shot, (uint64_t)k);
+    const int bit = (u * (p0 + p1) < p0) ? 0 : 1;
+    const double pb = bit ? p1 : p0;
+    const double sc = pb > 0.0 ? 1.0 / sqrt(pb) : 0.0;
+    for (int b = threadIdx.x; b < dr; b += blockDim.x) v[b] = sc * (bit ? w1s[b] : w0s[b]);
+    if (threadIdx.x == 0) out[(t * n_shots + shot) * (int64_t)s.n + k] = (uint8_t)bit;
+    __syncthreads();
+  }
 }
 
 // ---- measure helpers ------------------------------------------------------------

@@ -28,7 +28,7 @@ FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void
 
 EXPORTED = ["sim_create", "apply_layer", "unravel_opt", "sample_branch", "measure", "sim_export_mps",
             "sim_sync", "sim_profile", "destroy", "unravel_grad", "unravel_descend", "unravel_grad_noalloc",
-            "lemps_last_error"]
+            "sample_bitstrings", "eps_concentrated", "lemps_last_error"]
 KERNEL_KINDS = ["move", "contract", "unravel", "gram", "eig", "split", "other"]
 
 
@@ -88,6 +88,8 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     lib.sample_branch.argtypes = [vp, i64, i32, ctypes.POINTER(i32)]
     lib.measure.argtypes = [vp, ctypes.POINTER(Measurement)]
     lib.sim_export_mps.argtypes = [vp, i64, ctypes.POINTER(i32), dp]
+    lib.sample_bitstrings.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_uint8)]
+    lib.eps_concentrated.argtypes = [vp, i32, ctypes.c_double, dp, dp]
     lib.sim_sync.argtypes = [vp]
     lib.sim_profile.argtypes = [vp, i32, dp, ctypes.POINTER(i64)]
     lib.destroy.argtypes = [vp]
@@ -173,6 +175,23 @@ class Simulation:
         for layer in circuit.layers:
             self.apply_layer(layer)
 
+    def sample_bitstrings(self, n_shots: int) -> np.ndarray:
+        """[n_traj, n_shots, n] uint8 computational-basis samples of every
+        trajectory's current state (sample_bitstrings)."""
+        out = np.empty((self.B, int(n_shots), self.n), dtype=np.uint8)
+        _check(load().sample_bitstrings(self._h, int(n_shots), _ptr(out, ctypes.c_uint8)), "sample_bitstrings")
+        return out
+
+    def eps_concentrated(self, kind: str, param: float):
+        """(per-trajectory bounds, mean) of the concentration-improved error
+        bound; kind "alpha" (param = alpha) or "depolarizing" (param = p)."""
+        k = {"alpha": 0, "depolarizing": 1}[kind]
+        out = np.empty(self.B, dtype=np.float64)
+        hat = ctypes.c_double(0.0)
+        _check(load().eps_concentrated(self._h, k, float(param), _ptr(out, ctypes.c_double), ctypes.byref(hat)),
+               "eps_concentrated")
+        return out, hat.value
+
     def sample_branch(self, gate: int, slot: int) -> np.ndarray:
         out = np.empty(self.B, dtype=np.int32)
         _check(load().sample_branch(self._h, gate, slot, _ptr(out, ctypes.c_int32)), "sample_branch")
@@ -246,6 +265,14 @@ def apply_layer(sim: Simulation, layer) -> None:
 
 def sample_branch(sim: Simulation, gate: int, slot: int) -> np.ndarray:
     return sim.sample_branch(gate, slot)
+
+
+def sample_bitstrings(sim: Simulation, n_shots: int) -> np.ndarray:
+    return sim.sample_bitstrings(n_shots)
+
+
+def eps_concentrated(sim: Simulation, kind: str, param: float):
+    return sim.eps_concentrated(kind, param)
 
 
 def measure(sim: Simulation, per_trajectory: bool = True) -> dict:

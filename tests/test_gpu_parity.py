@@ -289,6 +289,63 @@ def test_global_layering_limits(L):
         L.Simulation(8, 16, 2, layering="sideways")
 
 
+def test_sample_bitstrings_match_oracle(L):
+    """Output-distribution sampling (Lemma sampling_reduction), FP64: every
+    shot's bitstring equals the oracle's sequential sampling of the same
+    trajectory's dense state on the same Philox counters."""
+    circ = I.workload_small_exact(seed=0)["circuit"]
+    sim, res, br = run_gpu(L, circ, 16, 8, seed=3)
+    bits = sim.sample_bitstrings(4)
+    bits2 = sim.sample_bitstrings(4)
+    sim.destroy()
+    assert np.array_equal(bits, bits2)     # same counters, same state
+    n = circ.n_qubits
+    for t in range(8):
+        psi = T.dense_trajectory(circ, t, 3).state
+        for shot in range(4):
+            assert np.array_equal(bits[t, shot], T.sample_bitstring_dense(psi, n, 3, t, shot))
+
+
+def test_sample_bitstrings_reproduce_the_noisy_distribution(L):
+    """Mixed precision, one shot per trajectory over 512 trajectories: <Z_i>
+    and <Z_i Z_i+1> from the bits match exact density-matrix evolution within
+    4 standard errors."""
+    circ = I.workload_small_exact(seed=0)["circuit"]
+    sim, _, _ = run_gpu(L, circ, 16, 512, seed=6, precision="mixed")
+    bits = sim.sample_bitstrings(1)[:, 0, :]
+    sim.destroy()
+    rho = T.density_evolution(circ)
+    zr, zzr = T.density_observables(rho, circ.n_qubits)
+    sgn = 1.0 - 2.0 * bits
+    mz, sz = T.trajectory_statistics(sgn)
+    mzz, szz = T.trajectory_statistics(sgn[:, :-1] * sgn[:, 1:])
+    z = np.concatenate([(mz - zr) / np.maximum(sz, 1e-3), (mzz - zzr) / np.maximum(szz, 1e-3)])
+    assert np.max(np.abs(z)) < 4.0, z
+
+
+def test_eps_concentrated_matches_oracle(L):
+    """Concentration-improved bound (Sec. III.C): per trajectory equal to the
+    oracle's weighting of its per-layer errors; alpha = 1 is the plain bound."""
+    circ = I.random_brickwork(10, 6, I.depolarizing_kraus(0.05), seed=4)
+    sim, res, _ = run_gpu(L, circ, 4, 8, seed=1, cutoff=1e-14)
+    e1, _ = sim.eps_concentrated("alpha", 1.0)
+    ea, ha = sim.eps_concentrated("alpha", 0.7)
+    ed, _ = sim.eps_concentrated("depolarizing", 0.05)
+    with pytest.raises(L.LempsError) as e:
+        sim.eps_concentrated("alpha", 0.0)
+    assert e.value.status == L.LEMPS_EINVAL
+    with pytest.raises(L.LempsError):
+        sim.sample_bitstrings(0)
+    sim.destroy()
+    assert np.allclose(e1, res["eps_bound"], atol=1e-12)
+    assert abs(ha - ea.mean()) < 1e-15
+    for t in range(8):
+        ref = T.mps_trajectory(circ, t, 1, 4, cutoff=1e-14)
+        assert abs(ea[t] - T.concentrated_bound(ref.eps_layers, "alpha", 0.7, 10)) < 1e-9
+        assert abs(ed[t] - T.concentrated_bound(ref.eps_layers, "depolarizing", 0.05, 10)) < 1e-9
+    assert (ea <= e1 + 1e-15).all() and ea.max() > 0.0
+
+
 def test_traj_offset_shards_reproduce_the_full_run(L):
     """Trajectory ids key the Philox counter, so two shards reproduce one run."""
     circ = I.random_brickwork(6, 4, I.depolarizing_kraus(0.05), seed=8)
