@@ -452,3 +452,20 @@ def test_autograd_function_backward(L):
     cost.sum().backward()
     _, grad, _ = L.unravel_grad(th, p, h.detach())
     assert torch.allclose(h.grad, grad)
+
+
+# --- Lindbladian front end ----------------------------------------------------------
+
+def test_lindblad_circuit_matches_oracle(L):
+    """A Trotterized Heisenberg chain with decay (Lindbladian front end) runs
+    through the library: per trajectory equal to the oracle's dense trajectory
+    of the same circuit (FP64, no truncation)."""
+    from paper_2508_05745_gb300 import lindblad as LB
+    circ = LB.heisenberg_amplitude_damping(6, 0.3, 0.1, 4)
+    sim, res, br = run_gpu(L, circ, 8, 8, seed=2)
+    sim.destroy()
+    for t in range(8):
+        ref = T.dense_trajectory(circ, t, 2)
+        assert list(br[t]) == ref.branch
+        assert np.allclose(res["z"][t], ref.z, atol=1e-10)
+        assert abs(res["s_half"][t] - ref.s_half) < 1e-10
