@@ -126,7 +126,24 @@ def gates_in(circ, layers):
 
 # --- the GPU arm ------------------------------------------------------------------------
 
-def run_arm(L, torch, w, sizes, precision, args, pre, warm, steps, profile_step=False, e2e=False):
+def trajectory_offsets(rank, per_rank, sizes):
+    """Replicas: disjoint global trajectory ids for every (rank, size handle).
+    Handle i of rank r starts at (r * len(sizes) + i) * per_rank; the Philox
+    counters are keyed by these ids, so no two handles share a trajectory."""
+    return {n: (rank * len(sizes) + i) * per_rank for i, n in enumerate(sorted(sizes))}
+
+
+def combine_over_ranks(torch, dist, ms, updates, device):
+    """Job time = the slowest rank's (max), bond updates summed over ranks."""
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    u = torch.tensor([float(updates)], dtype=torch.float64, device=device)
+    dist.all_reduce(u)
+    return float(t.item()), float(u.item())
+
+
+def run_arm(L, torch, w, sizes, precision, args, pre, warm, steps, profile_step=False, e2e=False, offsets=None,
+            barrier=None):
     """Create one Simulation per system size, pre-evolve, warm up, time `steps`
     layers.  Returns dict with timing, per-kernel profile and the sims."""
     cutoff = 1e-12 if precision == "mixed" else 1e-20
@@ -138,6 +155,7 @@ def run_arm(L, torch, w, sizes, precision, args, pre, warm, steps, profile_step=
         if b == 0:
             continue
         sims[n] = L.Simulation(n, args.chi, b, seed=args.seed, precision=precision, cutoff=cutoff,
+                               traj_offset=(offsets or {}).get(n, 0),
                                log_capacity=w["circuits"][n].n_gates, stream=torch.cuda.Stream())
     stream = torch.cuda.current_stream()
 
@@ -158,6 +176,8 @@ def run_arm(L, torch, w, sizes, precision, args, pre, warm, steps, profile_step=
     for l in range(pre + warm):
         step(l)
     torch.cuda.synchronize()
+    if barrier:
+        barrier()
     t0 = l0 = pre + warm
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
@@ -167,6 +187,8 @@ def run_arm(L, torch, w, sizes, precision, args, pre, warm, steps, profile_step=
     join()
     ev1.record(stream)
     torch.cuda.synchronize()
+    if barrier:
+        barrier()
     ms = ev0.elapsed_time(ev1)
     updates = sum(sum(gates_in(w["circuits"][n], range(t0, t0 + steps))) * s.B for n, s in sims.items())
     out = dict(ms=ms, updates=updates, sims=sims, next_layer=t0 + steps, steps=steps)
@@ -318,21 +340,21 @@ def main():
     else:
         sizes = {n: per_rank // len(want) for n in want}
     log(f"sizes {sizes}")
+    offsets = trajectory_offsets(rank, per_rank, sizes)
+    barrier = None
+    if world > 1:
+        import torch.distributed as dist
+        barrier = dist.barrier
     clocks = ClockSampler(local)
     clocks.start()
     mixed = run_arm(L, torch, w, sizes, "mixed", args, args.pre_layers, args.warmup, args.steps,
-                    profile_step=True, e2e=not args.no_e2e)
+                    profile_step=True, e2e=not args.no_e2e, offsets=offsets, barrier=barrier)
     log(f"mixed arm: {mixed['updates']} updates in {mixed['ms']:.1f} ms")
     clk = clocks.stop()
     ms = mixed["ms"]
     if world > 1:
         import torch.distributed as dist
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        u = torch.tensor([float(mixed["updates"])], device="cuda")
-        dist.all_reduce(u)
-        total_updates = u.item()
+        ms, total_updates = combine_over_ranks(torch, dist, ms, mixed["updates"], "cuda")
     else:
         total_updates = mixed["updates"]
     value = total_updates / (ms / 1000.0)
