@@ -83,7 +83,9 @@ typedef enum {
 } lemps_layering;
 
 /* Device allocator hook (PyTorch's caching allocator from Python).  NULL
- * alloc means cudaMalloc / cudaFree. */
+ * alloc means cudaMalloc / cudaFree.  Blocks must be 16-byte aligned (the
+ * kernels stream workspaces with bulk copies); sim_create fails with
+ * LEMPS_EINVAL on a misaligned block. */
 typedef void* (*lemps_alloc_fn)(size_t bytes, void* stream, void* ctx);
 typedef void (*lemps_free_fn)(void* ptr, size_t bytes, void* stream, void* ctx);
 
@@ -124,7 +126,9 @@ typedef struct {
   double* zz;          /* [n_traj][n-1]   <Z_i Z_{i+1}> */
   double* s_half;      /* [n_traj]        entropy (nats) of bond n/2 */
   double* eps_bound;   /* [n_traj]        error bound of Thm. 1 / App. B */
-  int32_t* status;     /* [n_traj]        0 = ok, else a LEMPS_ENUMERIC reason code */
+  int32_t* status;     /* [n_traj]        0 = ok, else OR of LEMPS_ENUMERIC reason bits:
+                                          1 NaN/Inf, 2 lost norm, 4 eigensolver cap,
+                                          8 shape (internal), 16 copy time limit (internal) */
   /* reductions over trajectories, host, required */
   double* z_mean;      /* [n] */
   double* z_stderr;    /* [n] */

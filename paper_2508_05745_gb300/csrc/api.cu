@@ -426,10 +426,11 @@ lemps_status sim_create(const lemps_config* cfg, lemps_handle* out) {
   h->ws_stride = (int64_t)(2 * h->cap_max) * (2 * h->cap_max);
   h->log_cap = cfg->log_capacity > 0 ? cfg->log_capacity : 0;
   h->layer_cap = (int64_t)(n / 2 + 1) * 16 + 4 * kMaxKraus;
-  bool ok = true;
+  bool ok = true, aligned = true;
   auto A = [&](size_t bytes) {
     void* p = h->dalloc(bytes);
     if (!p) ok = false;
+    if (((uintptr_t)p & 15) != 0) aligned = false;
     return p;
   };
   h->mps = A(h->elem * tot);
@@ -453,10 +454,11 @@ lemps_status sim_create(const lemps_config* cfg, lemps_handle* out) {
   h->eps_hist = (double*)A(sizeof(double) * kEpsHistLayers * h->B);
   h->obs = (double*)A(sizeof(double) * h->B * (2 * n + 1));
   h->stats = (double*)A(sizeof(double) * (4 * n + 4));
-  if (!ok) {
+  if (!ok || !aligned) {
     h->release();
     delete h;
-    return fail(LEMPS_ENOMEM, "sim_create: device allocation failed");
+    return ok ? fail(LEMPS_EINVAL, "sim_create: the allocator returned a block that is not 16-byte aligned")
+              : fail(LEMPS_ENOMEM, "sim_create: device allocation failed");
   }
   cudaMemsetAsync(h->mps, 0, h->elem * tot, h->stream);
   if (h->log_cap > 0) cudaMemsetAsync(h->blog, 0xff, h->log_cap * 2 * h->B, h->stream);

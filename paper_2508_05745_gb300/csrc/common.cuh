@@ -73,8 +73,48 @@ enum TrajStatus : int32_t {
   TS_NAN = 1,        // NaN / Inf in a reduced density or branch weight
   TS_NORM = 2,       // two-site tensor lost its norm
   TS_JACOBI = 4,     // eigensolver hit its sweep cap above tolerance
-  TS_SHAPE = 8       // bond dimensions outside capacity (internal error)
+  TS_SHAPE = 8,      // bond dimensions outside capacity (internal error)
+  TS_COPY = 16       // an asynchronous copy missed its time limit (internal error)
 };
+
+// ---- mbarrier and 1-D bulk copies (TMA engine) ------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+// Makes barrier initialization, and this thread's earlier generic-proxy
+// writes (shared or global), visible to later bulk copies.
+__device__ __forceinline__ void fence_for_bulk_copies() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("fence.proxy.async;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+// Global -> shared copy of `bytes` (a multiple of 16; both addresses 16-byte
+// aligned) that completes its byte count on `bar`.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+// Waits for the phase of parity `parity` of `bar` to complete; gives up and
+// returns false after about two seconds (2^32 SM cycles).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const long long t0 = clock64();
+  for (;;) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (clock64() - t0 > (1LL << 32)) return false;
+  }
+}
 
 // ---- block reductions ---------------------------------------------------------
 template <class T>

@@ -7,7 +7,7 @@
 // cutoff * trace}, n); the count comes from one Sturm sequence at
 // cutoff * trace, so eigenvalues that will be discarded are never computed.
 //
-// Layout: G (n x n row-major, Hermitian) in ws1, overwritten.  Householder
+// Layout (16-byte aligned, n even): G (n x n row-major, Hermitian) in ws1, overwritten.  Householder
 // vectors in ws3 (row j holds v_j, unit norm, entries > j).  Eigenvectors are
 // written column-major to ws2: U[k * n + i], k < keep.  Eigenvalues (double,
 // descending) to evals[0..keep), keep and the trace to kept[] / trace[].
@@ -29,6 +29,7 @@ struct HeevView {
   int32_t* kept;    // [B]
   double* trace;    // [B]
   int32_t* bond;    // [B][n+1]
+  int32_t* status;  // [B] TrajStatus bits
   int32_t nq;       // qubits (bond row length n+1)
   int32_t chi;
   int64_t B;
@@ -67,6 +68,18 @@ struct HeevSmem {
 };
 
 __device__ __forceinline__ int pidx(int r, int c) { return r * (r + 1) / 2 + c; }
+
+// Two adjacent complex entries from 16-byte aligned global memory.
+__device__ __forceinline__ void load_pair(const cpx<float>* p, cpx<float>& a, cpx<float>& b) {
+  const float4 t = *reinterpret_cast<const float4*>(p);
+  a = mk(t.x, t.y);
+  b = mk(t.z, t.w);
+}
+__device__ __forceinline__ void load_pair(const cpx<double>* p, cpx<double>& a, cpx<double>& b) {
+  const double2 t0 = reinterpret_cast<const double2*>(p)[0], t1 = reinterpret_cast<const double2*>(p)[1];
+  a = mk(t0.x, t0.y);
+  b = mk(t1.x, t1.y);
+}
 
 // mode / q select the matrix size as in gram_size(); want_vectors = 0 returns
 // eigenvalues only (all n of them when cutoff = 0).
@@ -168,19 +181,34 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
       acc.im = warp_sum(acc.im);
       if (lane == 0) cc[kk] = acc;
     }
-    // y = G_sub v from the original (read-only) G: four rows per warp in
-    // flight, their eight partial sums reduced by one butterfly
+    // y = G_sub v from the original (read-only) G, which is served from L2:
+    // four rows per warp, each lane loading two adjacent entries of a row at
+    // a time (16-byte aligned: the segment starts at the even column c0 <= j +
+    // 1) with two such loads per row in flight; the eight partial sums of the
+    // four rows are reduced by one butterfly.
+    const int c0 = (j + 1) & ~1;
+    const int off = j + 1 - c0;        // 1: column c0 = j lies left of the block (weight 0)
+    const int npair = (n - c0) >> 1;
     for (int r0 = 4 * warp; r0 < m; r0 += 4 * nwarp) {
       const int nq = min(4, m - r0);
-      const cpx<R>* row = G + (int64_t)(j + 1 + r0) * n + (j + 1);
+      const cpx<R>* row = G + (int64_t)(j + 1 + r0) * n + c0;
       cpx<R> acc[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) acc[q] = mk<R>(0, 0);
-      for (int c = lane; c < m; c += 32) {
-        const cpx<R> x = sv[c];
+#pragma unroll 2
+      for (int p2 = lane; p2 < npair; p2 += 32) {
+        const int c = 2 * p2 - off;    // local index of the first entry of the pair
+        const cpx<R> x0 = (c >= 0) ? sv[c] : mk<R>(0, 0), x1 = sv[c + 1];
+        cpx<R> a0[4], a1[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q)
-          if (q < nq) cfma(acc[q], row[(int64_t)q * n + c], x);
+          if (q < nq) load_pair(row + (int64_t)q * n + 2 * p2, a0[q], a1[q]);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (q < nq) {
+            cfma(acc[q], a0[q], x0);
+            cfma(acc[q], a1[q], x1);
+          }
       }
       R d[8];
 #pragma unroll
@@ -439,14 +467,22 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
       sec[n - 2] = aeff(b, a);
     }
     sd[n - 1] = aeff(b, b).re;
-    // phase normalization: delta_{j+1} = delta_j e_j / |e_j|
+  }
+  __syncthreads();
+  // phase normalization delta_{j+1} = delta_j e_j / |e_j|: the moduli and unit
+  // factors in parallel, their running product by one thread
+  for (int j = threadIdx.x; j + 1 < n; j += blockDim.x) {
+    const R aa = sqrt(norm2(sec[j]));
+    se[j] = aa;
+    se2[j] = aa * aa;
+    sv[j] = (aa > 0) ? mk<R>(sec[j].re / aa, sec[j].im / aa) : mk<R>(1, 0);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
     cpx<R> dl = mk<R>(1, 0);
     sph[0] = dl;
     for (int j = 0; j + 1 < n; ++j) {
-      R aa = sqrt(norm2(sec[j]));
-      se[j] = aa;
-      se2[j] = aa * aa;
-      if (aa > 0) dl = dl * mk<R>(sec[j].re / aa, sec[j].im / aa);
+      dl = dl * sv[j];
       sph[j + 1] = dl;
     }
   }
@@ -534,16 +570,19 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
         const int k = k0 + kk;
         R* w3 = wsp + koff + kk;
         const R lam = (R)ev[k];
+        // w3[i][0] holds 1 / d_i, so that the solves multiply
+        auto recip = [](R x) { return sizeof(R) == 4 ? (R)__fdividef(1.0f, (float)x) : (R)1 / x; };
         R dprev = sd[0] - lam;
         if (fabs(dprev) < pivmin) dprev = pivmin;
-        w3[(0 * 3 + 0) * ld] = dprev;
+        R rprev = recip(dprev);
+        w3[(0 * 3 + 0) * ld] = rprev;
         for (int i = 0; i + 1 < n; ++i) {
-          R li = se[i] / dprev;
+          R li = se[i] * rprev;
           w3[(i * 3 + 1) * ld] = li;
           R dn = (sd[i + 1] - lam) - li * se[i];
           if (fabs(dn) < pivmin) dn = pivmin;
-          w3[((i + 1) * 3 + 0) * ld] = dn;
-          dprev = dn;
+          rprev = recip(dn);
+          w3[((i + 1) * 3 + 0) * ld] = rprev;
         }
         for (int i = 0; i < n; ++i) w3[(i * 3 + 2) * ld] = (R)start_entry(k, i);
         for (int iter = 0; iter < 2; ++iter) {
@@ -552,11 +591,11 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
             y = w3[(i * 3 + 2) * ld] - w3[((i - 1) * 3 + 1) * ld] * y;
             w3[(i * 3 + 2) * ld] = y;
           }
-          R zn = w3[((n - 1) * 3 + 2) * ld] / w3[((n - 1) * 3 + 0) * ld];
+          R zn = w3[((n - 1) * 3 + 2) * ld] * w3[((n - 1) * 3 + 0) * ld];
           w3[((n - 1) * 3 + 2) * ld] = zn;
           R amax = fabs(zn);
           for (int i = n - 2; i >= 0; --i) {
-            zn = w3[(i * 3 + 2) * ld] / w3[(i * 3 + 0) * ld] - w3[(i * 3 + 1) * ld] * zn;
+            zn = w3[(i * 3 + 2) * ld] * w3[(i * 3 + 0) * ld] - w3[(i * 3 + 1) * ld] * zn;
             w3[(i * 3 + 2) * ld] = zn;
             amax = fmax(amax, fabs(zn));
           }
@@ -762,9 +801,13 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
     }
   }
   // ---- phase 5: back-transformation U = Q D z --------------------------------
-  // Each warp owns NCOL columns held in registers (PER entries per lane each);
-  // reflectors are staged through shared memory in chunks of rc rows (row
-  // stride 32 * nper, zero-padded), placed after the shared-memory copy of z.
+  // Each warp owns NCOL columns held in registers (PER entries per lane each).
+  // The reflectors stream through two shared-memory buffers of rc rows (row
+  // stride ldv = 32 * nper, zero-padded), placed after the shared-memory copy
+  // of z and filled by bulk copies on one mbarrier each: the copy of chunk
+  // g + 1 runs while chunk g is applied, and a buffer is refilled (chunk g +
+  // 2) once every warp has passed the barrier that ends chunk g.  Chunks run
+  // from the last reflector down and repeat for each pass over the columns.
   // Reflector j is zero in rows <= j, so 32-row groups below it are skipped.
   // The NCOL complex dot products of a reflector are summed over the warp by
   // one reduce-scatter / broadcast butterfly.
@@ -774,11 +817,46 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
   const int nper = (n + 31) >> 5;
   const int ldv = 32 * nper;
   const size_t zbytes = zsm ? zs_bytes + cb_bytes : 0;
-  const int rc = min(32, (int)((HeevSmem<R>::kBytes - zbytes) / ((size_t)ldv * sizeof(cpx<R>))));
-  cpx<R> y[NCOL][PER];
-  cpx<R>* vst = reinterpret_cast<cpx<R>*>(heev_smem + zbytes);
+  const int rc = min(32, (int)((HeevSmem<R>::kBytes - zbytes) / (2 * (size_t)ldv * sizeof(cpx<R>))));
+  if (rc < 1) {   // cannot happen for n <= 256 (the z copy leaves >= 8 n entries)
+    if (threadIdx.x == 0) atomicOr(s.status + t, (int32_t)TS_SHAPE);
+    return;
+  }
+  cpx<R>* vbuf[2];
+  vbuf[0] = reinterpret_cast<cpx<R>*>(heev_smem + zbytes);
+  vbuf[1] = vbuf[0] + (size_t)rc * ldv;
+  __shared__ __align__(8) uint64_t s_bar[2];
+  const int nch = (n >= 3) ? (n - 3) / rc + 1 : 0;   // chunks per pass
   const int ngroups = (keep + NCOL - 1) / NCOL;
   const int passes = (ngroups + nwarp - 1) / nwarp;
+  const int nchunk = nch * passes;
+  auto issue = [&](int g) {   // one thread: copy chunk g into buffer g & 1
+    const int c = g % nch;
+    const int jtop = n - 3 - c * rc, jlo = max(0, jtop - rc + 1), rows = jtop - jlo + 1;
+    uint64_t* bar = &s_bar[g & 1];
+    mbar_expect_tx(bar, (uint32_t)(rows * n * sizeof(cpx<R>)));
+    if (ldv == n) {
+      bulk_g2s(vbuf[g & 1], Hv + (int64_t)jlo * n, (uint32_t)(rows * n * sizeof(cpx<R>)), bar);
+    } else {
+      for (int rr = 0; rr < rows; ++rr)
+        bulk_g2s(vbuf[g & 1] + (size_t)rr * ldv, Hv + (int64_t)(jlo + rr) * n, (uint32_t)(n * sizeof(cpx<R>)), bar);
+    }
+  };
+  if (ldv != n)   // padding columns n .. ldv-1 of both buffers, never copied over
+    for (int e = threadIdx.x; e < 2 * rc * (ldv - n); e += blockDim.x) {
+      const int r = e / (ldv - n), i = n + e % (ldv - n);
+      vbuf[0][(size_t)r * ldv + i] = mk<R>(0, 0);
+    }
+  if (threadIdx.x == 0) {
+    mbar_init(&s_bar[0], 1);
+    mbar_init(&s_bar[1], 1);
+  }
+  // Hv was written with ordinary stores and the buffers last held other data
+  fence_for_bulk_copies();
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int g = 0; g < min(2, nchunk); ++g) issue(g);
+  cpx<R> y[NCOL][PER];
   for (int pass = 0; pass < passes; ++pass) {
     const int k0 = NCOL * (warp + pass * nwarp);
     const bool act = k0 < keep;
@@ -789,14 +867,12 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
         const int i = lane + 32 * a;
         y[c][a] = (i < n && k0 + c < keep) ? sph[i] * Z(k0 + c, i) : mk<R>(0, 0);
       }
-    __syncthreads();
-    for (int jtop = n - 3; jtop >= 0; jtop -= rc) {
-      const int jlo = max(0, jtop - rc + 1);
-      for (int rr = warp; rr <= jtop - jlo; rr += nwarp)
-        for (int i = lane; i < ldv; i += 32)
-          vst[rr * ldv + i] = (i < n) ? Hv[(int64_t)(jlo + rr) * n + i] : mk<R>(0, 0);
-      __syncthreads();
-      if (act) {
+    for (int c = 0; c < nch; ++c) {
+      const int g = pass * nch + c;
+      const int jtop = n - 3 - c * rc, jlo = max(0, jtop - rc + 1);
+      const cpx<R>* vst = vbuf[g & 1];
+      const bool ready = mbar_wait(&s_bar[g & 1], (uint32_t)((g >> 1) & 1));
+      if (act && ready) {
         for (int j = jtop; j >= jlo; --j) {
           const cpx<R>* v = vst + (j - jlo) * ldv;
           const int a0 = (j + 1) >> 5;   // groups a < a0 hold rows <= j only
@@ -809,10 +885,10 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
             vr[a] = (a >= a0 && a < nper) ? v[lane + 32 * a] : mk<R>(0, 0);
             if (a >= a0 && a < nper) {
 #pragma unroll
-              for (int c = 0; c < NCOL; ++c) {
+              for (int c2 = 0; c2 < NCOL; ++c2) {
                 // d_c += conj(v_i) y_c[i]
-                d[2 * c] = fma(vr[a].re, y[c][a].re, fma(vr[a].im, y[c][a].im, d[2 * c]));
-                d[2 * c + 1] = fma(vr[a].re, y[c][a].im, fma(-vr[a].im, y[c][a].re, d[2 * c + 1]));
+                d[2 * c2] = fma(vr[a].re, y[c2][a].re, fma(vr[a].im, y[c2][a].im, d[2 * c2]));
+                d[2 * c2 + 1] = fma(vr[a].re, y[c2][a].im, fma(-vr[a].im, y[c2][a].re, d[2 * c2 + 1]));
               }
             }
           }
@@ -824,20 +900,29 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
           for (int a = 0; a < PER; ++a) {
             if (a >= a0 && a < nper) {
 #pragma unroll
-              for (int c = 0; c < NCOL; ++c) y[c][a] -= vr[a] * mk<R>(dd[2 * c], dd[2 * c + 1]);
+              for (int c2 = 0; c2 < NCOL; ++c2) y[c2][a] -= vr[a] * mk<R>(dd[2 * c2], dd[2 * c2 + 1]);
             }
           }
         }
       }
-      __syncthreads();
+      if (__syncthreads_or(!ready)) {
+        // a copy missed its time limit: flag the trajectory, give the copies
+        // still in flight (chunks g and g + 1) a bounded wait, and stop
+        if (threadIdx.x == 0) {
+          atomicOr(s.status + t, (int32_t)TS_COPY);
+          for (int h = g; h < min(g + 2, nchunk); ++h) mbar_wait(&s_bar[h & 1], (uint32_t)((h >> 1) & 1));
+        }
+        return;
+      }
+      if (threadIdx.x == 0 && g + 2 < nchunk) issue(g + 2);
     }
 #pragma unroll
     for (int a = 0; a < PER; ++a) {
       const int i = lane + 32 * a;
       if (i < n) {
 #pragma unroll
-        for (int c = 0; c < NCOL; ++c)
-          if (k0 + c < keep) U[(int64_t)(k0 + c) * n + i] = y[c][a];
+        for (int c2 = 0; c2 < NCOL; ++c2)
+          if (k0 + c2 < keep) U[(int64_t)(k0 + c2) * n + i] = y[c2][a];
       }
     }
   }

@@ -521,7 +521,7 @@ template <class R>
 HeevView<R> heev_view(const SimView<R>& s) {
   HeevView<R> h;
   h.ws1 = s.ws1; h.ws2 = s.ws2; h.ws3 = s.ws3; h.ws_stride = s.ws_stride;
-  h.evals = s.evals; h.kept = s.kept; h.trace = s.trace; h.bond = s.bond;
+  h.evals = s.evals; h.kept = s.kept; h.trace = s.trace; h.bond = s.bond; h.status = s.status;
   h.nq = s.n; h.chi = s.chi; h.B = s.B;
   return h;
 }
