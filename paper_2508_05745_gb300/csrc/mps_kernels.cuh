@@ -81,27 +81,58 @@ template <class R>
 __device__ void qr_build_t(QrSmem<R>& sm, int pm, int pb) {
   constexpr int NB = QrSmem<R>::NB;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-  // dots D[a][b] = v_a^dagger v_b for a < b, into w (reused), then the recurrence
-  for (int pr = warp; pr < pb * pb; pr += nwarp) {
-    const int a = pr / pb, bb = pr % pb;
-    if (a >= bb) continue;
-    cpx<R> d = mk<R>(0, 0);
-    for (int i = lane; i < pm; i += 32) cfmac(d, sm.vs[a * pm + i], sm.vs[bb * pm + i]);
-    d.re = warp_sum(d.re);
-    d.im = warp_sum(d.im);
-    if (lane == 0) sm.w[a * NB + bb] = d;
+  // D[a][b] = v_a^dagger v_b for a < b, into w (reused).  Warp w takes the
+  // columns b = w and NB - 1 - w (NB - 1 pairs together), eight a at a time
+  // with lanes over rows; one reduce-scatter butterfly sums the eight dots.
+  auto dots = [&](int bcol) {
+    if (bcol >= pb) return;
+    for (int a0 = 0; a0 < bcol; a0 += 8) {
+      R d[16];
+#pragma unroll
+      for (int e = 0; e < 16; ++e) d[e] = 0;
+      for (int i = lane; i < pm; i += 32) {
+        const cpx<R> vb = sm.vs[bcol * pm + i];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          if (a0 + q < bcol) {
+            const cpx<R> va = sm.vs[(a0 + q) * pm + i];
+            d[2 * q] = fma(va.re, vb.re, fma(va.im, vb.im, d[2 * q]));
+            d[2 * q + 1] = fma(va.re, vb.im, fma(-va.im, vb.re, d[2 * q + 1]));
+          }
+        }
+      }
+      const R tot = warp_reduce_scatter<16>(d, lane);
+      const int e = Scatter<16>::index(lane), a = a0 + (e >> 1);
+      if ((lane & 1) == 0 && a < bcol) {
+        if (e & 1) sm.w[a * NB + bcol].im = tot;
+        else sm.w[a * NB + bcol].re = tot;
+      }
+    }
+  };
+  for (int bq = warp; bq < NB / 2; bq += nwarp) {
+    dots(bq);
+    dots(NB - 1 - bq);
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int i = 0; i < pb; ++i) {
-      for (int r = 0; r < i; ++r) {
+  // T recurrence T[0:i, i] = -2 T[0:i, 0:i] D[0:i, i], T[i][i] = 2, by one
+  // warp: lane r keeps row r of T in registers
+  if (warp == 0) {
+    cpx<R> trow[NB];
+#pragma unroll
+    for (int c = 0; c < NB; ++c) trow[c] = mk<R>(0, 0);
+#pragma unroll
+    for (int i = 0; i < NB; ++i) {
+      if (i < pb) {
         cpx<R> acc = mk<R>(0, 0);
-        for (int c = r; c < i; ++c) cfma(acc, sm.tm[r * NB + c], sm.w[c * NB + i]);
-        sm.tm[r * NB + i] = (R)-2 * acc;
+#pragma unroll
+        for (int c = 0; c < i; ++c)
+          if (c >= lane) cfma(acc, trow[c], sm.w[c * NB + i]);
+        trow[i] = (lane < i) ? (R)-2 * acc : mk<R>(lane == i ? 2 : 0, 0);
       }
-      sm.tm[i * NB + i] = mk<R>(2, 0);
-      for (int r = i + 1; r < pb; ++r) sm.tm[r * NB + i] = mk<R>(0, 0);
     }
+    if (lane < NB)
+#pragma unroll
+      for (int c = 0; c < NB; ++c) sm.tm[lane * NB + c] = trow[c];
   }
   __syncthreads();
 }
@@ -120,18 +151,30 @@ __device__ void qr_vdag_y(QrSmem<R>& sm, const cpx<R>* Y, int ldy, int row0, int
   constexpr int HA = NB / 2;
   constexpr int SL = NB * QrSmem<R>::MMAX / 128;   // staged rows per slab
   static_assert(SL == 16 || SL == 32, "slab height");
+  constexpr int PF = SL * 128 / 256;                // staged entries per thread
   cpx<R>* ys = sm.p;
   const int c = threadIdx.x & 127, h = threadIdx.x >> 7;   // 256 threads
   cpx<R> acc[HA];
 #pragma unroll
   for (int a = 0; a < HA; ++a) acc[a] = mk<R>(0, 0);
+  // the next slab's entries are loaded into registers while this one is used
+  cpx<R> pre[PF];
+  auto fetch = [&](int i0) {
+#pragma unroll
+    for (int k = 0; k < PF; ++k) {
+      const int e = threadIdx.x + 256 * k, ii = e & (SL - 1), cc = e / SL;
+      pre[k] = (i0 + ii < pm && cc < ncc) ? Y[(int64_t)(colbase + cc) * ldy + row0 + i0 + ii] : mk<R>(0, 0);
+    }
+  };
+  fetch(0);
   for (int i0 = 0; i0 < pm; i0 += SL) {
-    for (int e = threadIdx.x; e < SL * 128; e += blockDim.x) {
-      const int ii = e & (SL - 1), cc = e / SL;
-      ys[ii * 128 + (cc ^ ii)] =
-          (i0 + ii < pm && cc < ncc) ? Y[(int64_t)(colbase + cc) * ldy + row0 + i0 + ii] : mk<R>(0, 0);
+#pragma unroll
+    for (int k = 0; k < PF; ++k) {
+      const int e = threadIdx.x + 256 * k, ii = e & (SL - 1), cc = e / SL;
+      ys[ii * 128 + (cc ^ ii)] = pre[k];
     }
     __syncthreads();
+    if (i0 + SL < pm) fetch(i0 + SL);
     const int ni = min(SL, pm - i0);
     for (int ii = 0; ii < ni; ++ii) {
       const cpx<R> y = ys[ii * 128 + (c ^ ii)];
@@ -201,17 +244,26 @@ __device__ void qr_apply_block(QrSmem<R>& sm, cpx<R>* Y, int ldy, int row0, int 
     // W = V^dagger Y  (pb x ncc)
     qr_vdag_y(sm, Y, ldy, row0, col0 + c0, pm, pb, ncc);
     __syncthreads();
-    // W <- T W  or  T^dagger W  (in place by rows, top-down for T^dagger? use a copy)
-    for (int e = threadIdx.x; e < ncc; e += blockDim.x) {
+    // W <- T W  or  T^dagger W: thread (e, h) reads column e of W into
+    // registers and, after a barrier, writes its rows [h NB/2, (h+1) NB/2)
+    {
+      const int e = threadIdx.x & 127, h = threadIdx.x >> 7;   // 256 threads
       cpx<R> col[NB];
-      for (int a = 0; a < pb; ++a) col[a] = sm.w[a * 128 + e];
-      for (int a = 0; a < pb; ++a) {
-        cpx<R> acc = mk<R>(0, 0);
-        for (int b = 0; b < pb; ++b) {
-          const cpx<R> tab = adjoint ? conj(sm.tm[b * NB + a]) : sm.tm[a * NB + b];
-          cfma(acc, tab, col[b]);
+#pragma unroll
+      for (int bb = 0; bb < NB; ++bb) col[bb] = (bb < pb && e < ncc) ? sm.w[bb * 128 + e] : mk<R>(0, 0);
+      __syncthreads();
+      if (e < ncc) {
+#pragma unroll
+        for (int q = 0; q < NB / 2; ++q) {
+          const int a = h * (NB / 2) + q;
+          if (a < pb) {
+            cpx<R> acc = mk<R>(0, 0);
+#pragma unroll
+            for (int bb = 0; bb < NB; ++bb)
+              if (bb < pb) cfma(acc, adjoint ? conj(sm.tm[bb * NB + a]) : sm.tm[a * NB + bb], col[bb]);
+            sm.w[a * 128 + e] = acc;
+          }
         }
-        sm.w[a * 128 + e] = acc;
       }
     }
     __syncthreads();
