@@ -81,6 +81,37 @@ __device__ __forceinline__ void load_pair(const cpx<double>* p, cpx<double>& a, 
   b = mk(t1.x, t1.y);
 }
 
+// y_c <- (I - 2 v v^dagger) y_c for a warp's NCOL columns (PER entries per
+// lane, row lane + 32 a).  Groups a < A0 are zero in v and are skipped at
+// compile time; the NCOL complex dots are summed over the warp by one
+// reduce-scatter / broadcast butterfly.
+template <class R, int NCOL, int PER, int A0>
+__device__ __forceinline__ void bt_reflector(cpx<R> (&y)[NCOL][PER], const cpx<R>* v, int lane, int nper) {
+  constexpr int NV = 2 * NCOL;
+  R d[NV];
+#pragma unroll
+  for (int e = 0; e < NV; ++e) d[e] = 0;
+  cpx<R> vr[PER];
+#pragma unroll
+  for (int a = A0; a < PER; ++a) {
+    vr[a] = (a < nper) ? v[lane + 32 * a] : mk<R>(0, 0);
+#pragma unroll
+    for (int c = 0; c < NCOL; ++c) {
+      // d_c += conj(v_i) y_c[i]
+      d[2 * c] = fma(vr[a].re, y[c][a].re, fma(vr[a].im, y[c][a].im, d[2 * c]));
+      d[2 * c + 1] = fma(vr[a].re, y[c][a].im, fma(-vr[a].im, y[c][a].re, d[2 * c + 1]));
+    }
+  }
+  const R tot = warp_reduce_scatter<NV>(d, lane);
+  R dd[NV];
+#pragma unroll
+  for (int e = 0; e < NV; ++e) dd[e] = (R)2 * __shfl_sync(0xffffffffu, tot, Scatter<NV>::source(e));
+#pragma unroll
+  for (int a = A0; a < PER; ++a)
+#pragma unroll
+    for (int c = 0; c < NCOL; ++c) y[c][a] -= vr[a] * mk<R>(dd[2 * c], dd[2 * c + 1]);
+}
+
 // mode / q select the matrix size as in gram_size(); want_vectors = 0 returns
 // eigenvalues only (all n of them when cutoff = 0).
 template <class R>
@@ -808,12 +839,10 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
   // g + 1 runs while chunk g is applied, and a buffer is refilled (chunk g +
   // 2) once every warp has passed the barrier that ends chunk g.  Chunks run
   // from the last reflector down and repeat for each pass over the columns.
-  // Reflector j is zero in rows <= j, so 32-row groups below it are skipped.
-  // The NCOL complex dot products of a reflector are summed over the warp by
-  // one reduce-scatter / broadcast butterfly.
+  // Reflector j is zero in rows <= j, so the 32-row groups above it are
+  // skipped (bt_reflector, specialized on the first live group).
   constexpr int PER = 8;  // n <= 256 -> 8 elements per lane
   constexpr int NCOL = sizeof(R) == 4 ? 4 : 2;
-  constexpr int NV = 2 * NCOL;
   const int nper = (n + 31) >> 5;
   const int ldv = 32 * nper;
   const size_t zbytes = zsm ? zs_bytes + cb_bytes : 0;
@@ -875,33 +904,15 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
       if (act && ready) {
         for (int j = jtop; j >= jlo; --j) {
           const cpx<R>* v = vst + (j - jlo) * ldv;
-          const int a0 = (j + 1) >> 5;   // groups a < a0 hold rows <= j only
-          R d[NV];
-#pragma unroll
-          for (int e = 0; e < NV; ++e) d[e] = 0;
-          cpx<R> vr[PER];
-#pragma unroll
-          for (int a = 0; a < PER; ++a) {
-            vr[a] = (a >= a0 && a < nper) ? v[lane + 32 * a] : mk<R>(0, 0);
-            if (a >= a0 && a < nper) {
-#pragma unroll
-              for (int c2 = 0; c2 < NCOL; ++c2) {
-                // d_c += conj(v_i) y_c[i]
-                d[2 * c2] = fma(vr[a].re, y[c2][a].re, fma(vr[a].im, y[c2][a].im, d[2 * c2]));
-                d[2 * c2 + 1] = fma(vr[a].re, y[c2][a].im, fma(-vr[a].im, y[c2][a].re, d[2 * c2 + 1]));
-              }
-            }
-          }
-          const R tot = warp_reduce_scatter<NV>(d, lane);
-          R dd[NV];
-#pragma unroll
-          for (int e = 0; e < NV; ++e) dd[e] = (R)2 * __shfl_sync(0xffffffffu, tot, Scatter<NV>::source(e));
-#pragma unroll
-          for (int a = 0; a < PER; ++a) {
-            if (a >= a0 && a < nper) {
-#pragma unroll
-              for (int c2 = 0; c2 < NCOL; ++c2) y[c2][a] -= vr[a] * mk<R>(dd[2 * c2], dd[2 * c2 + 1]);
-            }
+          switch ((j + 1) >> 5) {   // groups a < (j + 1) / 32 hold rows <= j only
+            case 0: bt_reflector<R, NCOL, PER, 0>(y, v, lane, nper); break;
+            case 1: bt_reflector<R, NCOL, PER, 1>(y, v, lane, nper); break;
+            case 2: bt_reflector<R, NCOL, PER, 2>(y, v, lane, nper); break;
+            case 3: bt_reflector<R, NCOL, PER, 3>(y, v, lane, nper); break;
+            case 4: bt_reflector<R, NCOL, PER, 4>(y, v, lane, nper); break;
+            case 5: bt_reflector<R, NCOL, PER, 5>(y, v, lane, nper); break;
+            case 6: bt_reflector<R, NCOL, PER, 6>(y, v, lane, nper); break;
+            default: bt_reflector<R, NCOL, PER, 7>(y, v, lane, nper); break;
           }
         }
       }

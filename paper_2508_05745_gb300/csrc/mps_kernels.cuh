@@ -356,6 +356,37 @@ __device__ void householder_qr(cpx<R>* X, cpx<R>* V, cpx<R>* Qm, int m, int n, i
   }
 }
 
+// dst[q * ldd + p] = src[p * lds + q] for p < P, q < Q: a transposing copy
+// through shared memory (TP x TQ tiles, rows padded by one entry), with
+// coalesced global loads and stores; a tile's loads are all issued before
+// its stores.  `tile` holds TP * (TQ + 1) entries; 256 threads.
+template <class R>
+__device__ void transpose_copy(cpx<R>* dst, int64_t ldd, const cpx<R>* src, int64_t lds, int P, int Q, cpx<R>* tile) {
+  constexpr int TP = 32, TQ = sizeof(R) == 4 ? 128 : 64, LDT = TQ + 1;
+  constexpr int PT = TP * TQ / kGemmThreads;
+  for (int p0 = 0; p0 < P; p0 += TP)
+    for (int q0 = 0; q0 < Q; q0 += TQ) {
+      cpx<R> r[PT];
+#pragma unroll
+      for (int k = 0; k < PT; ++k) {
+        const int e = threadIdx.x + kGemmThreads * k, pp = e / TQ, qq = e % TQ;
+        r[k] = (p0 + pp < P && q0 + qq < Q) ? src[(int64_t)(p0 + pp) * lds + q0 + qq] : mk<R>(0, 0);
+      }
+#pragma unroll
+      for (int k = 0; k < PT; ++k) {
+        const int e = threadIdx.x + kGemmThreads * k, pp = e / TQ, qq = e % TQ;
+        tile[pp * LDT + qq] = r[k];
+      }
+      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < PT; ++k) {
+        const int e = threadIdx.x + kGemmThreads * k, pp = e % TP, qq = e / TP;
+        if (p0 + pp < P && q0 + qq < Q) dst[(int64_t)(q0 + qq) * ldd + p0 + pp] = tile[pp * LDT + qq];
+      }
+      __syncthreads();
+    }
+}
+
 // Move the centre from site k to k+1 (dir = +1, QR of A_k as (2 dl) x dr) or
 // to k-1 (dir = -1, LQ of A_k as dl x (2 dr)).
 template <class R>
@@ -375,12 +406,14 @@ __global__ void __launch_bounds__(kGemmThreads, sizeof(R) == 4 ? 2 : 1) k_move_c
   cpx<R>* Tm = s.ws3 + t * s.ws_stride;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   // element copies run as (warp, lane) loops, lanes along the site tensor's
-  // contiguous index, with no per-element division
+  // contiguous index, with no per-element division; the transposing copies
+  // of the QR direction go through shared-memory tiles
+  cpx<R>* tile = reinterpret_cast<cpx<R>*>(move_smem);
+  static_assert(sizeof(QrSmem<R>) >= 32 * ((sizeof(R) == 4 ? 128 : 64) + 1) * sizeof(cpx<R>),
+                "the transpose tile fits in the QR shared memory");
   if (dir > 0) {
     const int m = 2 * dl, n = dr, r = min(m, n);
-    for (int i = warp; i < m; i += nwarp)
-      for (int c = lane; c < n; c += 32) X[(int64_t)c * m + i] = A[(int64_t)i * capr + c];
-    __syncthreads();
+    transpose_copy(X, m, A, capr, m, n, tile);
     householder_qr(X, V, Qm, m, n, r, qs);
     // A_{k+1} <- R A_{k+1}: A_{k+1} is dr x (2 d2), R is r x dr (upper part of X)
     const int d2 = bd[k + 2], cap2 = s.cap[k + 2];
@@ -399,8 +432,7 @@ __global__ void __launch_bounds__(kGemmThreads, sizeof(R) == 4 ? 2 : 1) k_move_c
         B[(int64_t)(i * 2 + ss) * cap2 + b] = Tm[(int64_t)i * 2 * d2 + cc];
       }
     // A_k <- Q (m x r) reshaped (dl, 2, r)
-    for (int i = warp; i < m; i += nwarp)
-      for (int c = lane; c < r; c += 32) A[(int64_t)i * capr + c] = Qm[(int64_t)c * m + i];
+    transpose_copy(A, capr, Qm, m, r, m, tile);
     if (threadIdx.x == 0) bd[k + 1] = r;
   } else {
     // X = A_k^dagger: (2 dr) x dl, column-major, X[c][i] = conj(A[i][c])
