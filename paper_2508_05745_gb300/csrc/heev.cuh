@@ -639,15 +639,20 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
       __syncthreads();
     }
   }
-  // ---- phase 4: Gram-Schmidt (twice) in descending eigenvalue order ----------
+  // ---- phase 4: Gram-Schmidt in descending eigenvalue order -----------------
   // When the vectors fit in shared memory (Z[k * ldz + i], rows padded so
   // that 16-byte loads of consecutive rows hit distinct banks) they are
-  // orthonormalized in blocks of 16 (block classical Gram-Schmidt, twice):
-  // project the block against all earlier vectors, then orthonormalize it
-  // by Cholesky QR of its 16 x 16 Gram matrix.  A block whose Cholesky
+  // orthonormalized in blocks of 16 (block classical Gram-Schmidt): project
+  // the block against all earlier vectors, then orthonormalize it by
+  // Cholesky QR of its 16 x 16 Gram matrix.  A second pass follows only when
+  // the first may have left an orthogonality error above a few ulps (the
+  // Daniel-Gragg-Kaufman-Stewart criterion): the projection removed more than
+  // half of some vector's squared norm, or a Cholesky pivot fell below half
+  // of its diagonal entry (an ill-conditioned block).  Inverse-iteration
+  // vectors of well-separated eigenvalues pass with one.  A block whose
   // pivots show near-dependence (pivot < tol * squared norm) is redone by
-  // per-vector classical Gram-Schmidt (twice).  Otherwise the vectors stay
-  // in the global scratch and the per-vector scheme runs for all of them.
+  // per-vector classical Gram-Schmidt (twice).  When the vectors do not fit,
+  // they stay in the global scratch and the per-vector scheme runs for all.
   constexpr int NB = 16;
   constexpr int E = 16 / (int)sizeof(R);             // elements per 16-byte load
   constexpr int ROWQ = 128 / (int)sizeof(R);         // elements per 128 bytes
@@ -698,12 +703,19 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
     R* cb = Zs + (size_t)keep * ldz;                   // [128][NB] projection coefficients
     R* gq = reinterpret_cast<R*>(sv);                  // [NB][NB] block Gram matrix
     R* lq = gq + NB * NB;                              // [NB][NB] its Cholesky factor
-    __shared__ int s_fail;
+    __shared__ int s_fail, s_redo;
+    __shared__ R s_n0[NB];   // squared norms of the block before its projection
     const int nvec = (n + E - 1) / E;
     const R tol = (sizeof(R) == 8) ? (R)1e-8 : (R)1e-3;
     for (int kb = 0; kb < keep; kb += NB) {
       const int nbk = min(NB, keep - kb);
       for (int rep = 0; rep < 2; ++rep) {
+        if (rep == 0 && kb > 0 && warp < nbk) {   // read after the Gram barrier below
+          R acc = 0;
+          for (int i = lane; i < n; i += 32) acc = fma(Zs[(size_t)(kb + warp) * ldz + i], Zs[(size_t)(kb + warp) * ldz + i], acc);
+          acc = warp_sum(acc);
+          if (lane == 0) s_n0[warp] = acc;
+        }
         if (kb > 0) {
           // cb[a][b] = <z_a, z_{kb+b}>, a < kb: thread (a, 4 consecutive b)
           {
@@ -783,7 +795,7 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
           R li[NB];
 #pragma unroll
           for (int c = 0; c < NB; ++c) li[c] = 0;
-          int fail = 0;
+          int fail = 0, redo = 0;
           const R gii = (lane < nbk) ? gq[lane * NB + lane] : (R)1;
 #pragma unroll
           for (int j = 0; j < NB; ++j) {
@@ -794,6 +806,7 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
               const R piv = __shfl_sync(0xffffffffu, sj, j);
               const R gjj = __shfl_sync(0xffffffffu, gii, j);
               if (!(piv > tol * gjj) || !(gjj > (R)0)) fail = 1;
+              if (!(piv >= (R)0.5 * gjj) || (kb > 0 && !(gjj >= (R)0.5 * s_n0[j]))) redo = 1;
               const R ljj = sqrt(fmax(piv, (R)0));
               if (lane == j) li[j] = ljj;
               else if (lane > j) li[j] = (ljj > 0) ? sj / ljj : (R)0;
@@ -802,7 +815,10 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
           if (lane < NB)
 #pragma unroll
             for (int c = 0; c < NB; ++c) lq[lane * NB + c] = li[c];
-          if (lane == 0) s_fail = fail;
+          if (lane == 0) {
+            s_fail = fail;
+            s_redo = redo;
+          }
         }
         __syncthreads();
         if (s_fail) {
@@ -828,6 +844,7 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
           }
           __syncthreads();
         }
+        if (rep == 0 && !s_fail && !s_redo) break;   // uniform: set before the barriers above
       }
     }
   }

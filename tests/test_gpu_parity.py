@@ -469,3 +469,29 @@ def test_lindblad_circuit_matches_oracle(L):
         assert list(br[t]) == ref.branch
         assert np.allclose(res["z"][t], ref.z, atol=1e-10)
         assert abs(res["s_half"][t] - ref.s_half) < 1e-10
+
+
+# --- canonical form after truncation -------------------------------------------------
+
+@pytest.mark.parametrize("precision,tol", [("mixed", 1e-5), ("fp64", 1e-13)])
+def test_canonical_form_after_truncation(L, precision, tol):
+    """After truncating layers at chi=128 (Gram matrices of size 256 through the
+    whole eigensolver, QR and LQ centre moves), every site left of the
+    orthogonality centre is a left isometry and every site right of it a right
+    isometry, to the precision's rounding level.  This checks the orthonormality
+    of the kept eigenvectors and of the Q factors directly, not through
+    observables."""
+    circ = I.random_brickwork(16, 16, I.depolarizing_kraus(1.0), 5, coin_p=0.005)
+    sim = L.Simulation(16, 128, 8, seed=5, precision=precision, cutoff=1e-12 if precision == "mixed" else 1e-20)
+    sim.run(circ)
+    assert sim.measure()["n_failed"] == 0
+    for t in (0, 3, 7):
+        tensors, bonds = sim.export_mps(t)
+        assert bonds.max() == 128
+        left = [np.abs(np.einsum('asb,asc->bc', a.conj(), a) - np.eye(a.shape[2])).max() for a in tensors]
+        right = [np.abs(np.einsum('asb,csb->ac', a, a.conj()) - np.eye(a.shape[0])).max() for a in tensors]
+        n = len(tensors)
+        centres = [c for c in range(n)
+                   if all(left[k] < tol for k in range(c)) and all(right[k] < tol for k in range(c + 1, n))]
+        assert centres, (precision, t, np.max(left), np.max(right))
+    sim.destroy()
