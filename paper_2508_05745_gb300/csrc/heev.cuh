@@ -425,9 +425,9 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
     const int ntb = ((M0 - 1) >> 5) - tb0 + 1;
     const int nun = ntb * (ntb + 1) / 2 * NQ;
     R ssp = 0;
+    int I = 0;   // tile row of tile tl; a warp's tl only grow, so I carries over
     for (int u = warp; u < nun; u += nwarp) {
       const int tl = u / NQ, hf = u % NQ;
-      int I = 0;
       while ((I + 1) * (I + 2) / 2 <= tl) ++I;
       const int J = tl - I * (I + 1) / 2;
       const int Rr = 32 * (tb0 + I) + lane;
