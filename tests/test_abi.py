@@ -53,3 +53,33 @@ def test_no_cpu_fallback_without_gpu():
         pytest.skip("GPU present")
     with pytest.raises(RuntimeError):
         lemps.Simulation(4, 4, 2)
+
+
+def test_misaligned_allocator_blocks_are_refused_and_freed(lib_path):
+    """sim_create checks that every block from a user allocator hook is 16-byte
+    aligned (the kernels stream workspaces with bulk copies) before anything
+    touches device memory: one misaligned block fails the call with
+    LEMPS_EINVAL, no handle is returned, and every block handed out goes back
+    through the free hook.  Host only: the fake blocks are never dereferenced."""
+    import ctypes
+    from paper_2508_05745_gb300 import lemps as L
+    lib = L.load()
+    handed, freed = [], []
+
+    def alloc(nbytes, stream, ctx):
+        p = 0x7F0000000000 + 0x1000000 * (len(handed) + 1) + (8 if len(handed) == 3 else 0)
+        handed.append(p)
+        return p
+
+    def free(ptr, nbytes, stream, ctx):
+        freed.append(ptr)
+
+    cb = (L.ALLOC_FN(alloc), L.FREE_FN(free))
+    cfg = L.Config(n_qubits=8, chi_max=16, trunc_cutoff=1e-12, n_traj=4, traj_offset=0, seed=1,
+                   precision=L.LEMPS_MIXED, unravel_mode=L.LEMPS_UNRAVEL_OPTIMAL, log_capacity=0, eps_max=2.0,
+                   cuda_stream=None, alloc=cb[0], free=cb[1], alloc_ctx=None, layering=L.LEMPS_LAYER_LOCAL)
+    h = ctypes.c_void_p()
+    assert lib.sim_create(ctypes.byref(cfg), ctypes.byref(h)) == L.LEMPS_EINVAL
+    assert b"16-byte aligned" in lib.lemps_last_error()
+    assert h.value is None
+    assert len(handed) > 3 and sorted(freed) == sorted(handed)
