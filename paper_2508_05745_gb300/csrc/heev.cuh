@@ -601,40 +601,102 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
         const int k = k0 + kk;
         R* w3 = wsp + koff + kk;
         const R lam = (R)ev[k];
-        // w3[i][0] holds 1 / d_i, so that the solves multiply
+        // w3[i][0] holds 1 / d_i (the solves multiply), w3[i][1] l_i, w3[i][2]
+        // the iterate.  Stores to w3 would keep the compiler from hoisting the
+        // next step's loads (the strides are runtime values), so the loops run
+        // in blocks of four steps whose loads all precede their stores; the
+        // chains then wait on arithmetic only.  The start vector enters the
+        // first forward solve directly, the rescaling of the first iterate the
+        // second one, and that of the second the copy-out.
         auto recip = [](R x) { return sizeof(R) == 4 ? (R)__fdividef(1.0f, (float)x) : (R)1 / x; };
+        auto Dr = [&](int i) -> R& { return w3[(i * 3 + 0) * ld]; };
+        auto Lw = [&](int i) -> R& { return w3[(i * 3 + 1) * ld]; };
+        auto Zw = [&](int i) -> R& { return w3[(i * 3 + 2) * ld]; };
         R dprev = sd[0] - lam;
         if (fabs(dprev) < pivmin) dprev = pivmin;
         R rprev = recip(dprev);
-        w3[(0 * 3 + 0) * ld] = rprev;
-        for (int i = 0; i + 1 < n; ++i) {
-          R li = se[i] * rprev;
-          w3[(i * 3 + 1) * ld] = li;
-          R dn = (sd[i + 1] - lam) - li * se[i];
-          if (fabs(dn) < pivmin) dn = pivmin;
-          rprev = recip(dn);
-          w3[((i + 1) * 3 + 0) * ld] = rprev;
-        }
-        for (int i = 0; i < n; ++i) w3[(i * 3 + 2) * ld] = (R)start_entry(k, i);
-        for (int iter = 0; iter < 2; ++iter) {
-          R y = w3[(0 * 3 + 2) * ld];
-          for (int i = 1; i < n; ++i) {
-            y = w3[(i * 3 + 2) * ld] - w3[((i - 1) * 3 + 1) * ld] * y;
-            w3[(i * 3 + 2) * ld] = y;
+        Dr(0) = rprev;
+        {
+          auto step = [&](R si, R di) {   // returns l_i, advances rprev to 1 / d_{i+1}
+            const R li = si * rprev;
+            R dn = di - li * si;
+            if (fabs(dn) < pivmin) dn = pivmin;
+            rprev = recip(dn);
+            return li;
+          };
+          int i = 0;
+          for (; i + 4 < n; i += 4) {
+            R s4[4], d4[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              s4[q] = se[i + q];
+              d4[q] = sd[i + q + 1] - lam;
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              Lw(i + q) = step(s4[q], d4[q]);
+              Dr(i + q + 1) = rprev;
+            }
           }
-          R zn = w3[((n - 1) * 3 + 2) * ld] * w3[((n - 1) * 3 + 0) * ld];
-          w3[((n - 1) * 3 + 2) * ld] = zn;
+          for (; i + 1 < n; ++i) {
+            Lw(i) = step(se[i], sd[i + 1] - lam);
+            Dr(i + 1) = rprev;
+          }
+        }
+        R sc = 1;
+        for (int iter = 0; iter < 2; ++iter) {
+          auto zin = [&](int i) { return iter == 0 ? (R)start_entry(k, i) : sc * Zw(i); };
+          R y = zin(0);
+          Zw(0) = y;
+          int i = 1;
+          for (; i + 3 < n; i += 4) {
+            R z4[4], l4[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              z4[q] = zin(i + q);
+              l4[q] = Lw(i + q - 1);
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              y = z4[q] - l4[q] * y;
+              Zw(i + q) = y;
+            }
+          }
+          for (; i < n; ++i) {
+            y = zin(i) - Lw(i - 1) * y;
+            Zw(i) = y;
+          }
+          R zn = Zw(n - 1) * Dr(n - 1);
+          Zw(n - 1) = zn;
           R amax = fabs(zn);
-          for (int i = n - 2; i >= 0; --i) {
-            zn = w3[(i * 3 + 2) * ld] * w3[(i * 3 + 0) * ld] - w3[(i * 3 + 1) * ld] * zn;
-            w3[(i * 3 + 2) * ld] = zn;
+          i = n - 2;
+          for (; i >= 3; i -= 4) {
+            R z4[4], d4[4], l4[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              z4[q] = Zw(i - q);
+              d4[q] = Dr(i - q);
+              l4[q] = Lw(i - q);
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              zn = z4[q] * d4[q] - l4[q] * zn;
+              Zw(i - q) = zn;
+              amax = fmax(amax, fabs(zn));
+            }
+          }
+          for (; i >= 0; --i) {
+            zn = Zw(i) * Dr(i) - Lw(i) * zn;
+            Zw(i) = zn;
             amax = fmax(amax, fabs(zn));
           }
-          R sc = (amax > 0) ? (R)1 / amax : (R)1;
-          for (int i = 0; i < n; ++i) w3[(i * 3 + 2) * ld] *= sc;
+          sc = (amax > 0) ? (R)1 / amax : (R)1;
         }
-        if (in_smem)
-          for (int i = 0; i < n; ++i) scr[(i * 3 + 2) * keep + k] = w3[(i * 3 + 2) * ld];
+        if (in_smem) {
+          for (int i = 0; i < n; ++i) scr[(i * 3 + 2) * keep + k] = sc * Zw(i);
+        } else {
+          for (int i = 0; i < n; ++i) Zw(i) *= sc;
+        }
       }
       __syncthreads();
     }
