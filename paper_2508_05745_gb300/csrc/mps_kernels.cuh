@@ -311,11 +311,14 @@ __device__ void householder_qr(cpx<R>* X, cpx<R>* V, cpx<R>* Qm, int m, int n, i
       __syncthreads();
       for (int c = jj + warp; c < pb; c += nwarp) {
         cpx<R> d = mk<R>(0, 0);
+#pragma unroll 4
         for (int i = jj + lane; i < pm; i += 32) cfmac(d, sm.vs[jj * pm + i], sm.p[c * pm + i]);
         d.re = warp_sum(d.re);
         d.im = warp_sum(d.im);
         d = (R)2 * d;
         R nn = 0;
+        // unrolled so that the loads of several rows precede their stores
+#pragma unroll 4
         for (int i = jj + lane; i < pm; i += 32) {
           const cpx<R> y = sm.p[c * pm + i] - sm.vs[jj * pm + i] * d;
           sm.p[c * pm + i] = y;
