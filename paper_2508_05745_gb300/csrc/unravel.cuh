@@ -84,18 +84,26 @@ __device__ inline void jacobi_sym_n(double* a, double* v, double* w) {
         double zeta = (a[q * N + q] - a[p * N + p]) / (2.0 * apq);
         double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
         double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
+        // A <- J^T A J, J = [[c, s], [-s, c]] on (p, q).  A stays symmetric, so
+        // rows p, q are rotated once and mirrored into the columns, and the
+        // pivot block takes its closed form (a_pq -> 0, a_pp -= t a_pq, a_qq
+        // += t a_pq): about 0.6 of the FP64 operations of two full passes,
+        // which is what a rotation costs at the FP64 rate.
+        const double app = a[p * N + p], aqq = a[q * N + q];
 #pragma unroll
-        for (int k = 0; k < N; ++k) {  // columns p, q
-          double akp = a[k * N + p], akq = a[k * N + q];
-          a[k * N + p] = c * akp - s * akq;
-          a[k * N + q] = s * akp + c * akq;
+        for (int k = 0; k < N; ++k) {
+          if (k == p || k == q) continue;
+          const double akp = a[k * N + p], akq = a[k * N + q];
+          const double nkp = c * akp - s * akq, nkq = s * akp + c * akq;
+          a[k * N + p] = nkp;
+          a[p * N + k] = nkp;
+          a[k * N + q] = nkq;
+          a[q * N + k] = nkq;
         }
-#pragma unroll
-        for (int k = 0; k < N; ++k) {  // rows p, q
-          double apk = a[p * N + k], aqk = a[q * N + k];
-          a[p * N + k] = c * apk - s * aqk;
-          a[q * N + k] = s * apk + c * aqk;
-        }
+        a[p * N + p] = app - t * apq;
+        a[q * N + q] = aqq + t * apq;
+        a[p * N + q] = 0.0;
+        a[q * N + p] = 0.0;
 #pragma unroll
         for (int k = 0; k < N; ++k) {
           double vkp = v[k * N + p], vkq = v[k * N + q];
