@@ -81,9 +81,13 @@ __device__ inline void jacobi_sym_n(double* a, double* v, double* w) {
         double apq = a[p * N + q];
         if (fabs(apq) <= thresh) continue;
         rotated = true;
-        double zeta = (a[q * N + q] - a[p * N + p]) / (2.0 * apq);
-        double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-        double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
+        // t = sgn(zeta) / (|zeta| + sqrt(1 + zeta^2)), zeta = (a_qq - a_pp) / (2 a_pq),
+        // written with one square root and one divide (each a sequence of FP64
+        // operations), and c = 1 / sqrt(1 + t^2) by the reciprocal square root
+        const double diff = a[q * N + q] - a[p * N + p], ta = 2.0 * apq;
+        const double sz = (diff == 0.0 || ((diff > 0.0) == (apq > 0.0))) ? 1.0 : -1.0;
+        const double t = sz * fabs(ta) / (fabs(diff) + sqrt(diff * diff + ta * ta));
+        const double c = rsqrt(1.0 + t * t), s = c * t;
         // A <- J^T A J, J = [[c, s], [-s, c]] on (p, q).  A stays symmetric, so
         // rows p, q are rotated once and mirrored into the columns, and the
         // pivot block takes its closed form (a_pq -> 0, a_pp -= t a_pq, a_qq
@@ -353,13 +357,14 @@ __device__ __noinline__ bool optimal_unraveling(const zd* rho, const zd* kin, in
           be += norm2(f[q * 4 + i]);
           cfmac(g, f[p * 4 + i], f[q * 4 + i]);
         }
-        double gn = sqrt(norm2(g));
-        if (gn <= 1e-16 * sqrt(al * be) || gn <= 1e-30 * fnorm2) continue;
+        const double gn2 = norm2(g);
+        if (gn2 <= 1e-32 * (al * be) || gn2 <= 1e-60 * (fnorm2 * fnorm2)) continue;
         rotated = true;
-        double zeta = (be - al) / (2.0 * gn);
-        double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-        double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
-        zd eph = mk(g.re / gn, -g.im / gn);  // e^{-i phi}
+        // as in the symmetric case: zeta = (be - al) / (2 |g|) > -0 picks the sign
+        const double ign = rsqrt(gn2), gn = gn2 * ign, diff = be - al;
+        const double t = (diff >= 0.0 ? 1.0 : -1.0) * (2.0 * gn) / (fabs(diff) + sqrt(diff * diff + 4.0 * gn2));
+        const double c = rsqrt(1.0 + t * t), s = c * t;
+        const zd eph = mk(g.re * ign, -g.im * ign);  // e^{-i phi}
         for (int i = 0; i < 4; ++i) {
           zd fp = f[p * 4 + i], fq = f[q * 4 + i] * eph;
           f[p * 4 + i] = c * fp - s * fq;
