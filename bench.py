@@ -182,8 +182,10 @@ def run_arm(L, torch, w, sizes, precision, args, pre, warm, steps, profile_step=
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     fork(ev0)
+    torch.cuda.nvtx.range_push("timed_steps")   # lets a profiler select these launches
     for l in range(t0, t0 + steps):
         step(l)
+    torch.cuda.nvtx.range_pop()
     join()
     ev1.record(stream)
     torch.cuda.synchronize()
@@ -226,9 +228,11 @@ def run_arm(L, torch, w, sizes, precision, args, pre, warm, steps, profile_step=
         out["profile_work"] = work
         for s in sims.values():
             s.profile(True)
+        torch.cuda.nvtx.range_push("profiled_layer")
         for n, s in sims.items():
             s.apply_layer(w["circuits"][n].layers[l2])
             torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
         prof = {}
         for s in sims.values():
             for k, (kms, cnt) in s.profile(False, collect=True).items():
