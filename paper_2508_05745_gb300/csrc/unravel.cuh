@@ -73,7 +73,9 @@ __device__ inline void jacobi_sym_n(double* a, double* v, double* w) {
   double tot = 0.0;
 #pragma unroll
   for (int i = 0; i < N * N; ++i) tot += a[i] * a[i];
-  const double thresh = 1e-17 * sqrt(tot);  // rotate only |a_pq| above this
+  // rotate only |a_pq| above eps_64 ||A||_F, the accuracy of a backward-stable
+  // eigensolver; smaller entries are rounding noise of the earlier rotations
+  const double thresh = 2.2e-16 * sqrt(tot);
   for (int sweep = 0; sweep < 60; ++sweep) {
     bool rotated = false;
     for (int p = 0; p < N - 1; ++p)
