@@ -90,6 +90,7 @@ __device__ void qr_build_t(QrSmem<R>& sm, int pm, int pb) {
       R d[16];
 #pragma unroll
       for (int e = 0; e < 16; ++e) d[e] = 0;
+#pragma unroll 2
       for (int i = lane; i < pm; i += 32) {
         const cpx<R> vb = sm.vs[bcol * pm + i];
 #pragma unroll
@@ -123,11 +124,13 @@ __device__ void qr_build_t(QrSmem<R>& sm, int pm, int pb) {
 #pragma unroll
     for (int i = 0; i < NB; ++i) {
       if (i < pb) {
-        cpx<R> acc = mk<R>(0, 0);
+        // four partial sums: the chain over c is a quarter as deep
+        cpx<R> acc[4] = {mk<R>(0, 0), mk<R>(0, 0), mk<R>(0, 0), mk<R>(0, 0)};
 #pragma unroll
         for (int c = 0; c < i; ++c)
-          if (c >= lane) cfma(acc, trow[c], sm.w[c * NB + i]);
-        trow[i] = (lane < i) ? (R)-2 * acc : mk<R>(lane == i ? 2 : 0, 0);
+          if (c >= lane) cfma(acc[c & 3], trow[c], sm.w[c * NB + i]);
+        const cpx<R> sum = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+        trow[i] = (lane < i) ? (R)-2 * sum : mk<R>(lane == i ? 2 : 0, 0);
       }
     }
     if (lane < NB)
