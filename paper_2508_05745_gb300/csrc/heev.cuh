@@ -7,10 +7,11 @@
 // cutoff * trace}, n); the count comes from one Sturm sequence at
 // cutoff * trace, so eigenvalues that will be discarded are never computed.
 //
-// Layout (16-byte aligned, n even): G (n x n row-major, Hermitian) in ws1, overwritten.  Householder
-// vectors in ws3 (row j holds v_j, unit norm, entries > j).  Eigenvectors are
-// written column-major to ws2: U[k * n + i], k < keep.  Eigenvalues (double,
-// descending) to evals[0..keep), keep and the trace to kept[] / trace[].
+// Layout (buffers 16-byte aligned, n even): G (n x n row-major, Hermitian)
+// in ws1, overwritten.  Householder vectors in ws3 (row j holds v_j, unit
+// norm, entries > j).  Eigenvectors are written column-major to ws2:
+// U[k * n + i], k < keep.  Eigenvalues (double, descending) to
+// evals[0..keep), keep and the trace to kept[] / trace[].
 #pragma once
 
 #include <type_traits>
