@@ -542,6 +542,25 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
   __syncthreads();
   const int keep = s_keep;
   double* ev = s.evals + t * (2 * s.chi);
+  // Brackets: one Sturm count per thread on an increasing grid of blockDim.x
+  // points (the packed triangle's shared memory is free by now).  When a
+  // cutoff is set, every kept eigenvalue lies above x_lo = cutoff * trace and
+  // the grid is geometric from x_lo to gu (neighbouring points about 5 %
+  // apart), so each eigenvalue starts from a narrow relative interval instead
+  // of [gl, gu]; else it is uniform on [gl, gu].  Any increasing grid is
+  // valid, so it is formed in single precision.
+  R* gx = reinterpret_cast<R*>(heev_smem);
+  int* gcnt = reinterpret_cast<int*>(gx + blockDim.x);
+  {
+    const int ng = blockDim.x;
+    const float xlo = (float)(cutoff * s_tr), xhi = (float)gu;
+    const bool geo = cutoff > 0.0 && xlo > 0.0f && xlo < xhi;
+    const float f = (float)threadIdx.x / (float)(ng - 1);
+    const R x = geo ? (R)(xlo * exp2f(log2f(xhi / xlo) * f)) : gl + (gu - gl) * (R)(threadIdx.x + 1) / (R)(ng + 1);
+    gx[threadIdx.x] = x;
+    gcnt[threadIdx.x] = sturm_greater<R>(sd, se2, n, x, pivmin);
+  }
+  __syncthreads();
   {
     // Multisection: G lanes of a warp share eigenvalue k and evaluate the
     // Sturm count at G interior points of its interval, which shrinks by
@@ -554,6 +573,18 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
     for (int kb = 0; kb < keep; kb += nwarp * per_warp) {
       const int k = kb + warp * per_warp + lane / G;
       R lo = gl, hi = gu;
+      if (k < keep) {
+        // grid counts do not increase along the grid: a = last point below
+        // eigenvalue k (count > k), b = a + 1 the first at or above it
+        int a = -1, b = (int)blockDim.x;
+        while (b - a > 1) {
+          const int mid = (a + b) >> 1;
+          if (gcnt[mid] > k) a = mid;
+          else b = mid;
+        }
+        if (a >= 0) lo = gx[a];
+        if (b < (int)blockDim.x) hi = gx[b];
+      }
       bool done = k >= keep;
       for (int it = 0; it < 200; ++it) {
         const R h = (hi - lo) / (R)(G + 1);
