@@ -464,9 +464,9 @@ def layer_work(left_qubits, bonds, chi):
 # DRAM bytes (read + write) of one ncu capture of the kernel as it is now
 # (profiles/<kernel>_chi128_n48_b152.md); remove an entry when its kernel changes.
 NCU_TRAFFIC = {
-    "eig": {"bytes": 237.9e6,
+    "eig": {"bytes": 243.2e6,
             "note": "one k_heev launch at the n_Gram=256 gate (gate 12 of layer 8), 152 trajectories, dram read "
-                    "113.3 MB + write 124.6 MB: 1.57 MB per trajectory against ~1.5 MB of algorithmic bytes (G read, "
+                    "115.7 MB + write 127.5 MB: 1.60 MB per trajectory against ~1.5 MB of algorithmic bytes (G read, "
                     "reflectors written and read back, U written); bench launches mix gate sizes, so this is the "
                     "full-size launch, not the average"},
 }
