@@ -495,3 +495,48 @@ def test_canonical_form_after_truncation(L, precision, tol):
                    if all(left[k] < tol for k in range(c)) and all(right[k] < tol for k in range(c + 1, n))]
         assert centres, (precision, t, np.max(left), np.max(right))
     sim.destroy()
+
+
+# --- the chi=128 benchmark configuration, sampled -------------------------------------
+
+@pytest.mark.slow
+def test_chi128_workload_sampled_against_oracle(L):
+    """The chi=128 benchmark configuration, checked on sampled trajectories.
+
+    The circuit is the n=48 one of the uneven workload (depth-32 Haar brickwork,
+    two-qubit depolarizing p=0.005), cut to 14 layers so that the middle bonds
+    sit at chi=128 in the later layers.  Mixed precision runs in one handle of
+    608 trajectories, the bench's per-size scale of one CTA per trajectory and
+    kernel; FP64 runs in a handle of 2.  Two trajectories of each are recomputed
+    by the oracle's FP64 MPS trajectory:
+    - FP64: equal branch sequences, observables to 1e-8, error bound to 1e-6.
+    - Mixed: observables within 1e-4 wherever the branch sequence matches
+      (complex64 rounding can flip a branch whose uniform falls within ~1e-7
+      of a threshold)."""
+    w = I.workload_uneven(seed=0, n_traj=8, depth=32)
+    full = w["circuits"][48]
+    circ = I.Circuit(full.n_qubits, full.layers[:14])
+    seed = 11
+    sim, res, br = run_gpu(L, circ, 128, 608, seed=seed, precision="mixed", cutoff=1e-12)
+    _, bonds = sim.export_mps(0)
+    sim.destroy()
+    assert bonds.max() == 128 and res["n_failed"] == 0
+    checked = 0
+    for t in (0, 1):
+        ref = T.mps_trajectory(circ, t, seed, chi_max=128, cutoff=1e-12)
+        if list(br[t]) != ref.branch:
+            continue
+        checked += 1
+        assert np.allclose(res["z"][t], ref.z, atol=1e-4)
+        assert np.allclose(res["zz"][t], ref.zz, atol=1e-4)
+        assert abs(res["s_half"][t] - ref.s_half) < 1e-4
+    assert checked >= 1
+    sim, res, br = run_gpu(L, circ, 128, 2, seed=seed, precision="fp64", cutoff=1e-20)
+    sim.destroy()
+    for t in (0, 1):
+        ref = T.mps_trajectory(circ, t, seed, chi_max=128, cutoff=1e-20)
+        assert list(br[t]) == ref.branch
+        assert np.allclose(res["z"][t], ref.z, atol=1e-8)
+        assert np.allclose(res["zz"][t], ref.zz, atol=1e-8)
+        assert abs(res["s_half"][t] - ref.s_half) < 1e-8
+        assert abs(res["eps_bound"][t] - ref.eps_bound) < 1e-6
