@@ -97,7 +97,7 @@ def dense_observables(psi, n):
         m = np.moveaxis(prob, (i, i + 1), (0, 1)).reshape(2, 2, -1).sum(axis=2)
         zz[i] = m[0, 0] - m[0, 1] - m[1, 0] + m[1, 1]
     h = n // 2
-    s = np.linalg.svd(psi.reshape(2 ** h, -1), compute_uv=False)
+    s = _svd(psi.reshape(2 ** h, -1), compute_uv=False)
     lam = s ** 2 / np.sum(s ** 2)
     lam = lam[lam > 0]
     return z, zz, float(-np.sum(lam * np.log(lam)))
@@ -236,7 +236,7 @@ class MPS:
                 zz[k] = w[0, 0] - w[0, 1] - w[1, 0] + w[1, 1]
             if k == n // 2 - 1:
                 dl, _, dr = a.shape
-                s = np.linalg.svd(a.reshape(dl * 2, dr), compute_uv=False)
+                s = _svd(a.reshape(dl * 2, dr), compute_uv=False)
                 lam = s ** 2 / np.sum(s ** 2)
                 lam = lam[lam > 0]
                 s_half = float(-np.sum(lam * np.log(lam)))
@@ -257,12 +257,23 @@ def _pair_tensor(m, q, gate=None):
     return th.reshape(a.shape[0], 2, 2, b.shape[2])
 
 
+def _svd(a, **kw):
+    """numpy's SVD (LAPACK gesdd, divide and conquer).  On gesdd's rare
+    non-convergence, the same decomposition by LAPACK gesvd (QR iteration)
+    through scipy."""
+    try:
+        return np.linalg.svd(a, **kw)
+    except np.linalg.LinAlgError:
+        import scipy.linalg as sla
+        return sla.svd(a, lapack_driver="gesvd", **kw)
+
+
 def _split(m, q, th, cap, cutoff, rec):
     """SVD split of the pair (Eq. MPS_truncation_error): keep
     chi' = min(cap, #{s_k^2 > cutoff * sum s^2}) values, renormalize, centre on
     q+1; returns the discarded weight."""
     dl, dr = th.shape[0], th.shape[3]
-    u, s, vh = np.linalg.svd(th.reshape(dl * 2, 2 * dr), full_matrices=False)
+    u, s, vh = _svd(th.reshape(dl * 2, 2 * dr), full_matrices=False)
     w = s ** 2
     tot = np.sum(w)
     keep = int(min(cap, np.sum(w > cutoff * tot)))

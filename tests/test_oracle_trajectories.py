@@ -299,3 +299,23 @@ def test_concentration_bound_definitions():
     assert T.concentration_weight("depolarizing", 0.3, 0, 10) == 1.0
     k = 40
     assert abs(T.concentration_weight("depolarizing", 0.3, k, 10) - math.sqrt(80.0) * 0.7 ** k) < 1e-18
+
+
+def test_svd_fallback_gives_the_same_decomposition(monkeypatch):
+    """The oracle's split SVD falls back to LAPACK gesvd when gesdd reports
+    non-convergence (seen on one x86 LAPACK at chi=128).  The fallback must give
+    the same singular values and a valid factorization: u s vh = a, orthonormal
+    columns of u."""
+    rng = np.random.default_rng(5)
+    a = rng.standard_normal((40, 24)) + 1j * rng.standard_normal((40, 24))
+    ref = np.linalg.svd(a, compute_uv=False)
+
+    def fail(*args, **kw):
+        raise np.linalg.LinAlgError("SVD did not converge")
+
+    monkeypatch.setattr(np.linalg, "svd", fail)
+    u, s, vh = T._svd(a, full_matrices=False)
+    assert np.allclose(s, ref, atol=1e-12)
+    assert np.allclose((u * s) @ vh, a, atol=1e-12)
+    assert np.allclose(u.conj().T @ u, np.eye(24), atol=1e-12)
+    assert np.allclose(T._svd(a, compute_uv=False), ref, atol=1e-12)
