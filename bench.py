@@ -10,19 +10,23 @@ optimal unraveling), chi_max = 128, truncation cutoff 1e-12 (mixed) / 1e-20
 
 A step is one circuit layer applied to every trajectory of the batch (one pass
 of the whole hot path: centre moves, contraction, unraveling and sampling on
-both qubits, Gram + eigensolve, truncation, error bookkeeping).  Before the
-timed steps the states are pre-evolved (untimed) so that the middle bonds sit
-at chi_max.  One bond update = one gate on one trajectory.  The MPS state of
-the batch is far larger than the 129 MB L2, so every step streams it from HBM.
+both qubits, Gram + eigensolve, truncation, error bookkeeping).  Before any
+warm-up or timed step the states are pre-evolved (untimed) so that the middle
+bonds sit at chi_max.  Every warm-up and timed step is a layer of the depth-32
+circuit: when the layers after the pre-evolution run out, the handles are
+created afresh and pre-evolved again, untimed (`layer_plan`).  One bond update
+= one gate on one trajectory.  The MPS state of the batch is far larger than
+the 129 MB L2, so every step streams it from HBM.
 
---impl reference runs the CPU oracle (oracle/, numpy FP64) on the host cores
-for a bounded sample of the same workload and prints its own line.
+--impl reference runs the CPU oracle (oracle/, FP64) on the host cores for a
+bounded sample of the same workload and prints its own line.
+--gpus N without a launcher-provided WORLD_SIZE starts N ranks itself through
+torch.distributed.run (replicas, one GPU each).
 """
 from __future__ import annotations
 
 import argparse
 import json
-import math
 import os
 import subprocess
 import sys
@@ -35,16 +39,20 @@ import numpy as np  # noqa: E402
 
 METRIC = "trajectory bond-updates/s at chi=128, mixed vs plain FP64; observable error"
 UNIT = "bond-updates/s"
+WORKLOAD = "uneven: n~U{24,48,64}, depth 32 Haar brickwork, 2q depolarizing p=0.005, chi_max=128"
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="lemps", choices=["lemps", "reference"])
-    ap.add_argument("--traj", type=int, default=4096, help="mixed-precision trajectories in the batch (one wave)")
-    ap.add_argument("--fp64-traj", type=int, default=128, help="FP64 comparator trajectories")
+    ap.add_argument("--traj", type=int, default=2048, help="mixed-precision trajectories in the batch per GPU")
+    ap.add_argument("--fp64-traj", type=int, default=1216,
+                    help="FP64 comparator trajectories (8 per SM: fills the GPU)")
+    ap.add_argument("--fp64-steps", type=int, default=3, help="timed FP64 steps (at most --steps)")
+    ap.add_argument("--e2e-steps", type=int, default=5, help="steps of the end-to-end measurement (at most --steps)")
     ap.add_argument("--pre-layers", type=int, default=10, help="untimed layers before warm-up")
     ap.add_argument("--depth", type=int, default=32)
     ap.add_argument("--chi", type=int, default=128)
@@ -54,7 +62,7 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--sizes", default="24,48,64", help="system sizes to include (profiling cases use one)")
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 T_START = time.time()
@@ -107,21 +115,61 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-# --- workload -----------------------------------------------------------------------
+# --- workload and layer plan ------------------------------------------------------
 
 def workload(args):
     from paper_2508_05745_gb300 import inputs as I
-    w = I.workload_uneven(seed=args.seed, n_traj=16384, depth=args.depth)
-    return w
-
-
-def batch_sizes(n_of_traj, total):
-    labels = n_of_traj[:total]
-    return {int(n): int(np.sum(labels == n)) for n in (24, 48, 64)}
+    return I.workload_uneven(seed=args.seed, n_traj=16384, depth=args.depth)
 
 
 def gates_in(circ, layers):
     return [len(circ.layers[l].left_qubits) for l in layers]
+
+
+class LayerPlan:
+    """Hands out the layers of a depth-`depth` circuit for warm-up, timed,
+    end-to-end and profiled steps so that every such step is a layer of the
+    circuit at index >= `pre` (the pre-evolution puts the middle bonds at
+    chi_max first).  When the layers run out, the next request starts with a
+    reset: fresh handles, pre-evolved untimed through layers 0..pre-1.
+
+    take(kind, count) returns a list of events ("reset", None), ("pre", l),
+    (kind, l); the caller applies them in order."""
+
+    def __init__(self, depth, pre):
+        if not 0 <= pre < depth:
+            raise ValueError(f"pre-evolution layers ({pre}) must leave at least one layer of the depth-{depth} circuit")
+        self.depth, self.pre = depth, pre
+        self.pos = depth    # no handles yet: the first request resets
+
+    def take(self, kind, count):
+        ev = []
+        for _ in range(count):
+            if self.pos >= self.depth:
+                ev.append(("reset", None))
+                ev.extend(("pre", l) for l in range(self.pre))
+                self.pos = self.pre
+            ev.append((kind, self.pos))
+            self.pos += 1
+        return ev
+
+
+def timed_segments(events):
+    """Split a list of plan events at the resets: [(untimed events, timed
+    layers)], where the untimed events (reset / pre) precede the segment's
+    timed layers."""
+    segs, pending, run = [], [], []
+    for e in events:
+        if e[0] in ("reset", "pre"):
+            if run:
+                segs.append((pending, run))
+                pending, run = [], []
+            pending.append(e)
+        else:
+            run.append(e[1])
+    if run or pending:
+        segs.append((pending, run))
+    return segs
 
 
 # --- the GPU arm ------------------------------------------------------------------------
@@ -142,121 +190,172 @@ def combine_over_ranks(torch, dist, ms, updates, device):
     return float(t.item()), float(u.item())
 
 
-def run_arm(L, torch, w, sizes, precision, args, pre, warm, steps, profile_step=False, e2e=False, offsets=None,
-            barrier=None):
-    """Create one Simulation per system size, pre-evolve, warm up, time `steps`
-    layers.  Returns dict with timing, per-kernel profile and the sims."""
-    cutoff = 1e-12 if precision == "mixed" else 1e-20
-    # One CUDA stream per system size: the handles are independent, so their
-    # kernels may overlap on the GPU.  The timed region is bracketed on the
-    # launching stream, which every handle's stream joins before the stop event.
-    sims = {}
-    for n, b in sizes.items():
-        if b == 0:
-            continue
-        sims[n] = L.Simulation(n, args.chi, b, seed=args.seed, precision=precision, cutoff=cutoff,
-                               traj_offset=(offsets or {}).get(n, 0),
-                               log_capacity=w["circuits"][n].n_gates, stream=torch.cuda.Stream())
-    stream = torch.cuda.current_stream()
+class Arm:
+    """One handle per system size, each on its own CUDA stream (the handles are
+    independent, so their kernels may overlap); layers are applied through the
+    public API (Simulation.apply_layer -> apply_layer of the C ABI)."""
 
-    def step(l):
-        for n, s in sims.items():
-            s.apply_layer(w["circuits"][n].layers[l])
+    def __init__(self, L, torch, w, sizes, precision, args, offsets=None, barrier=None):
+        self.L, self.torch, self.w, self.args = L, torch, w, args
+        self.sizes = {n: b for n, b in sizes.items() if b > 0}
+        self.precision = precision
+        self.cutoff = 1e-12 if precision == "mixed" else 1e-20
+        self.offsets = offsets or {}
+        self.barrier = barrier
+        self.sims = {}
+        self.plan = LayerPlan(args.depth, args.pre_layers)
+        self.resets = 0
 
-    def fork(ev):
-        for s in sims.values():
-            s.stream.wait_event(ev)
+    def reset(self):
+        torch = self.torch
+        for s in self.sims.values():
+            s.destroy()
+        self.sims = {}
+        for n, b in self.sizes.items():
+            self.sims[n] = self.L.Simulation(n, self.args.chi, b, seed=self.args.seed, precision=self.precision,
+                                             cutoff=self.cutoff, traj_offset=self.offsets.get(n, 0),
+                                             log_capacity=self.w["circuits"][n].n_gates, stream=torch.cuda.Stream())
+        self.resets += 1
 
-    def join():
-        for s in sims.values():
-            e = torch.cuda.Event()
-            e.record(s.stream)
-            stream.wait_event(e)
+    def apply(self, l):
+        for n, s in self.sims.items():
+            s.apply_layer(self.w["circuits"][n].layers[l])
 
-    for l in range(pre + warm):
-        step(l)
-    torch.cuda.synchronize()
-    if barrier:
-        barrier()
-    t0 = l0 = pre + warm
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    fork(ev0)
-    torch.cuda.nvtx.range_push("timed_steps")   # lets a profiler select these launches
-    for l in range(t0, t0 + steps):
-        step(l)
-    torch.cuda.nvtx.range_pop()
-    join()
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    if barrier:
-        barrier()
-    ms = ev0.elapsed_time(ev1)
-    updates = sum(sum(gates_in(w["circuits"][n], range(t0, t0 + steps))) * s.B for n, s in sims.items())
-    out = dict(ms=ms, updates=updates, sims=sims, next_layer=t0 + steps, steps=steps)
-    if e2e:
-        # end to end through the public API: host gate arrays copied in every
-        # apply_layer call, branch indices of the layer read back to the host.
-        l1 = out["next_layer"]
-        torch.cuda.synchronize()
-        t_start = time.perf_counter()
-        h2d = d2h = 0
-        for l in range(l1, l1 + steps):
-            for n, s in sims.items():
-                layer = w["circuits"][n].layers[l]
-                s.apply_layer(layer)
-                h2d += layer.gates.nbytes + layer.kraus.nbytes + layer.left_qubits.nbytes
-            for s in sims.values():
-                g_last = s.gates_applied - 1
-                s.sample_branch(g_last, 1)
-                d2h += 4 * s.B
-        torch.cuda.synchronize()
-        el = time.perf_counter() - t_start
-        upd = sum(sum(gates_in(w["circuits"][n], range(l1, l1 + steps))) * s.B for n, s in sims.items())
-        out.update(e2e_value=upd / el, h2d=h2d // steps, d2h=d2h // steps)
-        out["next_layer"] = l1 + steps
-    if profile_step:
-        # per-kernel CUDA events; the handles run one after another here so
-        # that no kernel's duration includes another handle's work
-        l2 = out["next_layer"]
+    def untimed(self, events):
+        for kind, l in events:
+            if kind == "reset":
+                self.reset()
+            else:
+                self.apply(l)
+
+    def updates(self, layers):
+        return sum(sum(gates_in(self.w["circuits"][n], layers)) * s.B for n, s in self.sims.items())
+
+    def warmup(self, count):
+        self.untimed(self.plan.take("warm", count))
+        self.torch.cuda.synchronize()
+
+    def timed(self, count):
+        """Time `count` steps with CUDA events on the launching stream, one
+        bracket per segment between resets (barrier + synchronize on both
+        sides of each); returns (ms, updates, layers)."""
+        torch = self.torch
+        stream = torch.cuda.current_stream()
+        ms, upd, layers = 0.0, 0, []
+        for pending, run in timed_segments(self.plan.take("timed", count)):
+            self.untimed(pending)
+            if not run:
+                continue
+            torch.cuda.synchronize()
+            if self.barrier:
+                self.barrier()
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            for s in self.sims.values():
+                s.stream.wait_event(ev0)
+            torch.cuda.nvtx.range_push("timed_steps")   # lets a profiler select these launches
+            for l in run:
+                self.apply(l)
+            torch.cuda.nvtx.range_pop()
+            for s in self.sims.values():
+                e = torch.cuda.Event()
+                e.record(s.stream)
+                stream.wait_event(e)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            if self.barrier:
+                self.barrier()
+            ms += ev0.elapsed_time(ev1)
+            upd += self.updates(run)
+            layers += run
+        return ms, upd, layers
+
+    def e2e(self, count):
+        """End to end through the public API: the layer's host gate arrays are
+        copied in every apply_layer call and the branch indices of the layer's
+        last gate are read back to the host; wall clock around each segment."""
+        torch = self.torch
+        el, upd, h2d, d2h, nsteps = 0.0, 0, 0, 0, 0
+        for pending, run in timed_segments(self.plan.take("e2e", count)):
+            self.untimed(pending)
+            if not run:
+                continue
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for l in run:
+                for n, s in self.sims.items():
+                    layer = self.w["circuits"][n].layers[l]
+                    s.apply_layer(layer)
+                    h2d += layer.gates.nbytes + layer.kraus.nbytes + layer.left_qubits.nbytes
+                for s in self.sims.values():
+                    s.sample_branch(s.gates_applied - 1, 1)
+                    d2h += 4 * s.B
+            torch.cuda.synchronize()
+            el += time.perf_counter() - t0
+            upd += self.updates(run)
+            nsteps += len(run)
+        return dict(value=upd / el if el > 0 else None, h2d=h2d // max(nsteps, 1), d2h=d2h // max(nsteps, 1),
+                    steps=nsteps)
+
+    def profile_step(self):
+        """Per-kernel CUDA events over one further layer; the handles run one
+        after another so that no kernel's duration includes another handle's
+        work.  Returns ({kind: (ms, launches)}, {kind: algorithmic CMAC}, updates)."""
+        torch = self.torch
+        ev = self.plan.take("profile", 1)
+        self.untimed(ev[:-1])
+        l = ev[-1][1]
         torch.cuda.synchronize()
         work = {}
-        for n, s in sims.items():
+        for n, s in self.sims.items():
             _, bonds = s.export_mps(0)
-            for k, v in layer_work(w["circuits"][n].layers[l2].left_qubits, bonds, args.chi).items():
+            for k, v in layer_work(self.w["circuits"][n].layers[l].left_qubits, bonds, self.args.chi).items():
                 work[k] = work.get(k, 0.0) + v * s.B
-        out["profile_work"] = work
-        for s in sims.values():
+        for s in self.sims.values():
             s.profile(True)
         torch.cuda.nvtx.range_push("profiled_layer")
-        for n, s in sims.items():
-            s.apply_layer(w["circuits"][n].layers[l2])
+        for n, s in self.sims.items():
+            s.apply_layer(self.w["circuits"][n].layers[l])
             torch.cuda.synchronize()
         torch.cuda.nvtx.range_pop()
         prof = {}
-        for s in sims.values():
+        for s in self.sims.values():
             for k, (kms, cnt) in s.profile(False, collect=True).items():
                 a, b = prof.get(k, (0.0, 0))
                 prof[k] = (a + kms, b + cnt)
-        out["profile"] = prof
-        out["profile_updates"] = sum(len(w["circuits"][n].layers[l2].left_qubits) * s.B for n, s in sims.items())
-        out["next_layer"] = l2 + 1
-    return out
+        return prof, work, self.updates([l])
+
+    def measure(self):
+        return {n: s.measure() for n, s in self.sims.items()}
+
+    def destroy(self):
+        for s in self.sims.values():
+            s.destroy()
+        self.sims = {}
 
 
-def observable_error(res_m, res_d, bf_by_n):
-    """Per-observable |mixed - FP64| over the FP64 trajectories (same ids)."""
+def observable_error(res_m, res_d):
+    """Per-observable |mixed - FP64| over trajectories with the same ids, and
+    the largest |mean_mixed - mean_FP64| / combined standard error."""
     errs = {"z": [], "zz": [], "s_half": []}
+    zmax = 0.0
     for n, rd in res_d.items():
         rm = res_m[n]
-        k = bf_by_n[n]
-        errs["z"].append(np.abs(rm["z"][:k] - rd["z"][:k]).ravel())
-        errs["zz"].append(np.abs(rm["zz"][:k] - rd["zz"][:k]).ravel())
-        errs["s_half"].append(np.abs(rm["s_half"][:k] - rd["s_half"][:k]).ravel())
+        for k in errs:
+            errs[k].append(np.abs(rm[k] - rd[k]).ravel())
+        for k, km, ks in (("z", "z_mean", "z_stderr"), ("zz", "zz_mean", "zz_stderr")):
+            se = np.sqrt(rm[ks] ** 2 + rd[ks] ** 2)
+            ok = se > 0
+            if ok.any():
+                zmax = max(zmax, float(np.max(np.abs(rm[km] - rd[km])[ok] / se[ok])))
+        se = np.hypot(rm["s_half_stderr"], rd["s_half_stderr"])
+        if se > 0:
+            zmax = max(zmax, abs(rm["s_half_mean"] - rd["s_half_mean"]) / se)
     out = {}
     for k, v in errs.items():
         v = np.concatenate(v) if v else np.zeros(1)
         out[k] = {"median_abs": float(np.median(v)), "max_abs": float(np.max(v))}
+    out["max_mean_z_score"] = zmax
     return out
 
 
@@ -269,7 +368,6 @@ def _oracle_worker(job):
     w = I.workload_uneven(seed=seed, n_traj=16, depth=depth)
     circ = w["circuits"][n]
     marks = []
-    t_start = time.perf_counter()
 
     class Stop(Exception):
         pass
@@ -317,104 +415,7 @@ def cpu_baseline(args, pre_layers, budget_s):
                       f"rate = updates / (summed timed seconds / cores)"}
 
 
-# --- main ----------------------------------------------------------------------------------
-
-def main():
-    args = parse()
-    if args.impl == "reference":
-        return main_reference(args)
-    import torch
-
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-        torch.cuda.set_device(local)
-    from paper_2508_05745_gb300 import build, lemps as L
-    build.build()
-    w = workload(args)
-    # replicas: rank r takes trajectories [r*B, (r+1)*B) of the global sample
-    per_rank = args.traj
-    labels = w["n_of_traj"][rank * per_rank:(rank + 1) * per_rank]
-    want = [int(x) for x in args.sizes.split(",")]
-    if len(want) == 3:
-        sizes = {int(n): int(np.sum(labels == n)) for n in (24, 48, 64)}
-    else:
-        sizes = {n: per_rank // len(want) for n in want}
-    log(f"sizes {sizes}")
-    offsets = trajectory_offsets(rank, per_rank, sizes)
-    barrier = None
-    if world > 1:
-        import torch.distributed as dist
-        barrier = dist.barrier
-    clocks = ClockSampler(local)
-    clocks.start()
-    mixed = run_arm(L, torch, w, sizes, "mixed", args, args.pre_layers, args.warmup, args.steps,
-                    profile_step=True, e2e=not args.no_e2e, offsets=offsets, barrier=barrier)
-    log(f"mixed arm: {mixed['updates']} updates in {mixed['ms']:.1f} ms")
-    clk = clocks.stop()
-    ms = mixed["ms"]
-    if world > 1:
-        import torch.distributed as dist
-        ms, total_updates = combine_over_ranks(torch, dist, ms, mixed["updates"], "cuda")
-    else:
-        total_updates = mixed["updates"]
-    value = total_updates / (ms / 1000.0)
-
-    # FP64 comparator on the first trajectories of each size, same layers
-    fp64 = None
-    obs_err = None
-    if not args.no_fp64 and rank == 0:
-        bf = {n: min(b, max(1, args.fp64_traj * b // max(1, sum(sizes.values())))) for n, b in sizes.items() if b}
-        d = run_arm(L, torch, w, bf, "fp64", args, args.pre_layers, args.warmup, args.steps)
-        fp64 = d["updates"] / (d["ms"] / 1000.0)
-        log(f"fp64 arm: {d['updates']} updates in {d['ms']:.1f} ms")
-        # bring the mixed sims to the same depth as the FP64 sims and compare
-        res_d = {}
-        for n, s in d["sims"].items():
-            res_d[n] = s.measure()
-        # mixed sims advanced further (e2e + profile steps): rerun a mixed arm at equal depth
-        mm = run_arm(L, torch, w, bf, "mixed", args, args.pre_layers, args.warmup, args.steps)
-        res_m = {n: s.measure() for n, s in mm["sims"].items()}
-        obs_err = observable_error(res_m, res_d, bf)
-        log("observable error done")
-        for s in list(d["sims"].values()) + list(mm["sims"].values()):
-            s.destroy()
-    prof = mixed["profile"]
-    dom = max(prof.items(), key=lambda kv: kv[1][0])
-    total_prof = sum(v[0] for v in prof.values())
-    rl = roofline(prof, mixed["profile_work"], args)
-    line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "c64 (FP64 unraveling/weights)", "data": "synthetic",
-        "config": {"workload": "uneven: n~U{24,48,64}, depth 32 Haar brickwork, 2q depolarizing p=0.005, chi_max=128",
-                   "trajectories_per_gpu": per_rank, "by_n": sizes, "pre_layers": args.pre_layers,
-                   "step": "one layer over the batch", "l2": "state >> 129 MB L2 (streamed from HBM each step)",
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
-        "fp64_value": fp64, "mixed_over_fp64": (value / fp64) if fp64 else None,
-        "observable_error_mixed_vs_fp64": obs_err,
-        "e2e": {"value": mixed.get("e2e_value"), "unit": UNIT, "h2d_bytes_per_step": mixed.get("h2d"),
-                "d2h_bytes_per_step": mixed.get("d2h")},
-        "gpu_launches": gpu_launches(prof, args.steps, mixed["profile_updates"], mixed["updates"]),
-        "kernel_share": {k: round(v[0] / total_prof, 4) for k, v in prof.items() if total_prof > 0},
-        "roofline": rl, "clocks": clk,
-    }
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args, args.pre_layers, args.cpu_sample_s)
-        log("cpu baseline done")
-    for s in mixed["sims"].values():
-        s.destroy()
-    if rank == 0:
-        print(json.dumps(line))
-
-
-def gpu_launches(prof, steps, prof_updates, updates):
-    launches = sum(v[1] for v in prof.values())  # launches of one profiled step
-    return int(launches * steps)
-
+# --- roofline -------------------------------------------------------------------------------
 
 # Algorithmic work, in complex multiply-adds (1 CMAC = 8 real flops), of one
 # layer for one trajectory, per kernel kind, from the bond dimensions b[] of
@@ -461,50 +462,177 @@ def layer_work(left_qubits, bonds, chi):
     return w
 
 
-# DRAM bytes (read + write) of one ncu capture of the kernel as it is now
-# (profiles/<kernel>_chi128_n48_b152.md); remove an entry when its kernel changes.
-NCU_TRAFFIC = {
-    "eig": {"bytes": 243.2e6,
-            "note": "one k_heev launch at the n_Gram=256 gate (gate 12 of layer 8), 152 trajectories, dram read "
-                    "115.7 MB + write 127.5 MB: 1.60 MB per trajectory against ~1.5 MB of algorithmic bytes (G read, "
-                    "reflectors written and read back, U written); bench launches mix gate sizes, so this is the "
-                    "full-size launch, not the average"},
-}
+# Arithmetic type of each kernel kind in the mixed arm: the eigensolver works
+# in complex128 on the FP64 pipe, the others in complex64 on the FP32 pipe.
+MIXED_PIPE = {"eig": "fp64", "contract": "fp32", "gram": "fp32", "split": "fp32", "move": "fp32"}
 
 
-def fp32_peak_tflops():
+def peaks_tflops():
+    """SIMT peaks from unit counts and the maximum SM clock: 152 SMs x 128 FP32
+    lanes x 2 flop (FMA) per clock, and the FP64 pipe at 1/64 of that (2 FP64
+    FMA per SM and clock: the nominal 1.25 TFLOP/s of GB300 at 2070 MHz)."""
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     sm_max = 2070.0
     if os.path.exists(peaks_path):
         sm_max = json.load(open(peaks_path)).get("sm_max_mhz", sm_max)
-    # FP32 SIMT peak from unit counts: 152 SMs x 128 FP32 lanes x 2 flop x clock
-    return 152 * 128 * 2 * sm_max * 1e6 / 1e12
+    fp32 = 152 * 128 * 2 * sm_max * 1e6 / 1e12
+    return {"fp32": fp32, "fp64": fp32 / 64.0}
 
 
-def roofline(prof, work, args, fp64=False):
+def roofline(prof, work, pipes):
     """Per kernel kind: achieved TFLOP/s = algorithmic flops of the profiled
     layer (layer_work over every trajectory, from the actual bond dimensions)
-    / the summed CUDA-event time of that kind's launches; the dominant kind is
-    reported."""
-    peak = fp32_peak_tflops() / (64.0 if fp64 else 1.0)
+    / the summed CUDA-event time of that kind's launches, against the peak of
+    the pipe it computes on; the dominant kind is reported."""
+    peaks = peaks_tflops()
     rows = {}
     for kind, (ms, cnt) in prof.items():
         if kind not in work or ms <= 0:
             continue
         flops = 8.0 * work[kind]
         ach = flops / (ms / 1000.0) / 1e12
+        pk = peaks[pipes.get(kind, "fp32")]
         rows[kind] = {"ms": ms, "launches": cnt, "avg_launch_ms": ms / max(cnt, 1), "gflop": flops / 1e9,
-                      "achieved_tflops": ach, "frac": ach / peak}
+                      "achieved_tflops": ach, "pipe": pipes.get(kind, "fp32"), "peak_tflops": pk, "frac": ach / pk}
     dom = max(prof.items(), key=lambda kv: kv[1][0])[0]
     r = rows.get(dom, {})
-    cap = NCU_TRAFFIC.get(dom)
-    return {"kernel": dom, "bound": "alu", "achieved": r.get("achieved_tflops"), "peak": peak, "unit": "TFLOP/s",
-            "frac": r.get("frac"), "traffic": cap["bytes"] if cap else None,
-            "traffic_note": cap["note"] if cap else None, "avg_launch_ms": r.get("avg_launch_ms"),
-            "peak_note": "FP32 SIMT peak derived from 152 SMs x 128 lanes x 2 x max SM clock (MEASURED_PEAKS sm_max_mhz); of derived",
+    return {"kernel": dom, "bound": "alu", "achieved": r.get("achieved_tflops"), "peak": r.get("peak_tflops"),
+            "unit": "TFLOP/s", "frac": r.get("frac"), "traffic": None,
+            "traffic_note": "DRAM bytes come from ncu captures, which never run inside the bench; "
+                            "the per-kernel ncu figures are kept with the profiles",
+            "avg_launch_ms": r.get("avg_launch_ms"),
+            "peak_note": "of derived: SIMT peak from 152 SMs x 128 FP32 lanes x 2 flop x max SM clock "
+                         "(MEASURED_PEAKS sm_max_mhz); FP64 pipe = FP32 / 64",
             "work_note": "algorithmic complex multiply-adds of the profiled layer from the bond dimensions "
                          "before it (bench.py layer_work), 8 flops each",
             "kernels": rows}
+
+
+# --- main ----------------------------------------------------------------------------------
+
+def spawn_ranks(args):
+    """--gpus N > 1 without a launcher: run this script under
+    torch.distributed.run with N ranks on 127.0.0.1 and pass its output on."""
+    import socket
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={args.gpus}",
+           "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.abspath(__file__)] + sys.argv[1:]
+    return subprocess.call(cmd)
+
+
+def main():
+    args = parse()
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        sys.exit(spawn_ranks(args))
+    if args.impl == "reference":
+        return main_reference(args)
+    if args.steps < 1 or args.warmup < 0:
+        raise SystemExit("--steps must be >= 1 and --warmup >= 0")
+    import torch
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2508_05745_gb300 import build, lemps as L
+    build.build()
+    w = workload(args)
+    # replicas: rank r takes trajectories [r*B, (r+1)*B) of the global sample
+    per_rank = args.traj
+    labels = w["n_of_traj"][(rank * per_rank) % 16384:][:per_rank]
+    want = [int(x) for x in args.sizes.split(",")]
+    if len(want) == 3:
+        sizes = {int(n): int(np.sum(labels == n)) for n in (24, 48, 64)}
+    else:
+        sizes = {n: per_rank // len(want) for n in want}
+    log(f"sizes {sizes}")
+    offsets = trajectory_offsets(rank, per_rank, sizes)
+    barrier = None
+    if world > 1:
+        import torch.distributed as dist
+        barrier = dist.barrier
+
+    mixed = Arm(L, torch, w, sizes, "mixed", args, offsets=offsets, barrier=barrier)
+    mixed.warmup(args.warmup)
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms, updates, layers = mixed.timed(args.steps)
+    clk = clocks.stop()
+    log(f"mixed arm: {updates} updates in {ms:.1f} ms over layers {layers} ({mixed.resets} handle sets)")
+    if world > 1:
+        import torch.distributed as dist
+        ms, total_updates = combine_over_ranks(torch, dist, ms, updates, "cuda")
+    else:
+        total_updates = updates
+    value = total_updates / (ms / 1000.0)
+    e2e = None if args.no_e2e else mixed.e2e(min(args.e2e_steps, args.steps))
+    prof, work, prof_updates = mixed.profile_step()
+    mixed.destroy()
+
+    # FP64 comparator: the same path in complex128 on a batch that fills the
+    # GPU, and a mixed arm on the same trajectories and layers for the
+    # observable error
+    fp64 = None
+    obs_err = None
+    fp64_info = None
+    if not args.no_fp64 and rank == 0:
+        tot = max(1, sum(sizes.values()))
+        bf = {n: max(1, args.fp64_traj * b // tot) for n, b in sizes.items() if b}
+        k64 = max(1, min(args.fp64_steps, args.steps))
+        d = Arm(L, torch, w, bf, "fp64", args, offsets=offsets)
+        d.warmup(min(args.warmup, 1))
+        d_ms, d_upd, d_layers = d.timed(k64)
+        fp64 = d_upd / (d_ms / 1000.0)
+        fp64_info = {"trajectories": sum(bf.values()), "by_n": bf, "timed_steps": k64, "ms_per_step": d_ms / k64}
+        log(f"fp64 arm: {d_upd} updates in {d_ms:.1f} ms")
+        res_d = d.measure()
+        d.destroy()
+        mm = Arm(L, torch, w, bf, "mixed", args, offsets=offsets)
+        mm.warmup(min(args.warmup, 1))
+        mm.timed(k64)
+        res_m = mm.measure()
+        mm.destroy()
+        obs_err = observable_error(res_m, res_d)
+        log("observable error done")
+    rl = roofline(prof, work, MIXED_PIPE)
+    total_prof = sum(v[0] for v in prof.values())
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "c64 contractions, c128 eigensolver, FP64 unraveling/weights", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "trajectories_per_gpu": per_rank, "by_n": sizes,
+                   "pre_layers": args.pre_layers, "timed_layers": layers, "handle_sets": mixed.resets,
+                   "step": "one layer over the batch", "l2": "state >> 129 MB L2 (streamed from HBM each step)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "fp64_value": fp64, "fp64": fp64_info, "mixed_over_fp64": (value / fp64) if fp64 else None,
+        "observable_error_mixed_vs_fp64": obs_err,
+        "e2e": None if e2e is None else {"value": e2e["value"], "unit": UNIT, "h2d_bytes_per_step": e2e["h2d"],
+                                         "d2h_bytes_per_step": e2e["d2h"], "steps": e2e["steps"]},
+        "gpu_launches": gpu_launches(prof, args.steps),
+        "kernel_share": {k: round(v[0] / total_prof, 4) for k, v in prof.items() if total_prof > 0},
+        "roofline": rl, "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args, args.pre_layers, args.cpu_sample_s)
+        log("cpu baseline done")
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line))
+
+
+def gpu_launches(prof, steps):
+    launches = sum(v[1] for v in prof.values())  # launches of one profiled step
+    return int(launches * steps)
 
 
 def main_reference(args):
@@ -515,7 +643,7 @@ def main_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": 0,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "uneven: n~U{24,48,64}, depth 32 Haar brickwork, 2q depolarizing p=0.005, chi_max=128"},
+            "config": {"workload": WORKLOAD},
             "cpu_baseline": cb,
             "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))

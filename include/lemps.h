@@ -49,9 +49,11 @@ typedef enum {
 
 typedef enum {
   LEMPS_FP64 = 0,      /* complex128 storage and arithmetic everywhere */
-  LEMPS_MIXED = 1      /* complex64 MPS storage, contractions and eigensolver;
-                          reduced densities, unraveling, branch weights,
-                          discarded weights and entropies in FP64 */
+  LEMPS_MIXED = 1      /* complex64 MPS storage and contractions (two-site
+                          tensor, Gram matrix, projections, centre moves);
+                          the Gram eigensolve of the split, reduced densities,
+                          unraveling, branch weights, discarded weights and
+                          entropies in FP64 (complex128) */
 } lemps_precision;
 
 typedef enum {
@@ -223,9 +225,15 @@ lemps_status unravel_grad(const void* theta, int32_t theta_fp64, int64_t batch, 
                           const double* p, const double* h, double* cost, double* grad,
                           double* rho_out, void* stream);
 
-/* `steps` gradient-descent steps H <- H - lr * Gamma on the device for the
- * reduced states rho_a (device [batch][2][2] complex, e.g. rho_out above);
- * h is updated in place; cost_trace: device [steps][batch] or NULL. */
+/* `steps` gradient-descent steps H <- H - alpha * Gamma on the device (the
+ * per-site unraveling optimisation of the differentiation workload, driving
+ * the cost of Eq. target_optimal_unitary towards its minimum E_oF of Thm. 2)
+ * for the reduced states rho_a (device [batch][2][2] complex, e.g. rho_out
+ * above).  The step size is found by backtracking: it starts at lr, is halved
+ * until E(H - alpha Gamma) <= E(H) - 1e-4 alpha ||Gamma||_F^2 (the step is
+ * skipped once alpha < 1e-12), and the next step starts from twice the final
+ * alpha (at most 1e4).  h is updated in place; cost_trace: device
+ * [steps][batch] costs after each step, or NULL. */
 lemps_status unravel_descend(const double* rho_a, const double* p, int64_t batch, int32_t steps,
                              double lr, double* h, double* cost_trace, void* stream);
 

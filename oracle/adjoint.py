@@ -78,13 +78,32 @@ def fd_gradient(h: np.ndarray, rho_a: np.ndarray, kraus: np.ndarray, step: float
 
 
 def gradient_descent(h0, rho_a, kraus, steps: int = 50, lr: float = 0.5):
-    """Plain gradient descent H <- H - lr * Gamma with FD gradients; returns the
-    cost after each step (oracle of the on-device optimization loop)."""
+    """Gradient descent H <- H - alpha * Gamma with FD gradients and a
+    backtracking step size (oracle of the on-device optimization loop).
+
+    The step size starts at lr; at every step it is halved until the cost
+    decreases by at least 1e-4 * alpha * ||Gamma||_F^2 (Armijo's sufficient
+    decrease), the step is skipped if alpha falls below 1e-12, and the next
+    step starts from twice the final alpha (at most 1e4).  Returns (H, the
+    cost after each step)."""
     h = np.array(h0, dtype=np.complex128)
+    e = expected_entropy(h, rho_a, kraus)
+    alpha = lr
     costs = []
     for _ in range(steps):
-        h = h - lr * fd_gradient(h, rho_a, kraus)
-        costs.append(expected_entropy(h, rho_a, kraus))
+        g = fd_gradient(h, rho_a, kraus)
+        gg = float(np.sum(np.abs(g) ** 2))
+        while True:
+            h_try = h - alpha * g
+            e_try = expected_entropy(h_try, rho_a, kraus)
+            if e_try <= e - 1e-4 * alpha * gg:
+                h, e = h_try, e_try
+                break
+            alpha *= 0.5
+            if alpha < 1e-12:
+                break
+        costs.append(e)
+        alpha = min(2.0 * alpha, 1e4)
     return h, np.array(costs)
 
 

@@ -261,16 +261,43 @@ __global__ void k_cost_grad(const zd* rho, const double* p, const zd* h, int64_t
     for (int i = 0; i < 16; ++i) grad[b * 16 + i] = g[i];
 }
 
+// Gradient steps H <- H - alpha Gamma with a backtracking step size: each
+// step tries alpha (lr at the first step, then twice the previous step's
+// accepted or last tried value, at most kMaxStep), halving it until the
+// sufficient-decrease (Armijo) condition E(H - alpha Gamma) <= E(H) -
+// kArmijo alpha ||Gamma||_F^2 holds; below kMinStep the step is skipped.
+// trace[s][b] = cost after step s.
+constexpr double kArmijo = 1e-4, kMinStep = 1e-12, kMaxStep = 1e4;
+
 __global__ void k_descend(const zd* rho, const double* p, int64_t batch, int steps, double lr, zd* h, double* trace) {
   const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= batch) return;
-  zd hh[16], g[16], r[4];
+  zd hh[16], g[16], hn[16], r[4];
   for (int i = 0; i < 16; ++i) hh[i] = h[b * 16 + i];
   for (int i = 0; i < 4; ++i) r[i] = rho[b * 4 + i];
+  const double pb = p[b];
+  double e = cost_grad(r, pb, hh, g);
+  double alpha = lr;
   for (int s = 0; s < steps; ++s) {
-    cost_grad(r, p[b], hh, g);
-    for (int i = 0; i < 16; ++i) hh[i] -= lr * g[i];
-    if (trace) trace[(int64_t)s * batch + b] = cost_grad(r, p[b], hh, nullptr);
+    double gg = 0.0;
+    for (int i = 0; i < 16; ++i) gg += norm2(g[i]);
+    bool moved = false;
+    for (;;) {
+      for (int i = 0; i < 16; ++i) hn[i] = hh[i] - alpha * g[i];
+      const double en = cost_grad(r, pb, hn, nullptr);
+      if (en <= e - kArmijo * alpha * gg) {
+        moved = true;
+        break;
+      }
+      alpha *= 0.5;
+      if (alpha < kMinStep) break;
+    }
+    if (moved) {
+      for (int i = 0; i < 16; ++i) hh[i] = hn[i];
+      e = cost_grad(r, pb, hh, g);
+    }
+    if (trace) trace[(int64_t)s * batch + b] = e;
+    alpha = fmin(2.0 * alpha, kMaxStep);
   }
   for (int i = 0; i < 16; ++i) h[b * 16 + i] = hh[i];
 }

@@ -136,6 +136,9 @@ struct lemps_sim {
     v.ws1 = reinterpret_cast<cpx<R>*>(ws[1]);
     v.ws2 = reinterpret_cast<cpx<R>*>(ws[2]);
     v.ws3 = reinterpret_cast<cpx<R>*>(ws[3]);
+    v.g64 = reinterpret_cast<zd*>(ws[1]);
+    v.u64 = reinterpret_cast<zd*>(ws[2]);
+    v.h64 = reinterpret_cast<zd*>(ws[3]);
     v.ws_stride = ws_stride;
     v.evals = evals;
     v.rho12 = rho12;
@@ -181,20 +184,20 @@ void move_center_to(lemps_sim* h, int target) {
 
 constexpr int kHeevThreads = 512;
 
-// Hermitian eigensolve of the Gram matrix; keeps the top min(chi_max,
-// #{l > cutoff * trace}) eigenpairs (vectors = 1) or computes every
-// eigenvalue (vectors = 0, cutoff = 0).
+// Hermitian eigensolve of the Gram matrix, in complex128 in both precisions;
+// keeps the top min(chi_max, #{l > cutoff * trace}) eigenpairs (vectors = 1)
+// or computes every eigenvalue (vectors = 0, cutoff = 0).
 template <class R>
 void launch_heev(lemps_sim* h, int q, int mode, double cutoff, int keep_max, int vectors) {
-  const size_t smem = HeevSmem<R>::kBytes;
-  static bool attr = false;  // one opt-in per instantiation
+  const size_t smem = HeevSmem<double>::kBytes;
+  static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_heev<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_heev<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr = true;
   }
   h->timed(LEMPS_K_EIG, [&] {
-    k_heev<R><<<(unsigned)h->B, kHeevThreads, smem, h->stream>>>(heev_view(h->view<R>()), q, mode, cutoff,
-                                                                  keep_max, vectors);
+    k_heev<double><<<(unsigned)h->B, kHeevThreads, smem, h->stream>>>(heev_view(h->view<R>()), q, mode, cutoff,
+                                                                       keep_max, vectors);
   });
 }
 
@@ -437,7 +440,10 @@ lemps_status sim_create(const lemps_config* cfg, lemps_handle* out) {
   h->site_off = (int64_t*)A(sizeof(int64_t) * n);
   h->cap = (int32_t*)A(sizeof(int32_t) * (n + 1));
   h->bond = (int32_t*)A(sizeof(int32_t) * (n + 1) * h->B);
-  for (int i = 0; i < 4; ++i) h->ws[i] = A(h->elem * h->ws_stride * h->B);
+  // ws0 (two-site tensor) in the storage precision; ws1..ws3 at 16 bytes per
+  // entry: the Gram matrix, eigenvectors and reflectors are complex128
+  h->ws[0] = A(h->elem * h->ws_stride * h->B);
+  for (int i = 1; i < 4; ++i) h->ws[i] = A(sizeof(zd) * h->ws_stride * h->B);
   h->evals = (double*)A(sizeof(double) * 2 * h->cap_max * h->B);
   h->rho12 = (zd*)A(sizeof(zd) * 16 * h->B);
   h->top = (zd*)A(sizeof(zd) * 16 * h->B);

@@ -28,6 +28,12 @@ struct SimView {
   cpx<R>* ws1;               // [B][ws_stride] Gram matrix / reflectors
   cpx<R>* ws2;               // [B][ws_stride] eigenvectors / Q factor
   cpx<R>* ws3;               // [B][ws_stride] scratch
+  // complex128 views of ws1..ws3 (allocated at 16 bytes per entry in both
+  // precisions): the Gram matrix, its eigenvectors and the eigensolver's
+  // reflectors are FP64 in both modes
+  zd* g64;
+  zd* u64;
+  zd* h64;
   int64_t ws_stride;         // (2 chi)^2
   double* evals;             // [B][2 chi]
   zd* rho12;                 // [B][16]
@@ -556,7 +562,7 @@ __global__ void __launch_bounds__(kGemmThreads) k_apply_gram(SimView<R> s, int q
   const int32_t* bd = s.bond + t * (s.n + 1);
   const int dl = bd[q], dr = bd[q + 2];
   cpx<R>* th = s.ws0 + t * s.ws_stride;
-  cpx<R>* G = s.ws1 + t * s.ws_stride;
+  zd* G = s.g64 + t * s.ws_stride;   // FP64 input of the eigensolver
   // T (FP64 from the unraveling) is applied in the storage precision
   __shared__ cpx<R> T[16];
   if (threadIdx.x < 16) T[threadIdx.x] = cast<R>(s.top[t * 16 + threadIdx.x]);
@@ -586,8 +592,9 @@ __global__ void __launch_bounds__(kGemmThreads) k_apply_gram(SimView<R> s, int q
   const int ng = side == 0 ? 2 * dl : 2 * dr;
   auto st = [&](int i, int j, cpx<R> v) {
     if (j >= i) {
-      G[(int64_t)i * ng + j] = v;
-      G[(int64_t)j * ng + i] = conj(v);
+      const zd d = cast<double>(v);
+      G[(int64_t)i * ng + j] = d;
+      G[(int64_t)j * ng + i] = conj(d);
     }
   };
   if (side == 0) {
@@ -608,17 +615,17 @@ __device__ __forceinline__ int gram_size(const int32_t* bd, int k, int mode) {
 }
 
 template <class R>
-HeevView<R> heev_view(const SimView<R>& s) {
-  HeevView<R> h;
-  h.ws1 = s.ws1; h.ws2 = s.ws2; h.ws3 = s.ws3; h.ws_stride = s.ws_stride;
+HeevView<double> heev_view(const SimView<R>& s) {
+  HeevView<double> h;
+  h.ws1 = s.g64; h.ws2 = s.u64; h.ws3 = s.h64; h.ws_stride = s.ws_stride;
   h.evals = s.evals; h.kept = s.kept; h.trace = s.trace; h.bond = s.bond; h.status = s.status;
   h.nq = s.n; h.chi = s.chi; h.B = s.B;
   return h;
 }
 
 // ---- split and truncate ------------------------------------------------------
-// U (ws2, column-major, ng x keep) holds the kept eigenvectors of the Gram
-// matrix.  side 0 (left Gram, centre -> q+1):
+// U (ws2, complex128, column-major, ng x keep) holds the kept eigenvectors of
+// the Gram matrix; they enter the products in the storage precision.  side 0 (left Gram, centre -> q+1):
 //   A_q = U (left-orthonormal), B = U^dagger Theta, R = Theta - U B,
 //   A_{q+1} = B / ||B||.
 // side 1 (right Gram, centre -> q):
@@ -639,7 +646,8 @@ __global__ void __launch_bounds__(kGemmThreads) k_split(SimView<R> s, int q, int
   const int keep = s.kept[t];
   const double tot = s.trace[t];
   const cpx<R>* th = s.ws0 + t * s.ws_stride;
-  const cpx<R>* U = s.ws2 + t * s.ws_stride;
+  const zd* U64 = s.u64 + t * s.ws_stride;
+  auto U = [&](int64_t e) { return cast<R>(U64[e]); };
   const int64_t ld = 2 * dr;
   cpx<R>* A = site_ptr(s, q, t);
   cpx<R>* B = site_ptr(s, q + 1, t);
@@ -652,11 +660,11 @@ __global__ void __launch_bounds__(kGemmThreads) k_split(SimView<R> s, int q, int
   if (side == 0) {
     for (int e = threadIdx.x; e < 2 * dl * keep; e += blockDim.x) {
       const int row = e / keep, k = e % keep;
-      A[(int64_t)row * capm + k] = U[(int64_t)k * ng + row];
+      A[(int64_t)row * capm + k] = U((int64_t)k * ng + row);
     }
     // B = U^dagger Theta  (keep x 2dr)
     cta_gemm<R, true, false>(
-        keep, 2 * dr, 2 * dl, [&](int i, int k) { return conj(U[(int64_t)i * ng + k]); },
+        keep, 2 * dr, 2 * dl, [&](int i, int k) { return conj(U((int64_t)i * ng + k)); },
         [&](int k, int j) { return th[(int64_t)k * ld + j]; },
         [&](int i, int j, cpx<R> v) {
           bslot(i, j) = v;
@@ -666,18 +674,18 @@ __global__ void __launch_bounds__(kGemmThreads) k_split(SimView<R> s, int q, int
     __syncthreads();
     // residual Theta - U B
     cta_gemm<R, false, false>(
-        2 * dl, 2 * dr, keep, [&](int i, int k) { return U[(int64_t)k * ng + i]; },
+        2 * dl, 2 * dr, keep, [&](int i, int k) { return U((int64_t)k * ng + i); },
         [&](int k, int j) { return bslot(k, j); },
         [&](int i, int j, cpx<R> v) { rn += (double)norm2(th[(int64_t)i * ld + j] - v); }, sm);
   } else {
     for (int e = threadIdx.x; e < keep * 2 * dr; e += blockDim.x) {
       const int k = e / (2 * dr), c = e % (2 * dr);
-      bslot(k, c) = conj(U[(int64_t)k * ng + c]);
+      bslot(k, c) = conj(U((int64_t)k * ng + c));
     }
     // B = Theta U  (2dl x keep) into A_q
     cta_gemm<R, true, true>(
         2 * dl, keep, 2 * dr, [&](int i, int k) { return th[(int64_t)i * ld + k]; },
-        [&](int k, int j) { return U[(int64_t)j * ng + k]; },
+        [&](int k, int j) { return U((int64_t)j * ng + k); },
         [&](int i, int j, cpx<R> v) {
           A[(int64_t)i * capm + j] = v;
           bn += (double)norm2(v);
@@ -687,7 +695,7 @@ __global__ void __launch_bounds__(kGemmThreads) k_split(SimView<R> s, int q, int
     // residual Theta - B U^dagger
     cta_gemm<R, true, false>(
         2 * dl, 2 * dr, keep, [&](int i, int k) { return A[(int64_t)i * capm + k]; },
-        [&](int k, int j) { return conj(U[(int64_t)k * ng + j]); },
+        [&](int k, int j) { return conj(U((int64_t)k * ng + j)); },
         [&](int i, int j, cpx<R> v) { rn += (double)norm2(th[(int64_t)i * ld + j] - v); }, sm);
   }
   rn = block_sum(rn, redd);
@@ -805,7 +813,9 @@ __global__ void k_obs_from_rho12(const zd* rho12, int64_t B, int n, int q, doubl
   zz[t * (n - 1) + q] = (p00 - p01 - p10 + p11) * inv;
 }
 
-// Gram of the centre site A_k as (2 dl) x dr: G = M^dagger M (dr x dr) into ws1.
+// Gram of the centre site A_k as (2 dl) x dr: G = M^dagger M (dr x dr) into
+// the FP64 Gram buffer, accumulated in FP64 (the half-chain entropy is an
+// FP64 quantity in both precisions).
 template <class R>
 __global__ void k_site_gram(SimView<R> s, int k) {
   const int64_t t = blockIdx.x;
@@ -813,11 +823,12 @@ __global__ void k_site_gram(SimView<R> s, int k) {
   const int32_t* bd = s.bond + t * (s.n + 1);
   const int dl = bd[k], dr = bd[k + 1], capr = s.cap[k + 1];
   const cpx<R>* A = site_ptr(s, k, t);
-  cpx<R>* G = s.ws1 + t * s.ws_stride;
+  zd* G = s.g64 + t * s.ws_stride;
   for (int e = threadIdx.x; e < dr * dr; e += blockDim.x) {
     int i = e / dr, j = e % dr;
-    cpx<R> acc = mk<R>(0, 0);
-    for (int r = 0; r < 2 * dl; ++r) cfmac(acc, A[(int64_t)r * capr + i], A[(int64_t)r * capr + j]);
+    zd acc = mk(0.0, 0.0);
+    for (int r = 0; r < 2 * dl; ++r)
+      cfmac(acc, cast<double>(A[(int64_t)r * capr + i]), cast<double>(A[(int64_t)r * capr + j]));
     G[e] = acc;
   }
 }

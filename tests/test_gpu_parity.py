@@ -1,9 +1,15 @@
 """GPU parity tests: the CUDA path (through the C ABI) against the CPU oracle on
 the same seeded inputs and Philox stream.  Tolerances: FP64 mode 1e-10 per
-trajectory on observables and states (1e-8 after hundreds of truncating gates),
-mixed mode 1e-4 per trajectory on trajectories whose branch sequence matches,
-averages within 4 standard errors of exact density-matrix evolution."""
+trajectory on observables and states, relative to the observable's scale (1
+for <Z>, <ZZ> and the entropy in nats; the value itself for the error bound,
+with an absolute floor set by the FP64 residual of the discarded weight);
+mixed mode 1e-4 per trajectory; trajectory averages of mixed and FP64 within 3
+combined standard errors, and averages within 4 standard errors of exact
+density-matrix evolution."""
+import concurrent.futures
 import math
+import multiprocessing
+import os
 
 import numpy as np
 import pytest
@@ -118,8 +124,9 @@ def test_small_exact_averages_match_density_matrix(small_exact):
 
 
 def test_small_exact_mixed_precision(L, small_exact):
-    """Mixed mode (complex64 storage and eigensolver): trajectories with the
-    same branch sequence agree with the FP64 oracle to 1e-4."""
+    """Mixed mode (complex64 storage and contractions, FP64 eigensolver):
+    trajectories with the same branch sequence agree with the FP64 oracle to
+    1e-4."""
     w, res64, br64, _ = small_exact
     sim, res, br = run_gpu(L, w["circuit"], 16, 256, seed=0, precision="mixed")
     sim.destroy()
@@ -135,35 +142,54 @@ def test_small_exact_mixed_precision(L, small_exact):
 
 # --- truncation, uneven bond dimensions ---------------------------------------------
 
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-9), ("mixed", 2e-3)])
+def close(a, b, tol, scale=1.0):
+    """|a - b| <= tol * max(|b|, scale), elementwise."""
+    a, b = np.asarray(a), np.asarray(b)
+    return np.all(np.abs(a - b) <= tol * np.maximum(np.abs(b), scale))
+
+
+def bound_tol(ref_bound, precision):
+    """Error-bound tolerance.  FP64: 1e-10 relative; the discarded weight of a
+    split is the FP64 residual ||Theta - U U^dagger Theta||^2, accurate to a
+    few eps_64 of ||Theta||^2, and each layer adds 4 sqrt(2 sum eps), whose
+    derivative 2 sqrt(2) / sqrt(sum eps) is at most ~1e8 for the layers where
+    anything is discarded, hence the 1e-8 * eps_64-level floor of 1e-12 per
+    layer.  Mixed: 1e-4 like the observables."""
+    if precision == "mixed":
+        return 1e-4 * max(1.0, abs(ref_bound))
+    return 1e-10 * abs(ref_bound) + 1e-12 * 10
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed", 1e-4)])
 def test_truncated_run_matches_oracle_mps(L, precision, tol):
-    """Heavy truncation (chi=4): the cut often falls between close Schmidt
-    values, which amplifies complex64 rounding (error ~ eps_32 / gap), so the
-    mixed tolerance here is 2e-3; the 1e-4 mixed bar is checked on the exact
-    and chi=64 workloads."""
+    """Heavy truncation (chi=4, cutoff 1e-14) on a 10-qubit depolarizing
+    brickwork: every trajectory has the oracle's branch sequence, and its
+    observables and error bound match the oracle's FP64 MPS trajectory (FP64:
+    1e-10; mixed: 1e-4; the Gram eigensolve is FP64 in both modes)."""
     circ = I.random_brickwork(10, 10, I.depolarizing_kraus(0.05), seed=4)
     n_traj = 16
     sim, res, br = run_gpu(L, circ, 4, n_traj, seed=3, precision=precision, cutoff=1e-14)
     sim.destroy()
-    matched = 0
+    errs = []
     for t in range(n_traj):
         ref = T.mps_trajectory(circ, t, 3, chi_max=4, cutoff=1e-14)
-        if precision == "mixed" and list(br[t]) != ref.branch:
-            continue
-        matched += 1
-        assert list(br[t]) == ref.branch
-        assert np.allclose(res["z"][t], ref.z, atol=tol)
-        assert np.allclose(res["zz"][t], ref.zz, atol=tol)
-        assert abs(res["s_half"][t] - ref.s_half) < tol
-        assert abs(res["eps_bound"][t] - ref.eps_bound) < max(tol, 1e-3 if precision == "mixed" else 0)
-    assert matched >= n_traj - 2
+        assert list(br[t]) == ref.branch, t
+        errs.append(max(np.abs(res["z"][t] - ref.z).max(), np.abs(res["zz"][t] - ref.zz).max(),
+                        abs(res["s_half"][t] - ref.s_half)))
+        assert close(res["z"][t], ref.z, tol), (t, errs[-1])
+        assert close(res["zz"][t], ref.zz, tol), (t, errs[-1])
+        assert close(res["s_half"][t], ref.s_half, tol), (t, errs[-1])
+        assert abs(res["eps_bound"][t] - ref.eps_bound) <= bound_tol(ref.eps_bound, precision), \
+            (t, res["eps_bound"][t], ref.eps_bound)
+    print(f"{precision}: max observable error {max(errs):.3e}")
     assert res["eps_hat"] > 0
 
 
 @pytest.mark.slow
 def test_ad_dephasing_n32_chi64(L):
     """The AD-then-dephasing workload (n=32, depth 20, chi=64): FP64 GPU
-    trajectories equal the oracle MPS trajectories; mixed mode within 1e-4."""
+    trajectories equal the oracle MPS trajectories to 1e-10; mixed mode has
+    the same branch sequences and matches within 1e-4."""
     w = I.workload_ad_dephasing(seed=0, n_traj=3)
     circ = w["circuit"]
     sim, res, br = run_gpu(L, circ, 64, 3, seed=0)
@@ -173,12 +199,14 @@ def test_ad_dephasing_n32_chi64(L):
     for t in range(2):
         ref = T.mps_trajectory(circ, t, 0, chi_max=64, cutoff=1e-20)
         assert list(br[t]) == ref.branch
-        assert np.allclose(res["z"][t], ref.z, atol=1e-8)
-        assert np.allclose(res["zz"][t], ref.zz, atol=1e-8)
-        assert abs(res["s_half"][t] - ref.s_half) < 1e-8
-        assert abs(res["eps_bound"][t] - ref.eps_bound) < 1e-6
-        if list(brm[t]) == ref.branch:
-            assert np.allclose(resm["z"][t], ref.z, atol=1e-4)
+        assert close(res["z"][t], ref.z, 1e-10)
+        assert close(res["zz"][t], ref.zz, 1e-10)
+        assert close(res["s_half"][t], ref.s_half, 1e-10)
+        assert abs(res["eps_bound"][t] - ref.eps_bound) <= bound_tol(ref.eps_bound, "fp64")
+        assert list(brm[t]) == ref.branch
+        assert close(resm["z"][t], ref.z, 1e-4)
+        assert close(resm["zz"][t], ref.zz, 1e-4)
+        assert close(resm["s_half"][t], ref.s_half, 1e-4)
 
 
 def test_coin_noise_full_depolarizing(L):
@@ -416,6 +444,11 @@ def test_unravel_grad_matches_oracle(L, chi, dtype):
 
 
 def test_descent_on_device_approaches_optimum(L):
+    """50 on-device gradient steps (backtracking step size) from random
+    unitaries: the cost never rises, never goes below the exact optimum
+    E_oF, follows the oracle's descent for the first five steps, and ends
+    within 2e-4 nats of the brute-force minimum over the U(theta, phi) family
+    on a 24 x 24 grid (chi = 8)."""
     w = I.workload_adjoint(seed=12, batch=32, chi=8)
     th = torch.from_numpy(w["theta"]).cuda()
     p = torch.from_numpy(w["p"]).cuda()
@@ -425,21 +458,19 @@ def test_descent_on_device_approaches_optimum(L):
     trace = trace.cpu().numpy()
     rho = rho.cpu().numpy()
     cost0 = cost0.cpu().numpy()
-    gap0, gap1 = [], []
     for b in range(32):
         kr = I.depolarizing_kraus(w["p"][b])
         eof = U.unraveling_entropy(U.optimal_unraveling(rho[b], kr)[0], rho[b])
         assert trace[-1, b] >= eof - 1e-12
         assert trace[-1, b] <= cost0[b] + 1e-12
-        gap0.append(cost0[b] - eof)
-        gap1.append(trace[-1, b] - eof)
-        if b < 4:
-            ref_h, ref_costs = A.gradient_descent(w["H"][b], rho[b], kr, steps=5, lr=0.5)
-            assert np.allclose(trace[:5, b], ref_costs, atol=1e-6)
+        assert np.all(np.diff(trace[:, b]) <= 1e-15)
+        if b < 8:
             grid = A.grid_search(rho[b], kr, 24)[0]
             assert grid >= eof - 1e-12      # the brute-force family is bounded by the optimum too
-    # 50 steps from a random unitary close most of the gap to the exact optimum
-    assert np.mean(gap1) < 0.5 * np.mean(gap0), (np.mean(gap0), np.mean(gap1))
+            assert trace[-1, b] - grid < 2e-4, (b, trace[-1, b] - grid, cost0[b] - eof)
+        if b < 4:
+            _, ref_costs = A.gradient_descent(w["H"][b], rho[b], kr, steps=5, lr=0.5)
+            assert np.allclose(trace[:5, b], ref_costs, atol=1e-6)
 
 
 def test_autograd_function_backward(L):
@@ -499,6 +530,21 @@ def test_canonical_form_after_truncation(L, precision, tol):
 
 # --- the chi=128 benchmark configuration, sampled -------------------------------------
 
+def _oracle_mps_job(args):
+    circ, t, seed, chi, cutoff = args
+    r = T.mps_trajectory(circ, t, seed, chi_max=chi, cutoff=cutoff)
+    return r.branch, r.z, r.zz, r.s_half, r.eps_bound
+
+
+def oracle_mps_many(circ, trajs, seed, chi, cutoff):
+    """The oracle's FP64 MPS trajectories, one process per trajectory (a
+    spawn pool: safe after CUDA initialisation in this process)."""
+    jobs = [(circ, int(t), seed, chi, cutoff) for t in trajs]
+    ctx = multiprocessing.get_context("spawn")
+    with concurrent.futures.ProcessPoolExecutor(min(len(jobs), os.cpu_count() or 1), mp_context=ctx) as ex:
+        return list(ex.map(_oracle_mps_job, jobs))
+
+
 @pytest.mark.slow
 def test_chi128_workload_sampled_against_oracle(L):
     """The chi=128 benchmark configuration, checked on sampled trajectories.
@@ -507,12 +553,11 @@ def test_chi128_workload_sampled_against_oracle(L):
     two-qubit depolarizing p=0.005), cut to 14 layers so that the middle bonds
     sit at chi=128 in the later layers.  Mixed precision runs in one handle of
     608 trajectories, the bench's per-size scale of one CTA per trajectory and
-    kernel; FP64 runs in a handle of 2.  Two trajectories of each are recomputed
-    by the oracle's FP64 MPS trajectory:
-    - FP64: equal branch sequences, observables to 1e-8, error bound to 1e-6.
-    - Mixed: observables within 1e-4 wherever the branch sequence matches
-      (complex64 rounding can flip a branch whose uniform falls within ~1e-7
-      of a threshold)."""
+    kernel; FP64 runs in a handle of 2.  Sixteen mixed and two FP64
+    trajectories are recomputed by the oracle's FP64 MPS trajectory:
+    - FP64: equal branch sequences, observables to 1e-10, error bound to
+      1e-10 relative (see bound_tol).
+    - Mixed: equal branch sequences on all sixteen, observables within 1e-4."""
     w = I.workload_uneven(seed=0, n_traj=8, depth=32)
     full = w["circuits"][48]
     circ = I.Circuit(full.n_qubits, full.layers[:14])
@@ -521,22 +566,64 @@ def test_chi128_workload_sampled_against_oracle(L):
     _, bonds = sim.export_mps(0)
     sim.destroy()
     assert bonds.max() == 128 and res["n_failed"] == 0
-    checked = 0
-    for t in (0, 1):
-        ref = T.mps_trajectory(circ, t, seed, chi_max=128, cutoff=1e-12)
-        if list(br[t]) != ref.branch:
-            continue
-        checked += 1
-        assert np.allclose(res["z"][t], ref.z, atol=1e-4)
-        assert np.allclose(res["zz"][t], ref.zz, atol=1e-4)
-        assert abs(res["s_half"][t] - ref.s_half) < 1e-4
-    assert checked >= 1
+    refs = oracle_mps_many(circ, range(16), seed, 128, 1e-12)
+    worst = 0.0
+    for t, (branch, z, zz, s_half, _) in enumerate(refs):
+        assert list(br[t]) == branch, t
+        worst = max(worst, np.abs(res["z"][t] - z).max(), np.abs(res["zz"][t] - zz).max(), abs(res["s_half"][t] - s_half))
+        assert close(res["z"][t], z, 1e-4), t
+        assert close(res["zz"][t], zz, 1e-4), t
+        assert close(res["s_half"][t], s_half, 1e-4), t
+    print(f"mixed chi=128: max observable error over 16 trajectories {worst:.3e}")
     sim, res, br = run_gpu(L, circ, 128, 2, seed=seed, precision="fp64", cutoff=1e-20)
     sim.destroy()
-    for t in (0, 1):
-        ref = T.mps_trajectory(circ, t, seed, chi_max=128, cutoff=1e-20)
-        assert list(br[t]) == ref.branch
-        assert np.allclose(res["z"][t], ref.z, atol=1e-8)
-        assert np.allclose(res["zz"][t], ref.zz, atol=1e-8)
-        assert abs(res["s_half"][t] - ref.s_half) < 1e-8
-        assert abs(res["eps_bound"][t] - ref.eps_bound) < 1e-6
+    refs = oracle_mps_many(circ, range(2), seed, 128, 1e-20)
+    for t, (branch, z, zz, s_half, eps_bound) in enumerate(refs):
+        assert list(br[t]) == branch
+        assert close(res["z"][t], z, 1e-10), (t, np.abs(res["z"][t] - z).max())
+        assert close(res["zz"][t], zz, 1e-10), (t, np.abs(res["zz"][t] - zz).max())
+        assert close(res["s_half"][t], s_half, 1e-10), (t, res["s_half"][t] - s_half)
+        assert abs(res["eps_bound"][t] - eps_bound) <= bound_tol(eps_bound, "fp64"), (t, res["eps_bound"][t], eps_bound)
+
+
+# --- mixed precision against FP64: trajectory averages ---------------------------------
+
+def _mean_z_scores(rm, rd):
+    """(mean_mixed - mean_FP64) / sqrt(se_mixed^2 + se_FP64^2) for every
+    observable (<Z_i>, <Z_i Z_i+1>, S(n/2)); zero where both errors vanish."""
+    zs = []
+    for km, ks in (("z_mean", "z_stderr"), ("zz_mean", "zz_stderr")):
+        se = np.sqrt(rm[ks] ** 2 + rd[ks] ** 2)
+        d = rm[km] - rd[km]
+        zs.append(np.where(se > 0, d / np.where(se > 0, se, 1.0), np.where(d == 0, 0.0, np.inf)))
+    se = math.hypot(rm["s_half_stderr"], rd["s_half_stderr"])
+    d = rm["s_half_mean"] - rd["s_half_mean"]
+    zs.append(np.array([d / se if se > 0 else (0.0 if d == 0 else np.inf)]))
+    return np.concatenate(zs)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("config", ["chi64_ad_dephasing", "chi128_depolarizing"])
+def test_mixed_and_fp64_means_agree_within_3_se(L, config):
+    """Trajectory-averaged observables of the mixed path agree with those of
+    the FP64 path within 3 combined standard errors, over 256 trajectories:
+    the chi=64 AD-then-dephasing workload (n=32, depth 20) and the chi=128
+    two-qubit depolarizing workload (its n=48 circuit, 12 layers, so that the
+    middle bonds reach chi=128)."""
+    if config == "chi64_ad_dephasing":
+        circ, chi = I.workload_ad_dephasing(seed=0, n_traj=256)["circuit"], 64
+    else:
+        full = I.workload_uneven(seed=0, n_traj=8, depth=32)["circuits"][48]
+        circ, chi = I.Circuit(full.n_qubits, full.layers[:12]), 128
+    out = {}
+    for precision, cutoff in (("mixed", 1e-12), ("fp64", 1e-20)):
+        sim = L.Simulation(circ.n_qubits, chi, 256, seed=21, precision=precision, cutoff=cutoff)
+        sim.run(circ)
+        out[precision] = sim.measure()
+        _, bonds = sim.export_mps(0)
+        sim.destroy()
+        assert out[precision]["n_failed"] == 0
+    assert bonds.max() == chi
+    z = _mean_z_scores(out["mixed"], out["fp64"])
+    print(f"{config}: |z| max {np.abs(z).max():.3e}, median {np.median(np.abs(z)):.3e} over {z.size} observables")
+    assert np.all(np.abs(z) < 3.0), z

@@ -232,13 +232,23 @@ def test_fd_gradient_directional_consistency(rng):
 
 
 def test_gradient_descent_approaches_eof():
-    w = I.workload_adjoint(seed=3, batch=1, chi=4)
-    rho = A.reduced_target(w["theta"][0])
-    kr = I.depolarizing_kraus(w["p"][0])
-    _, costs = A.gradient_descent(w["H"][0], rho, kr, steps=30, lr=0.5)
-    best = U.unraveling_entropy(U.optimal_unraveling(rho, kr)[0], rho)
-    assert costs[-1] <= costs[0] + 1e-12
-    assert costs[-1] >= best - 1e-12
+    """The backtracking descent never raises the cost, stays above the exact
+    optimum E_oF, and after 50 steps sits within 2e-4 nats of the brute-force
+    minimum over the U(theta, phi) family (a 24 x 24 grid), which itself lies
+    within 1e-4 of E_oF for these problems."""
+    w = I.workload_adjoint(seed=3, batch=2, chi=4)
+    for b in range(2):
+        rho = A.reduced_target(w["theta"][b])
+        rho = rho / np.trace(rho).real
+        kr = I.depolarizing_kraus(w["p"][b])
+        _, costs = A.gradient_descent(w["H"][b], rho, kr, steps=50, lr=0.5)
+        best = U.unraveling_entropy(U.optimal_unraveling(rho, kr)[0], rho)
+        grid = A.grid_search(rho, kr, 24)[0]
+        assert np.all(np.diff(costs) <= 1e-15)
+        assert costs[-1] <= A.expected_entropy(w["H"][b], rho, kr) + 1e-12
+        assert costs[-1] >= best - 1e-12
+        assert grid - best < 1e-4
+        assert costs[-1] - grid < 2e-4, (costs[-1] - grid, costs[0] - best)
 
 
 # --- output-distribution sampling and the concentration-improved bound ---------
