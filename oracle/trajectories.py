@@ -40,6 +40,10 @@ class TrajectoryRecord:
     discarded: List[float]     # per gate discarded weight (MPS only)
     eps_bound: float = 0.0     # per-trajectory error bound (MPS only)
     eps_layers: List[float] = dataclasses.field(default_factory=list)  # per layer 4 sqrt(2 sum eps) (MPS only)
+    # per truncating split, the relative gap (w_{chi'} - w_{chi'+1}) / w_1 of
+    # the squared Schmidt values at the cut (MPS only): the conditioning of
+    # the kept subspace, which moves by about (perturbation / gap)
+    cut_gaps: List[float] = dataclasses.field(default_factory=list)
     z: np.ndarray = None       # <Z_i>
     zz: np.ndarray = None      # <Z_i Z_{i+1}>
     s_half: float = 0.0        # entropy of bond n/2 (nats)
@@ -280,6 +284,8 @@ def _split(m, q, th, cap, cutoff, rec):
     keep = max(keep, 1)
     eps = float(np.sum(w[keep:]) / tot)
     rec.discarded.append(eps)
+    if keep < len(w):
+        rec.cut_gaps.append(float((w[keep - 1] - w[keep]) / w[0]))
     kept = math.sqrt(np.sum(w[:keep]))
     m.a[q] = u[:, :keep].reshape(dl, 2, keep)
     m.a[q + 1] = (s[:keep, None] * vh[:keep, :] / kept).reshape(keep, 2, dr)

@@ -160,20 +160,40 @@ def bound_tol(ref_bound, precision):
     return 1e-10 * abs(ref_bound) + 1e-12 * 10
 
 
+def mixed_tol(ref):
+    """Per-trajectory tolerance of the mixed path against the FP64 oracle.
+
+    Complex64 storage and arithmetic perturb each two-site Gram matrix by
+    about eps_32 ||G|| (a few roundings per entry and gate), and the kept
+    subspace of a truncating split then turns by about that perturbation over
+    the relative gap of the squared Schmidt values at the cut (Davis-Kahan);
+    the oracle records those gaps.  So the 1e-4 bar holds wherever every cut
+    of the trajectory has a relative gap of at least 1e-2, and a trajectory
+    with a closer cut gets 1e-6 / (its smallest gap)."""
+    g = min(ref.cut_gaps) if ref.cut_gaps else 1.0
+    return max(1e-4, 1e-6 / max(g, 1e-300))
+
+
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed", 1e-4)])
 def test_truncated_run_matches_oracle_mps(L, precision, tol):
     """Heavy truncation (chi=4, cutoff 1e-14) on a 10-qubit depolarizing
     brickwork: every trajectory has the oracle's branch sequence, and its
     observables and error bound match the oracle's FP64 MPS trajectory (FP64:
-    1e-10; mixed: 1e-4; the Gram eigensolve is FP64 in both modes)."""
+    1e-10; mixed: 1e-4, or 1e-6 over the smallest relative cut gap where the
+    cut falls between close Schmidt values, see mixed_tol; the Gram eigensolve
+    is FP64 in both modes)."""
     circ = I.random_brickwork(10, 10, I.depolarizing_kraus(0.05), seed=4)
     n_traj = 16
     sim, res, br = run_gpu(L, circ, 4, n_traj, seed=3, precision=precision, cutoff=1e-14)
     sim.destroy()
     errs = []
+    loose = 0
     for t in range(n_traj):
         ref = T.mps_trajectory(circ, t, 3, chi_max=4, cutoff=1e-14)
         assert list(br[t]) == ref.branch, t
+        if precision == "mixed":
+            tol = mixed_tol(ref)
+            loose += tol > 1e-4
         errs.append(max(np.abs(res["z"][t] - ref.z).max(), np.abs(res["zz"][t] - ref.zz).max(),
                         abs(res["s_half"][t] - ref.s_half)))
         assert close(res["z"][t], ref.z, tol), (t, errs[-1])
@@ -181,7 +201,8 @@ def test_truncated_run_matches_oracle_mps(L, precision, tol):
         assert close(res["s_half"][t], ref.s_half, tol), (t, errs[-1])
         assert abs(res["eps_bound"][t] - ref.eps_bound) <= bound_tol(ref.eps_bound, precision), \
             (t, res["eps_bound"][t], ref.eps_bound)
-    print(f"{precision}: max observable error {max(errs):.3e}")
+    print(f"{precision}: max observable error {max(errs):.3e}; trajectories with a cut gap below 1e-2: {loose}")
+    assert loose <= n_traj // 4
     assert res["eps_hat"] > 0
 
 
@@ -541,8 +562,19 @@ def oracle_mps_many(circ, trajs, seed, chi, cutoff):
     spawn pool: safe after CUDA initialisation in this process)."""
     jobs = [(circ, int(t), seed, chi, cutoff) for t in trajs]
     ctx = multiprocessing.get_context("spawn")
-    with concurrent.futures.ProcessPoolExecutor(min(len(jobs), os.cpu_count() or 1), mp_context=ctx) as ex:
-        return list(ex.map(_oracle_mps_job, jobs))
+    # one BLAS thread per worker (set before the children import numpy)
+    keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+    saved = {k: os.environ.get(k) for k in keys}
+    os.environ.update({k: "1" for k in keys})
+    try:
+        with concurrent.futures.ProcessPoolExecutor(min(len(jobs), os.cpu_count() or 1), mp_context=ctx) as ex:
+            return list(ex.map(_oracle_mps_job, jobs))
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
 
 
 @pytest.mark.slow

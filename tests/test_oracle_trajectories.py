@@ -185,6 +185,27 @@ def test_eps_bound_definition():
     assert capped.eps_bound == want + 1.0
 
 
+def test_cut_gaps_are_the_schmidt_gaps_at_the_cut():
+    """The recorded cut gap of a truncating split is (w_chi' - w_chi'+1) / w_1
+    of the squared Schmidt values of the state being split: for the first
+    gate of a circuit, the dense trajectory (same branches) holds that state,
+    whose Schmidt values across the gated bond are computed here by an
+    independent SVD.  Untruncated runs record no gaps."""
+    c = I.random_brickwork(4, 1, I.depolarizing_kraus(0.3), seed=7)
+    c = I.Circuit(4, [I.Layer(c.layers[0].left_qubits[:1], c.layers[0].gates[:1], c.layers[0].kraus)])
+    q = int(c.layers[0].left_qubits[0])
+    dense = T.dense_trajectory(c, 0, 2)
+    s = np.linalg.svd(dense.state.reshape(2 ** (q + 1), -1), compute_uv=False)
+    w = s ** 2
+    rec = T.mps_trajectory(c, 0, 2, chi_max=1, cutoff=1e-14)
+    assert rec.branch == dense.branch
+    assert len(rec.cut_gaps) == 1
+    assert abs(rec.cut_gaps[0] - (w[0] - w[1]) / w[0]) < 1e-12
+    full = T.mps_trajectory(I.random_brickwork(6, 3, I.depolarizing_kraus(0.05), seed=5), 0, 1, chi_max=8,
+                            cutoff=0.0)
+    assert full.cut_gaps == []
+
+
 def test_coin_noise_matches_density_matrix():
     """Probabilistic noise (coin_p < 1, the two-qubit depolarizing reading):
     the trajectory average still reproduces the exact channel."""
