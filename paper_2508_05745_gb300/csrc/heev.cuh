@@ -22,7 +22,7 @@ namespace lemps {
 
 template <class R>
 struct HeevView {
-  cpx<R>* ws1;      // Gram matrix, then LDL^T scratch of the inverse iteration
+  cpx<R>* ws1;      // Gram matrix, then the inverse-iteration vectors
   cpx<R>* ws2;      // eigenvectors (output)
   cpx<R>* ws3;      // Householder vectors
   int64_t ws_stride;
@@ -37,18 +37,31 @@ struct HeevView {
 };
 
 // Number of eigenvalues of the real symmetric tridiagonal (d, e) that are
-// strictly greater than x (Sturm sequence of T - x I with a pivot guard).
-template <class R>
-__device__ __forceinline__ int sturm_greater(const R* d, const R* e2, int n, R x, R pivmin) {
+// strictly greater than x (Sturm sequence of T - x I with a pivot guard), in
+// FP64 on range-normalized data (|d_i|, e_i^2 of order 1 or less,
+// pivmin >= 1e-30): the quotient e^2 / q is e^2 r, where r is the FP32
+// reciprocal of q refined by two Newton-Raphson steps r <- r + r (1 - q r)
+// (each step doubles the correct bits, 24 -> 48 -> the full 53); the sign
+// test and the pivot guard |q| < pivmin -> q = -pivmin read the bit pattern.
+// On GB300 every FP64 instruction (add, compare, min/max as well as FMA)
+// issues at 1/64 of the FP32 rate, so this count keeps to six of them per
+// step.  Normalized |q| stays within [1e-30, 1e31], inside the FP32 range.
+__device__ __forceinline__ int sturm_greater_f64(const double* d, const double* e2, int n, double x, double pivmin) {
+  const long long pbits = __double_as_longlong(pivmin);
+  const long long nbits = __double_as_longlong(-pivmin);
   int neg = 0;
-  R q = d[0] - x;
-  if (fabs(q) < pivmin) q = -pivmin;
-  neg += (q < 0);
+  auto guard = [&](double v) {
+    long long b = __double_as_longlong(v);
+    if ((b & 0x7fffffffffffffffLL) < pbits) b = nbits;
+    neg += (int)((unsigned long long)b >> 63);
+    return __longlong_as_double(b);
+  };
+  double q = guard(d[0] - x);
   for (int i = 1; i < n; ++i) {
-    // c64: fast reciprocal-based divide (|q| >= pivmin keeps it in range)
-    q = (d[i] - x) - (sizeof(R) == 4 ? (R)__fdividef((float)e2[i - 1], (float)q) : e2[i - 1] / q);
-    if (fabs(q) < pivmin) q = -pivmin;
-    neg += (q < 0);
+    double r = (double)__frcp_rn((float)q);
+    r = fma(r, fma(-q, r, 1.0), r);
+    r = fma(r, fma(-q, r, 1.0), r);
+    q = guard(fma(-e2[i - 1], r, d[i] - x));
   }
   return n - neg;
 }
@@ -82,6 +95,35 @@ __device__ __forceinline__ void load_pair(const cpx<double>* p, cpx<double>& a, 
   b = mk(t1.x, t1.y);
 }
 
+// Complex updates written as chains of fused multiply-adds: on GB300 each FP64
+// instruction (FMA, multiply or add alike) takes one slot of the 1/64-rate FP64
+// pipe, so x - a b as two multiplies and adds per component costs half as
+// much again as the fused form.
+// x - v1 conj(w1) - w2 conj(v2): one entry of a Hermitian rank-2 update.
+template <class R>
+__device__ __forceinline__ cpx<R> rank2_sub(cpx<R> x, cpx<R> v1, cpx<R> w1, cpx<R> w2, cpx<R> v2) {
+  x.re = fma(-v1.re, w1.re, fma(-v1.im, w1.im, fma(-w2.re, v2.re, fma(-w2.im, v2.im, x.re))));
+  x.im = fma(-v1.im, w1.re, fma(v1.re, w1.im, fma(-w2.im, v2.re, fma(w2.re, v2.im, x.im))));
+  return x;
+}
+// acc -= a b
+template <class R>
+__device__ __forceinline__ void cfms(cpx<R>& acc, cpx<R> a, cpx<R> b) {
+  acc.re = fma(-a.re, b.re, fma(a.im, b.im, acc.re));
+  acc.im = fma(-a.re, b.im, fma(-a.im, b.re, acc.im));
+}
+// Sum over the block, returned to every thread: a warp butterfly, then each
+// warp sums the per-warp totals by a second butterfly (cheaper on the FP64
+// pipe than every thread adding them up).  `scratch` holds 32 values.
+__device__ __forceinline__ double block_sum_f64(double v, double* scratch) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  __syncthreads();
+  if (lane == 0) scratch[w] = v;
+  __syncthreads();
+  return warp_sum(lane < nw ? scratch[lane] : 0.0);
+}
+
 // y_c <- (I - 2 v v^dagger) y_c for a warp's NCOL columns (PER entries per
 // lane, row lane + 32 a).  Groups a < A0 are zero in v and are skipped at
 // compile time; the NCOL complex dots are summed over the warp by one
@@ -110,7 +152,7 @@ __device__ __forceinline__ void bt_reflector(cpx<R> (&y)[NCOL][PER], const cpx<R
 #pragma unroll
   for (int a = A0; a < PER; ++a)
 #pragma unroll
-    for (int c = 0; c < NCOL; ++c) y[c][a] -= vr[a] * mk<R>(dd[2 * c], dd[2 * c + 1]);
+    for (int c = 0; c < NCOL; ++c) cfms(y[c][a], vr[a], mk<R>(dd[2 * c], dd[2 * c + 1]));
 }
 
 // mode / q select the matrix size as in gram_size(); want_vectors = 0 returns
@@ -137,11 +179,12 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
   __shared__ double redd[32];
   __shared__ int s_keep;
   __shared__ double s_tr;
+  __shared__ cpx<R> s_hh[3];                 // Householder scalars of a step
 
   // trace (FP64) for the cutoff and the discarded weight
   double trp = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) trp += (double)G[(int64_t)i * n + i].re;
-  trp = block_sum(trp, redd);
+  trp = block_sum_f64(trp, redd);
   if (threadIdx.x == 0) s_tr = trp;
 
   // ---- phase 1: tridiagonalization ------------------------------------------
@@ -168,27 +211,46 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
       const int gi = j + 1 + i;
       cpx<R> x = G[(int64_t)gi * n + j];
       for (int k = 0; k < j; ++k)
-        x -= Vp[(int64_t)k * n + gi] * conj(Wp[(int64_t)k * n + j]) + Wp[(int64_t)k * n + gi] * conj(Vp[(int64_t)k * n + j]);
+        x = rank2_sub(x, Vp[(int64_t)k * n + gi], Wp[(int64_t)k * n + j], Wp[(int64_t)k * n + gi], Vp[(int64_t)k * n + j]);
       sv[i] = x;
-      if (i > 0) part += norm2(x);
+      if (i > 0) part = fma(x.re, x.re, fma(x.im, x.im, part));
     }
     if (threadIdx.x == 0) {
       R dj = G[(int64_t)j * n + j].re;
       for (int k = 0; k < j; ++k) dj -= (R)2 * cdot(Wp[(int64_t)k * n + j], Vp[(int64_t)k * n + j]).re;
       sd[j] = dj;
     }
-    R sig = block_sum(part, red);
-    cpx<R> x0 = sv[0];
-    R ax0 = sqrt(norm2(x0));
-    R nrm = sqrt(sig + ax0 * ax0);
-    const bool reflect = sig > (R)0;
-    cpx<R> alpha = x0;
+    part = warp_sum(part);
+    if (lane == 0) red[warp] = part;
+    __syncthreads();
+    // the Householder scalars of the step, by one warp (FP64 instructions
+    // cost the pipe the same with one lane or 32 active)
+    if (warp == 0) {
+      const R sig = warp_sum(lane < nwarp ? red[lane] : (R)0);
+      if (lane == 0) {
+        const cpx<R> x0 = sv[0];
+        const R ax0 = sqrt(norm2(x0));
+        const R nrm = sqrt(sig + ax0 * ax0);
+        cpx<R> alpha = x0, v0 = mk<R>(0, 0);
+        R inv = 0;
+        if (sig > (R)0) {
+          const cpx<R> ph = (ax0 > 0) ? mk<R>(x0.re / ax0, x0.im / ax0) : mk<R>(1, 0);
+          alpha = mk<R>(-nrm * ph.re, -nrm * ph.im);
+          inv = (R)1 / sqrt(sig + (ax0 + nrm) * (ax0 + nrm));
+          v0 = (x0 - alpha) * inv;
+        }
+        s_hh[0] = alpha;
+        s_hh[1] = v0;
+        s_hh[2] = mk<R>(inv, sig > (R)0 ? (R)1 : (R)0);
+      }
+    }
+    __syncthreads();
+    const cpx<R> alpha = s_hh[0];
+    const bool reflect = s_hh[2].im != (R)0;
     if (reflect) {
-      cpx<R> ph = (ax0 > 0) ? mk<R>(x0.re / ax0, x0.im / ax0) : mk<R>(1, 0);
-      alpha = mk<R>(-nrm * ph.re, -nrm * ph.im);
-      R inv = (R)1 / sqrt(sig + (ax0 + nrm) * (ax0 + nrm));
-      __syncthreads();
-      for (int i = threadIdx.x; i < m; i += blockDim.x) sv[i] = (i == 0) ? (x0 - alpha) * inv : sv[i] * inv;
+      const cpx<R> v0 = s_hh[1];
+      const R inv = s_hh[2].re;
+      for (int i = threadIdx.x; i < m; i += blockDim.x) sv[i] = (i == 0) ? v0 : sv[i] * inv;
     }
     __syncthreads();
     if (threadIdx.x == 0) sec[j] = alpha;
@@ -264,11 +326,14 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
     for (int i = threadIdx.x; i < m; i += blockDim.x) {
       const int gi = j + 1 + i;
       cpx<R> y = sw[i];
-      for (int k = 0; k < j; ++k) y -= Vp[(int64_t)k * n + gi] * cc[k] + Wp[(int64_t)k * n + gi] * cc[j + k];
+      for (int k = 0; k < j; ++k) {
+        cfms(y, Vp[(int64_t)k * n + gi], cc[k]);
+        cfms(y, Wp[(int64_t)k * n + gi], cc[j + k]);
+      }
       sw[i] = y;
-      sp += cdot(sv[i], y).re;
+      sp = fma(sv[i].re, y.re, fma(sv[i].im, y.im, sp));
     }
-    R ss = block_sum(sp, red);
+    R ss = block_sum_f64(sp, red);
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
       const cpx<R> wi = (i > j) ? (R)2 * sw[i - j - 1] - ((R)2 * ss) * sv[i - j - 1] : mk<R>(0, 0);
       Wp[(int64_t)j * n + i] = wi;
@@ -378,24 +443,36 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
     if (i < m) {
       const int Rr = jl + 1 + i;
       wi = wprev(Rr);
-      x = Lp[pidx(Rr, jl)] - vP[Rr] * conj(wPj) - wi * conj(vPj);
-      if (i > 0) part = norm2(x);
+      x = rank2_sub(Lp[pidx(Rr, jl)], vP[Rr], wPj, wi, vPj);
+      if (i > 0) part = fma(x.re, x.re, fma(x.im, x.im, part));
     }
-    const cpx<R> x0 = Lp[pidx(jl + 1, jl)] - vP[jl + 1] * conj(wPj) - wprev(jl + 1) * conj(vPj);
     part = warp_sum(part);
     if (lane == 0) redn[warp] = part;
     __syncthreads();
-    R sig = 0;
-    for (int w2 = 0; w2 < nwarp; ++w2) sig += redn[w2];
-    const R ax0 = sqrt(norm2(x0));
-    const R nrm = sqrt(sig + ax0 * ax0);
-    cpx<R> alpha = x0, vi = mk<R>(0, 0);
-    if (sig > (R)0) {
-      cpx<R> ph = (ax0 > 0) ? mk<R>(x0.re / ax0, x0.im / ax0) : mk<R>(1, 0);
-      alpha = mk<R>(-nrm * ph.re, -nrm * ph.im);
-      const R inv = (R)1 / sqrt(sig + (ax0 + nrm) * (ax0 + nrm));
-      vi = (i == 0) ? (x0 - alpha) * inv : x * inv;
+    // the step's Householder scalars by one warp (an FP64 instruction costs
+    // the pipe the same with one lane active as with 32)
+    if (warp == 0) {
+      const R sig = warp_sum(lane < nwarp ? redn[lane] : (R)0);
+      if (lane == 0) {
+        const cpx<R> x0 = rank2_sub(Lp[pidx(jl + 1, jl)], vP[jl + 1], wPj, wprev(jl + 1), vPj);
+        const R ax0 = sqrt(norm2(x0));
+        const R nrm = sqrt(sig + ax0 * ax0);
+        cpx<R> alpha = x0, v0 = mk<R>(0, 0);
+        R inv = 0;
+        if (sig > (R)0) {
+          const cpx<R> ph = (ax0 > 0) ? mk<R>(x0.re / ax0, x0.im / ax0) : mk<R>(1, 0);
+          alpha = mk<R>(-nrm * ph.re, -nrm * ph.im);
+          inv = (R)1 / sqrt(sig + (ax0 + nrm) * (ax0 + nrm));
+          v0 = (x0 - alpha) * inv;
+        }
+        s_hh[1] = v0;
+        s_hh[2] = mk<R>(inv, 0);
+        sd[j] = Lp[pidx(jl, jl)].re - (R)2 * cdot(wPj, vPj).re;
+        sec[j] = alpha;
+      }
     }
+    __syncthreads();
+    const cpx<R> vi = (i == 0) ? s_hh[1] : x * s_hh[2].re;   // zero when sig = 0 (inv = 0, v0 = 0)
     // every thread has read y of the previous step: it now becomes w
     cpx<R>* wP = const_cast<cpx<R>*>(yP);
     if (i < m) {
@@ -405,10 +482,6 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
       Hv[(int64_t)j * n + (j + 1 + i)] = vi;
     }
     if (i <= j) Hv[(int64_t)j * n + i] = mk<R>(0, 0);
-    if (threadIdx.x == 0) {
-      sd[j] = Lp[pidx(jl, jl)].re - (R)2 * cdot(wPj, vPj).re;
-      sec[j] = alpha;
-    }
     __syncthreads();
     // One pass over 32 x QW slices of the trailing triangle's 32 x 32 tiles
     // (aligned to multiples of 32 in local index), lane = row r.  It applies
@@ -451,7 +524,7 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
         if (C > jl && C < M0) {
           const cpx<R> cv = vP[C], cw = wP[C], cn = vN[C];
           if (rin && C <= Rr) {
-            const cpx<R> aa = rowp[C] - vr * conj(cw) - wr * conj(cv);
+            const cpx<R> aa = rank2_sub(rowp[C], vr, cw, wr, cv);
             rowp[C] = aa;
             cfma(acc, aa, cn);
             any = true;
@@ -464,7 +537,7 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
       if (any) {
         atomicAdd(&yN[Rr].re, acc.re);
         atomicAdd(&yN[Rr].im, acc.im);
-        ssp += cdot(nr, acc).re;
+        ssp = fma(nr.re, acc.re, fma(nr.im, acc.im, ssp));
       }
       const R tot = warp_reduce_scatter<NVQ>(d, lane);
       const int e = Scatter<NVQ>::index(lane);   // value 2 c + {re, im} of column cb + c
@@ -472,19 +545,17 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
       if ((lane & ((1 << (5 - LGQ)) - 1)) == 0 && Cc > jl && Cc < M0) {
         if (e & 1) {
           atomicAdd(&yN[Cc].im, tot);
-          ssp += vN[Cc].im * tot;
+          ssp = fma(vN[Cc].im, tot, ssp);
         } else {
           atomicAdd(&yN[Cc].re, tot);
-          ssp += vN[Cc].re * tot;
+          ssp = fma(vN[Cc].re, tot, ssp);
         }
       }
     }
     ssp = warp_sum(ssp);
     if (lane == 0) reds[warp] = ssp;
     __syncthreads();
-    R ss = 0;
-    for (int w2 = 0; w2 < nwarp; ++w2) ss += reds[w2];
-    ssP = ss;
+    ssP = warp_sum(lane < nwarp ? reds[lane] : (R)0);
     pb = qb;
   }
   if (threadIdx.x == 0) {
@@ -521,19 +592,52 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
   __syncthreads();
 
   // ---- phase 2: how many to keep, and the kept eigenvalues by bisection ------
-  R gl = sd[0], gu = sd[0], tnorm = 0;
-  for (int i = 0; i < n; ++i) {
-    R rad = (i > 0 ? se[i - 1] : (R)0) + (i + 1 < n ? se[i] : (R)0);
-    gl = fmin(gl, sd[i] - rad);
-    gu = fmax(gu, sd[i] + rad);
-    tnorm = fmax(tnorm, fabs(sd[i]) + rad);
+  // Gerschgorin bounds and the norm of T by a block reduction (every FP64
+  // instruction counts on this pipe), then T scaled by 1 / tnorm into shared
+  // memory (free once the packed triangle is done): the Sturm counts run on
+  // data of order one.
+  __shared__ double s_gl, s_gu, s_tn;
+  {
+    double lo = 1e300, hi = -1e300, tn = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const double rad = (i > 0 ? (double)se[i - 1] : 0.0) + (i + 1 < n ? (double)se[i] : 0.0);
+      lo = fmin(lo, (double)sd[i] - rad);
+      hi = fmax(hi, (double)sd[i] + rad);
+      tn = fmax(tn, fabs((double)sd[i]) + rad);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+      hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+      tn = fmax(tn, __shfl_xor_sync(0xffffffffu, tn, o));
+    }
+    double* rb = reinterpret_cast<double*>(heev_smem);
+    if (lane == 0) { rb[warp] = lo; rb[32 + warp] = hi; rb[64 + warp] = tn; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int w2 = 1; w2 < nwarp; ++w2) {
+        lo = fmin(lo, rb[w2]);
+        hi = fmax(hi, rb[32 + w2]);
+        tn = fmax(tn, rb[64 + w2]);
+      }
+      s_gl = lo; s_gu = hi; s_tn = (tn > 0.0) ? tn : 1.0;
+    }
+    __syncthreads();
   }
-  const R eps = (sizeof(R) == 8) ? (R)2.2e-16 : (R)1.2e-7;
-  const R pivmin = fmax((R)1e-30 * tnorm, (sizeof(R) == 8) ? (R)1e-290 : (R)1e-35);
-  gl -= 2 * eps * tnorm + pivmin;
-  gu += 2 * eps * tnorm + pivmin;
+  const double tnorm = s_tn, itn = 1.0 / tnorm;
+  const double eps = 2.2e-16;
+  const double pivmin = 1e-30;                     // normalized units
+  const double pivmin_abs = pivmin * tnorm;
+  const double gl = s_gl * itn - (2 * eps + pivmin), gu = s_gu * itn + (2 * eps + pivmin);
+  double* tdn = reinterpret_cast<double*>(heev_smem) + 3 * blockDim.x;   // after the grid arrays
+  double* te2n = tdn + 256;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    tdn[i] = (double)sd[i] * itn;
+    te2n[i] = (double)se2[i] * (itn * itn);
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
-    int cnt = (cutoff > 0.0) ? sturm_greater<R>(sd, se2, n, (R)(cutoff * s_tr), pivmin) : n;
+    int cnt = (cutoff > 0.0) ? sturm_greater_f64(tdn, te2n, n, cutoff * s_tr * itn, pivmin) : n;
     // a two-site Gram matrix has rank <= min(2 d_l, 2 d_r)
     const int rank_bound = (mode == 2) ? n : min(2 * bd[q], 2 * bd[q + 2]);
     int kp = min(cnt, min(keep_max, min(n, rank_bound)));
@@ -543,36 +647,42 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
   const int keep = s_keep;
   double* ev = s.evals + t * (2 * s.chi);
   // Brackets: one Sturm count per thread on an increasing grid of blockDim.x
-  // points (the packed triangle's shared memory is free by now).  When a
-  // cutoff is set, every kept eigenvalue lies above x_lo = cutoff * trace and
-  // the grid is geometric from x_lo to gu (neighbouring points about 5 %
-  // apart), so each eigenvalue starts from a narrow relative interval instead
-  // of [gl, gu]; else it is uniform on [gl, gu].  Any increasing grid is
-  // valid, so it is formed in single precision.
-  R* gx = reinterpret_cast<R*>(heev_smem);
+  // points.  When a cutoff is set, every kept eigenvalue lies above x_lo =
+  // cutoff * trace and the grid is geometric from x_lo to gu (neighbouring
+  // points about 5 % apart), so each eigenvalue starts from a narrow relative
+  // interval instead of [gl, gu]; else it is uniform on [gl, gu].  Any
+  // increasing grid is valid, so it is formed in single precision.
+  double* gx = reinterpret_cast<double*>(heev_smem);
   int* gcnt = reinterpret_cast<int*>(gx + blockDim.x);
+  __syncthreads();   // the reduction scratch above overlaps gx
   {
     const int ng = blockDim.x;
-    const float xlo = (float)(cutoff * s_tr), xhi = (float)gu;
+    const float xlo = (float)(cutoff * s_tr * itn), xhi = (float)gu;
     const bool geo = cutoff > 0.0 && xlo > 0.0f && xlo < xhi;
     const float f = (float)threadIdx.x / (float)(ng - 1);
-    const R x = geo ? (R)(xlo * exp2f(log2f(xhi / xlo) * f)) : gl + (gu - gl) * (R)(threadIdx.x + 1) / (R)(ng + 1);
+    const double x = geo ? (double)(xlo * exp2f(log2f(xhi / xlo) * f))
+                         : gl + (gu - gl) * (double)(threadIdx.x + 1) / (double)(ng + 1);
     gx[threadIdx.x] = x;
-    gcnt[threadIdx.x] = sturm_greater<R>(sd, se2, n, x, pivmin);
+    gcnt[threadIdx.x] = sturm_greater_f64(tdn, te2n, n, x, pivmin);
   }
   __syncthreads();
   {
     // Multisection: G lanes of a warp share eigenvalue k and evaluate the
     // Sturm count at G interior points of its interval, which shrinks by
     // G + 1 per round (G = 4 when 128 eigenvalues are kept on 512 threads).
+    // An interval stops at 4 eps ||T|| (normalized: 4 eps): the eigenvalues
+    // of the tridiagonal matrix are then as accurate as its backward-stable
+    // reduction from G allows (a few eps ||G|| absolute), which is all that
+    // the shifts of the inverse iteration and the entropies need.
     int G = 1;
     while (G < 32 && keep * (2 * G) <= (int)blockDim.x) G *= 2;
     const int per_warp = 32 / G;
     const int gi = lane & (G - 1);
     const unsigned gmask = (G == 32) ? 0xffffffffu : ((1u << G) - 1u);
+    const double tol = 4.0 * eps + pivmin;
     for (int kb = 0; kb < keep; kb += nwarp * per_warp) {
       const int k = kb + warp * per_warp + lane / G;
-      R lo = gl, hi = gu;
+      double lo = gl, hi = gu;
       if (k < keep) {
         // grid counts do not increase along the grid: a = last point below
         // eigenvalue k (count > k), b = a + 1 the first at or above it
@@ -587,23 +697,21 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
       }
       bool done = k >= keep;
       for (int it = 0; it < 200; ++it) {
-        const R h = (hi - lo) / (R)(G + 1);
-        if (hi - lo <= eps * (fabs(lo) + fabs(hi)) + (R)1e-3 * eps * tnorm + pivmin || !(lo + h > lo) ||
-            !(hi - h < hi))
-          done = true;
+        const double h = (hi - lo) / (double)(G + 1);
+        if (hi - lo <= tol || !(lo + h > lo) || !(hi - h < hi)) done = true;
         if (__all_sync(0xffffffffu, done)) break;
-        const R x = lo + h * (R)(gi + 1);
-        const bool above = !done && sturm_greater<R>(sd, se2, n, x, pivmin) > k;
+        const double x = lo + h * (double)(gi + 1);
+        const bool above = !done && sturm_greater_f64(tdn, te2n, n, x, pivmin) > k;
         const unsigned grp = (__ballot_sync(0xffffffffu, above) >> (lane & ~(G - 1))) & gmask;
         const int pcount = __popc(grp);   // interior points below eigenvalue k
         if (!done) {
-          const R nlo = (pcount > 0) ? lo + h * (R)pcount : lo;
-          const R nhi = (pcount < G) ? lo + h * (R)(pcount + 1) : hi;
+          const double nlo = (pcount > 0) ? lo + h * (double)pcount : lo;
+          const double nhi = (pcount < G) ? lo + h * (double)(pcount + 1) : hi;
           lo = nlo;
           hi = nhi;
         }
       }
-      if (k < keep && gi == 0) ev[k] = (double)((R)0.5 * (lo + hi));
+      if (k < keep && gi == 0) ev[k] = 0.5 * (lo + hi) * tnorm;
     }
   }
   if (threadIdx.x == 0) {
@@ -615,23 +723,26 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
 
   // ---- phase 3: inverse iteration (LDL^T of T - l I, two solves) ------------
   // Each thread owns one kept eigenvalue.  The LDL^T factors and the iterate
-  // live in shared memory (the packed triangle is no longer needed) when a
-  // chunk of vectors fits, else in the global scratch (ws1): per vector k the
-  // arrays dd[i], ll[i], z[i] at ((i * 3 + a) * kc + k).  Results go to the
-  // global scratch z[i][k] = scr[(i * 3 + 2) * keep + k].
-  R* scr = reinterpret_cast<R*>(G);
+  // of a chunk of vectors live in shared memory (the packed triangle is no
+  // longer needed): per vector k the arrays dd[i], ll[i], z[i] at
+  // ((i * 3 + a) * kc + k); a chunk holds at least 32 vectors for n <= 256.
+  // Results go to the global scratch (the Gram matrix is no longer needed)
+  // as Zg[k n + i], one contiguous vector per eigenvalue.
+  R* Zg = reinterpret_cast<R*>(G);
   {
     const int chunk_cap = HeevSmem<R>::kBytes / (3 * n * (int)sizeof(R));
-    const bool in_smem = chunk_cap >= 32;
-    const int kc_max = in_smem ? min(chunk_cap, (int)blockDim.x) : keep;
-    R* wsp = in_smem ? reinterpret_cast<R*>(heev_smem) : scr;
+    if (chunk_cap < 32) {   // cannot happen for n <= 256
+      if (threadIdx.x == 0) atomicOr(s.status + t, (int32_t)TS_SHAPE);
+      return;
+    }
+    const int kc_max = min(chunk_cap, (int)blockDim.x);
+    R* wsp = reinterpret_cast<R*>(heev_smem);
     for (int k0 = 0; k0 < keep; k0 += kc_max) {
       const int kc = min(kc_max, keep - k0);
-      const int ld = in_smem ? kc : keep;      // row stride of the work arrays
-      const int koff = in_smem ? 0 : k0;
+      const int ld = kc;      // row stride of the work arrays
       for (int kk = threadIdx.x; kk < kc; kk += blockDim.x) {
         const int k = k0 + kk;
-        R* w3 = wsp + koff + kk;
+        R* w3 = wsp + kk;
         const R lam = (R)ev[k];
         // w3[i][0] holds 1 / d_i (the solves multiply), w3[i][1] l_i, w3[i][2]
         // the iterate.  Stores to w3 would keep the compiler from hoisting the
@@ -645,14 +756,14 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
         auto Lw = [&](int i) -> R& { return w3[(i * 3 + 1) * ld]; };
         auto Zw = [&](int i) -> R& { return w3[(i * 3 + 2) * ld]; };
         R dprev = sd[0] - lam;
-        if (fabs(dprev) < pivmin) dprev = pivmin;
+        if (fabs(dprev) < pivmin_abs) dprev = pivmin_abs;
         R rprev = recip(dprev);
         Dr(0) = rprev;
         {
           auto step = [&](R si, R di) {   // returns l_i, advances rprev to 1 / d_{i+1}
             const R li = si * rprev;
             R dn = di - li * si;
-            if (fabs(dn) < pivmin) dn = pivmin;
+            if (fabs(dn) < pivmin_abs) dn = pivmin_abs;
             rprev = recip(dn);
             return li;
           };
@@ -724,162 +835,118 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
           }
           sc = (amax > 0) ? (R)1 / amax : (R)1;
         }
-        if (in_smem) {
-          for (int i = 0; i < n; ++i) scr[(i * 3 + 2) * keep + k] = sc * Zw(i);
-        } else {
-          for (int i = 0; i < n; ++i) Zw(i) *= sc;
-        }
+        Dr(0) = sc;   // the factors are done with: slot 0 keeps the final scale
+      }
+      __syncthreads();
+      // copy-out with the scale, coalesced along each vector
+      for (int kk = warp; kk < kc; kk += nwarp) {
+        const R* w3 = wsp + kk;
+        const R sc = w3[0];
+        for (int i = lane; i < n; i += 32) Zg[(size_t)(k0 + kk) * n + i] = sc * w3[(i * 3 + 2) * ld];
       }
       __syncthreads();
     }
   }
   // ---- phase 4: Gram-Schmidt in descending eigenvalue order -----------------
-  // When the vectors fit in shared memory (Z[k * ldz + i], rows padded so
-  // that 16-byte loads of consecutive rows hit distinct banks) they are
-  // orthonormalized in blocks of 16 (block classical Gram-Schmidt): project
-  // the block against all earlier vectors, then orthonormalize it by
-  // Cholesky QR of its 16 x 16 Gram matrix.  A second pass follows only when
-  // the first may have left an orthogonality error above a few ulps (the
-  // Daniel-Gragg-Kaufman-Stewart criterion): the projection removed more than
-  // half of some vector's squared norm, or a Cholesky pivot fell below half
-  // of its diagonal entry (an ill-conditioned block).  Inverse-iteration
-  // vectors of well-separated eigenvalues pass with one.  A block whose
-  // pivots show near-dependence (pivot < tol * squared norm) is redone by
-  // per-vector classical Gram-Schmidt (twice).  When the vectors do not fit,
-  // they stay in the global scratch and the per-vector scheme runs for all.
-  constexpr int NB = 16;
-  constexpr int E = 16 / (int)sizeof(R);             // elements per 16-byte load
-  constexpr int ROWQ = 128 / (int)sizeof(R);         // elements per 128 bytes
-  const int ldz = ((n + ROWQ - 1) / ROWQ) * ROWQ + E;
-  const size_t zs_bytes = (size_t)keep * ldz * sizeof(R);
-  const size_t cb_bytes = (size_t)128 * NB * sizeof(R);
-  const bool zsm = keep <= 128 && zs_bytes + cb_bytes + 8 * (size_t)n * sizeof(cpx<R>) <= (size_t)HeevSmem<R>::kBytes;
-  R* Zs = reinterpret_cast<R*>(heev_smem);
-  if (zsm)
-    for (int e = threadIdx.x; e < keep * ldz; e += blockDim.x) {
-      const int k = e / ldz, i = e - k * ldz;
-      Zs[e] = (i < n) ? scr[(i * 3 + 2) * keep + k] : (R)0;
-    }
-  __syncthreads();
-  auto Z = [&](int k, int i) -> R& { return zsm ? Zs[k * ldz + i] : scr[(i * 3 + 2) * keep + k]; };
-  R* cbuf = reinterpret_cast<R*>(sw);
-  // per-vector CGS2 + normalization of vectors k in [k_from, k_to), against
-  // all vectors in [p_from, k)
-  auto cgs_vectors = [&](int p_from, int k_from, int k_to) {
-    for (int k = k_from; k < k_to; ++k) {
-      for (int pass = 0; pass < 2; ++pass) {
-        for (int jj = p_from + warp; jj < k; jj += nwarp) {
-          R acc = 0;
-          for (int i = lane; i < n; i += 32) acc += Z(jj, i) * Z(k, i);
-          acc = warp_sum(acc);
-          if (lane == 0) cbuf[jj - p_from] = acc;
-        }
-        __syncthreads();
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
-          R v = Z(k, i);
-          for (int jj = p_from; jj < k; ++jj) v -= cbuf[jj - p_from] * Z(jj, i);
-          Z(k, i) = v;
-        }
-        __syncthreads();
-      }
-      R part = 0;
-      for (int i = threadIdx.x; i < n; i += blockDim.x) part += Z(k, i) * Z(k, i);
-      R nn = block_sum(part, red);
-      R inv = nn > 0 ? (R)1 / sqrt(nn) : (R)0;
-      for (int i = threadIdx.x; i < n; i += blockDim.x) Z(k, i) *= inv;
-      __syncthreads();
-    }
-  };
-  if (!zsm) {
-    cgs_vectors(0, 0, keep);
-  } else {
-    using V16 = typename std::conditional<sizeof(R) == 4, float4, double2>::type;
-    R* cb = Zs + (size_t)keep * ldz;                   // [128][NB] projection coefficients
-    R* gq = reinterpret_cast<R*>(sv);                  // [NB][NB] block Gram matrix
-    R* lq = gq + NB * NB;                              // [NB][NB] its Cholesky factor
+  // Blocks of NB = 16 vectors are orthonormalized in turn (block classical
+  // Gram-Schmidt).  The block is staged in shared memory; the earlier vectors
+  // stay in Zg (L2-resident, 256 KB per trajectory at n = 256, keep = 128).
+  // Projection: the coefficients <z_a, z_b> by one warp per earlier vector a
+  // (lanes along i, 16 sums per lane, one reduce-scatter butterfly), then
+  // z_b -= sum_a c_ab z_a with the z_a streamed from L2, coalesced.  Then
+  // Cholesky QR of the block's 16 x 16 Gram matrix.  A second pass follows
+  // only where the first may have left more than a few ulps of
+  // non-orthogonality (Daniel-Gragg-Kaufman-Stewart: the projection removed
+  // more than half of some vector's squared norm, or a Cholesky pivot fell
+  // below half of its diagonal entry); inverse-iteration vectors of
+  // well-separated eigenvalues pass with one.  A block whose pivots show
+  // near-dependence (pivot < 1e-8 of the squared norm) is redone vector by
+  // vector, each projected twice against everything before it.
+  {
+    constexpr int NB = 16;
+    const int ldb = n + 2;                       // row stride of the staged block
+    R* Zb = reinterpret_cast<R*>(heev_smem);     // [NB][ldb]
+    R* cb = Zb + NB * ldb;                       // [128][NB] projection coefficients
+    R* gq = cb + 128 * NB;                       // [NB][NB] block Gram matrix
+    R* lq = gq + NB * NB;                        // [NB][NB] its Cholesky factor
     __shared__ int s_fail, s_redo;
-    __shared__ R s_n0[NB];   // squared norms of the block before its projection
-    const int nvec = (n + E - 1) / E;
-    const R tol = (sizeof(R) == 8) ? (R)1e-8 : (R)1e-3;
+    __shared__ R s_n0[NB];                       // squared norms before the projection
+    const R tol = (R)1e-8;
+    const int nper = (n + 31) >> 5;
+    // c[a][b] = <z_a, Zb_b> for a in [a0, a1): warp per a
+    auto coeffs = [&](int a0, int a1, int nbk) {
+      for (int a = a0 + warp; a < a1; a += nwarp) {
+        R za[8];
+#pragma unroll
+        for (int t2 = 0; t2 < 8; ++t2) {
+          const int i = lane + 32 * t2;
+          za[t2] = (t2 < nper && i < n) ? Zg[(size_t)a * n + i] : (R)0;
+        }
+        R d[NB];
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+          R acc = 0;
+#pragma unroll
+          for (int t2 = 0; t2 < 8; ++t2) {
+            const int i = lane + 32 * t2;
+            if (t2 < nper && i < n && b < nbk) acc = fma(za[t2], Zb[b * ldb + i], acc);
+          }
+          d[b] = acc;
+        }
+        const R tot = warp_reduce_scatter<NB>(d, lane);
+        if ((lane & 1) == 0) cb[(a - a0) * NB + Scatter<NB>::index(lane)] = tot;
+      }
+    };
+    // Zb_b -= sum_{a in [a0, a1)} c[a][b] z_a: thread (row i, half h of the block)
+    auto subtract = [&](int a0, int a1, int nbk) {
+      const int i = threadIdx.x & 255, h = threadIdx.x >> 8;
+      if (i < n && h < 2) {
+        R y[NB / 2];
+#pragma unroll
+        for (int q2 = 0; q2 < NB / 2; ++q2) y[q2] = (h * NB / 2 + q2 < nbk) ? Zb[(h * NB / 2 + q2) * ldb + i] : (R)0;
+#pragma unroll 2
+        for (int a = a0; a < a1; ++a) {
+          const R za = Zg[(size_t)a * n + i];
+          const R* c = cb + (a - a0) * NB + h * NB / 2;
+#pragma unroll
+          for (int q2 = 0; q2 < NB / 2; ++q2) y[q2] = fma(-c[q2], za, y[q2]);
+        }
+#pragma unroll
+        for (int q2 = 0; q2 < NB / 2; ++q2)
+          if (h * NB / 2 + q2 < nbk) Zb[(h * NB / 2 + q2) * ldb + i] = y[q2];
+      }
+    };
     for (int kb = 0; kb < keep; kb += NB) {
       const int nbk = min(NB, keep - kb);
+      for (int e = threadIdx.x; e < NB * n; e += blockDim.x) {
+        const int b = e / n, i = e - b * n;
+        Zb[b * ldb + i] = (b < nbk) ? Zg[(size_t)(kb + b) * n + i] : (R)0;
+      }
+      __syncthreads();
       for (int rep = 0; rep < 2; ++rep) {
-        if (rep == 0 && kb > 0 && warp < nbk) {   // read after the Gram barrier below
-          R acc = 0;
-          for (int i = lane; i < n; i += 32) acc = fma(Zs[(size_t)(kb + warp) * ldz + i], Zs[(size_t)(kb + warp) * ldz + i], acc);
-          acc = warp_sum(acc);
-          if (lane == 0) s_n0[warp] = acc;
-        }
         if (kb > 0) {
-          // cb[a][b] = <z_a, z_{kb+b}>, a < kb: thread (a, 4 consecutive b)
-          {
-            const int b0 = (threadIdx.x >> 7) * 4;
-            for (int aa = threadIdx.x & 127; aa < kb; aa += 128) {
-              R acc[4] = {0, 0, 0, 0};
-              const V16* za = reinterpret_cast<const V16*>(Zs + (size_t)aa * ldz);
-              const V16* zb[4];
-#pragma unroll
-              for (int c = 0; c < 4; ++c)
-                zb[c] = reinterpret_cast<const V16*>(Zs + (size_t)min(kb + b0 + c, keep - 1) * ldz);
-              for (int v = 0; v < nvec; ++v) {
-                const V16 x = za[v];
-                const R* xr = reinterpret_cast<const R*>(&x);
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                  const V16 y = zb[c][v];
-                  const R* yr = reinterpret_cast<const R*>(&y);
-#pragma unroll
-                  for (int e = 0; e < E; ++e) acc[c] = fma(xr[e], yr[e], acc[c]);
-                }
-              }
-#pragma unroll
-              for (int c = 0; c < 4; ++c)
-                if (b0 + c < nbk) cb[aa * NB + b0 + c] = acc[c];
-            }
+          if (rep == 0 && warp < nbk) {
+            R acc = 0;
+            for (int i = lane; i < n; i += 32) acc = fma(Zb[warp * ldb + i], Zb[warp * ldb + i], acc);
+            acc = warp_sum(acc);
+            if (lane == 0) s_n0[warp] = acc;
           }
-          __syncthreads();
-          // z_{kb+b} -= sum_a cb[a][b] z_a: thread (16-byte column slice, 2 b)
-          {
-            const int b0 = (threadIdx.x >> 6) * 2;
-            if (b0 < nbk)
-              for (int v = threadIdx.x & 63; v < nvec; v += 64) {
-                V16* y0p = reinterpret_cast<V16*>(Zs + (size_t)(kb + b0) * ldz) + v;
-                V16* y1p = reinterpret_cast<V16*>(Zs + (size_t)(kb + min(b0 + 1, nbk - 1)) * ldz) + v;
-                V16 y0 = *y0p, y1 = *y1p;
-                R* r0 = reinterpret_cast<R*>(&y0);
-                R* r1 = reinterpret_cast<R*>(&y1);
-                for (int aa = 0; aa < kb; ++aa) {
-                  const V16 x = reinterpret_cast<const V16*>(Zs + (size_t)aa * ldz)[v];
-                  const R* xr = reinterpret_cast<const R*>(&x);
-                  const R c0 = cb[aa * NB + b0], c1 = cb[aa * NB + b0 + 1];
-#pragma unroll
-                  for (int e = 0; e < E; ++e) {
-                    r0[e] = fma(-c0, xr[e], r0[e]);
-                    r1[e] = fma(-c1, xr[e], r1[e]);
-                  }
-                }
-                *y0p = y0;
-                if (b0 + 1 < nbk) *y1p = y1;
-              }
+          // earlier vectors in chunks of 128 coefficient rows
+          for (int a0 = 0; a0 < kb; a0 += 128) {
+            const int a1 = min(kb, a0 + 128);
+            coeffs(a0, a1, nbk);
+            __syncthreads();
+            subtract(a0, a1, nbk);
+            __syncthreads();
           }
-          __syncthreads();
         }
         // Gram matrix of the block: thread pair (b, c), halves of the row
         {
           const int ent = threadIdx.x >> 1, h = threadIdx.x & 1;
           const int bb = ent / NB, cc2 = ent % NB;
           R acc = 0;
-          if (bb < nbk && cc2 < nbk) {
-            const V16* zb = reinterpret_cast<const V16*>(Zs + (size_t)(kb + bb) * ldz);
-            const V16* zc = reinterpret_cast<const V16*>(Zs + (size_t)(kb + cc2) * ldz);
-            for (int v = h; v < nvec; v += 2) {
-              const V16 x = zb[v], y = zc[v];
-              const R* xr = reinterpret_cast<const R*>(&x);
-              const R* yr = reinterpret_cast<const R*>(&y);
-#pragma unroll
-              for (int e = 0; e < E; ++e) acc = fma(xr[e], yr[e], acc);
-            }
-          }
+          if (bb < nbk && cc2 < nbk)
+            for (int i = h; i < n; i += 2) acc = fma(Zb[bb * ldb + i], Zb[cc2 * ldb + i], acc);
           acc += __shfl_xor_sync(0xffffffffu, acc, 1);
           if (h == 0 && ent < NB * NB) gq[ent] = acc;
         }
@@ -916,30 +983,61 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
         }
         __syncthreads();
         if (s_fail) {
-          cgs_vectors(kb, kb, kb + nbk);
+          // vector by vector: project twice against all earlier vectors and
+          // the block's earlier members, then normalize
+          R* cv = cb;   // coefficients, [kb + NB]
+          for (int b = 0; b < nbk; ++b) {
+            for (int pass = 0; pass < 2; ++pass) {
+              for (int a = warp; a < kb + b; a += nwarp) {
+                const R* za = (a < kb) ? Zg + (size_t)a * n : Zb + (a - kb) * ldb;
+                R acc = 0;
+                for (int i = lane; i < n; i += 32) acc = fma(za[i], Zb[b * ldb + i], acc);
+                acc = warp_sum(acc);
+                if (lane == 0) cv[a] = acc;
+              }
+              __syncthreads();
+              for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                R v = Zb[b * ldb + i];
+                for (int a = 0; a < kb + b; ++a) v = fma(-cv[a], (a < kb) ? Zg[(size_t)a * n + i] : Zb[(a - kb) * ldb + i], v);
+                Zb[b * ldb + i] = v;
+              }
+              __syncthreads();
+            }
+            R part = 0;
+            for (int i = threadIdx.x; i < n; i += blockDim.x) part = fma(Zb[b * ldb + i], Zb[b * ldb + i], part);
+            const R nn = block_sum(part, red);
+            const R inv = nn > 0 ? (R)1 / sqrt(nn) : (R)0;
+            for (int i = threadIdx.x; i < n; i += blockDim.x) Zb[b * ldb + i] *= inv;
+            __syncthreads();
+          }
         } else {
-          // Z_blk <- L^{-1} Z_blk, one column entry i per thread
+          // Zb <- L^{-1} Zb, one row entry i per thread
           for (int i = threadIdx.x; i < n; i += blockDim.x) {
             R x[NB];
 #pragma unroll
-            for (int b = 0; b < NB; ++b) x[b] = (b < nbk) ? Zs[(size_t)(kb + b) * ldz + i] : (R)0;
+            for (int b = 0; b < NB; ++b) x[b] = (b < nbk) ? Zb[b * ldb + i] : (R)0;
 #pragma unroll
             for (int b = 0; b < NB; ++b) {
               if (b < nbk) {
                 R v = x[b];
 #pragma unroll
-                for (int c = 0; c < b; ++c) v -= lq[b * NB + c] * x[c];
+                for (int c = 0; c < b; ++c) v = fma(-lq[b * NB + c], x[c], v);
                 x[b] = v / lq[b * NB + b];
               }
             }
 #pragma unroll
             for (int b = 0; b < NB; ++b)
-              if (b < nbk) Zs[(size_t)(kb + b) * ldz + i] = x[b];
+              if (b < nbk) Zb[b * ldb + i] = x[b];
           }
           __syncthreads();
         }
         if (rep == 0 && !s_fail && !s_redo) break;   // uniform: set before the barriers above
       }
+      for (int e = threadIdx.x; e < nbk * n; e += blockDim.x) {
+        const int b = e / n, i = e - b * n;
+        Zg[(size_t)(kb + b) * n + i] = Zb[b * ldb + i];
+      }
+      __syncthreads();
     }
   }
   // ---- phase 5: back-transformation U = Q D z --------------------------------
@@ -956,7 +1054,7 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
   constexpr int NCOL = sizeof(R) == 4 ? 4 : 2;
   const int nper = (n + 31) >> 5;
   const int ldv = 32 * nper;
-  const size_t zbytes = zsm ? zs_bytes + cb_bytes : 0;
+  const size_t zbytes = 0;   // the vectors are read from Zg
   const int rc = min(32, (int)((HeevSmem<R>::kBytes - zbytes) / (2 * (size_t)ldv * sizeof(cpx<R>))));
   if (rc < 1) {   // cannot happen for n <= 256 (the z copy leaves >= 8 n entries)
     if (threadIdx.x == 0) atomicOr(s.status + t, (int32_t)TS_SHAPE);
@@ -1005,7 +1103,7 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
 #pragma unroll
       for (int a = 0; a < PER; ++a) {
         const int i = lane + 32 * a;
-        y[c][a] = (i < n && k0 + c < keep) ? sph[i] * Z(k0 + c, i) : mk<R>(0, 0);
+        y[c][a] = (i < n && k0 + c < keep) ? sph[i] * Zg[(size_t)(k0 + c) * n + i] : mk<R>(0, 0);
       }
     for (int c = 0; c < nch; ++c) {
       const int g = pass * nch + c;

@@ -206,6 +206,35 @@ def test_cut_gaps_are_the_schmidt_gaps_at_the_cut():
     assert full.cut_gaps == []
 
 
+def test_complex64_rounding_is_amplified_at_close_cuts(monkeypatch):
+    """The reading behind the mixed-precision tolerance: rounding every split's
+    output to complex64 (the storage of the mixed path, nothing else changed)
+    moves a heavily truncated trajectory (chi = 4, 10 qubits, 10 layers of
+    depolarizing brickwork) by far more than eps_32: the kept subspace turns
+    by up to ~eps_32 / gap at a cut whose relative gap is small."""
+    circ = I.random_brickwork(10, 10, I.depolarizing_kraus(0.05), seed=4)
+    plain = T._split
+
+    def split_c64(m, q, th, cap, cutoff, rec):
+        e = plain(m, q, th.astype(np.complex64).astype(np.complex128), cap, cutoff, rec)
+        m.a[q] = m.a[q].astype(np.complex64).astype(np.complex128)
+        m.a[q + 1] = m.a[q + 1].astype(np.complex64).astype(np.complex128)
+        return e
+
+    out = []
+    for t in (0, 2):
+        ref = T.mps_trajectory(circ, t, 3, chi_max=4, cutoff=1e-14)
+        monkeypatch.setattr(T, "_split", split_c64)
+        r32 = T.mps_trajectory(circ, t, 3, chi_max=4, cutoff=1e-14)
+        monkeypatch.setattr(T, "_split", plain)
+        assert r32.branch == ref.branch
+        err = max(np.abs(r32.z - ref.z).max(), np.abs(r32.zz - ref.zz).max(), abs(r32.s_half - ref.s_half))
+        out.append((min(ref.cut_gaps), err))
+    (g0, e0), (g2, e2) = out
+    assert g0 < 2e-3 and e0 > 5e-6             # ~300 eps_32 at a cut gap of 1.4e-3
+    assert all(e < 1e-6 / g for g, e in out)   # within 1e-6 / gap, the GPU tolerance
+
+
 def test_coin_noise_matches_density_matrix():
     """Probabilistic noise (coin_p < 1, the two-qubit depolarizing reading):
     the trajectory average still reproduces the exact channel."""
