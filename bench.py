@@ -48,9 +48,12 @@ def parse(argv=None):
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="lemps", choices=["lemps", "reference"])
-    ap.add_argument("--traj", type=int, default=2048, help="mixed-precision trajectories in the batch per GPU")
-    ap.add_argument("--fp64-traj", type=int, default=1216,
-                    help="FP64 comparator trajectories (8 per SM: fills the GPU)")
+    ap.add_argument("--per-size", type=int, default=152,
+                    help="trajectories of each system size per GPU (default: one per SM, so that every per-gate "
+                         "launch of a size handle is one full wave of CTAs)")
+    ap.add_argument("--traj", type=int, default=0,
+                    help="if > 0: that many trajectories per GPU with the sizes drawn by the seeded sample instead")
+    ap.add_argument("--fp64-traj", type=int, default=0, help="FP64 comparator trajectories (default: the same batch)")
     ap.add_argument("--fp64-steps", type=int, default=3, help="timed FP64 steps (at most --steps)")
     ap.add_argument("--e2e-steps", type=int, default=5, help="steps of the end-to-end measurement (at most --steps)")
     ap.add_argument("--pre-layers", type=int, default=10, help="untimed layers before warm-up")
@@ -543,14 +546,17 @@ def main():
     from paper_2508_05745_gb300 import build, lemps as L
     build.build()
     w = workload(args)
-    # replicas: rank r takes trajectories [r*B, (r+1)*B) of the global sample
-    per_rank = args.traj
-    labels = w["n_of_traj"][(rank * per_rank) % 16384:][:per_rank]
+    # The batch: --per-size trajectories of each size (a stratified sample of
+    # the seeded size draw), or with --traj the first trajectories of the
+    # draw; replicas: rank r takes a disjoint block of ids (trajectory_offsets)
     want = [int(x) for x in args.sizes.split(",")]
-    if len(want) == 3:
-        sizes = {int(n): int(np.sum(labels == n)) for n in (24, 48, 64)}
+    if args.traj > 0:
+        labels = w["n_of_traj"][(rank * args.traj) % 16384:][:args.traj]
+        sizes = {n: int(np.sum(labels == n)) for n in want} if len(want) == 3 else \
+            {n: args.traj // len(want) for n in want}
     else:
-        sizes = {n: per_rank // len(want) for n in want}
+        sizes = {n: args.per_size for n in want}
+    per_rank = sum(sizes.values())
     log(f"sizes {sizes}")
     offsets = trajectory_offsets(rank, per_rank, sizes)
     barrier = None
@@ -583,7 +589,8 @@ def main():
     fp64_info = None
     if not args.no_fp64 and rank == 0:
         tot = max(1, sum(sizes.values()))
-        bf = {n: max(1, args.fp64_traj * b // tot) for n, b in sizes.items() if b}
+        bf = {n: max(1, args.fp64_traj * b // tot) for n, b in sizes.items() if b} if args.fp64_traj > 0 else \
+            {n: b for n, b in sizes.items() if b}
         k64 = max(1, min(args.fp64_steps, args.steps))
         d = Arm(L, torch, w, bf, "fp64", args, offsets=offsets)
         d.warmup(min(args.warmup, 1))
