@@ -8,8 +8,8 @@
 // cutoff * trace, so eigenvalues that will be discarded are never computed.
 //
 // Layout (buffers 16-byte aligned, n even): G (n x n row-major, Hermitian)
-// in ws1, overwritten.  Householder vectors in ws3 (row j holds v_j, unit
-// norm, entries > j).  Eigenvectors are written column-major to ws2:
+// in ws1, overwritten.  Householder vectors in ws3 (row j holds sqrt(2) v_j,
+// v_j of unit norm, entries > j).  Eigenvectors are written column-major to ws2:
 // U[k * n + i], k < keep.  Eigenvalues (double, descending) to
 // evals[0..keep), keep and the trace to kept[] / trace[].
 #pragma once
@@ -99,6 +99,10 @@ __device__ __forceinline__ int sturm_newton_f64(const double* d, const double* e
   return n - neg;
 }
 
+// The back-transformation stores each unit reflector v as u = sqrt(2) v, so that
+// applying I - 2 v v^dagger = I - u u^dagger needs no scaling of the dots.
+constexpr double kSqrt2 = 1.4142135623730950488;
+
 // Deterministic start vector entries in [0.5, 1.5) (a hash of (k, i)).
 __device__ __forceinline__ float start_entry(int k, int i) {
   uint32_t h = (uint32_t)k * 0x9E3779B1u ^ (uint32_t)(i + 1) * 0x85EBCA77u;
@@ -157,7 +161,8 @@ __device__ __forceinline__ double block_sum_f64(double v, double* scratch) {
   return warp_sum(lane < nw ? scratch[lane] : 0.0);
 }
 
-// y_c <- (I - 2 v v^dagger) y_c for a warp's NCOL columns (PER entries per
+// y_c <- (I - u u^dagger) y_c for a warp's NCOL columns (u = sqrt(2) v is the
+// stored form of the unit reflector v) (PER entries per
 // lane, row lane + 32 a).  Groups a < A0 are zero in v and are skipped at
 // compile time; the NCOL complex dots are summed over the warp by one
 // reduce-scatter / broadcast butterfly.
@@ -181,7 +186,7 @@ __device__ __forceinline__ void bt_reflector(cpx<R> (&y)[NCOL][PER], const cpx<R
   const R tot = warp_reduce_scatter<NV>(d, lane);
   R dd[NV];
 #pragma unroll
-  for (int e = 0; e < NV; ++e) dd[e] = (R)2 * __shfl_sync(0xffffffffu, tot, Scatter<NV>::source(e));
+  for (int e = 0; e < NV; ++e) dd[e] = __shfl_sync(0xffffffffu, tot, Scatter<NV>::source(e));
 #pragma unroll
   for (int a = A0; a < PER; ++a)
 #pragma unroll
@@ -221,36 +226,92 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
   if (threadIdx.x == 0) s_tr = trp;
 
   // ---- phase 1: tridiagonalization ------------------------------------------
-  // Steps whose trailing block does not fit in shared memory form one panel
-  // (LATRD style): G stays read-only in global memory, and the rank-2 updates
-  // G_eff = G - sum_k (v_k w_k^dagger + w_k v_k^dagger) of earlier panel steps
-  // are applied on the fly to the column and to the matvec.  After the panel,
-  // one tiled rank-2 j0 update brings the trailing block G[j0:, j0:] up to
-  // date; its lower triangle is then packed into shared memory and the
-  // remaining steps stay on chip.  V and W (j0 x n each, row k = step k) live
-  // in shared memory when they fit, else in ws2 (which receives the
-  // eigenvectors only at the end).
+  // The steps whose trailing block does not fit in shared memory run in
+  // panels of 32 (blocked LATRD): G stays in global memory (L2), and the
+  // rank-2 updates G_eff = G - sum_k (v_k w_k^dagger + w_k v_k^dagger) of the
+  // panel's earlier steps are applied on the fly to the column and to the
+  // matvec; between panels, and after the last one, a rank-2b update brings
+  // the trailing block of G up to date.  The block G[j0:, j0:] left at the
+  // end is packed into shared memory and the remaining steps stay on chip.
+  // V and W (j0 x n each, row k = step k) live in shared memory when they
+  // fit, else in ws2 (which receives the eigenvectors only at the end).
   int j0 = 0;
   while ((n - j0) * (n - j0 + 1) / 2 > HeevSmem<R>::kCap) ++j0;
   // V and W sit in shared memory (unused until the packing) when they fit
   const bool vw_sm = 2 * (size_t)j0 * n * sizeof(cpx<R>) <= (size_t)HeevSmem<R>::kBytes;
   cpx<R>* Vp = vw_sm ? Lp : U;
   cpx<R>* Wp = Vp + (int64_t)j0 * n;
+  // G[jt:, jt:] -= sum_{k in [kb0, kb1)} v_k w_k^dagger + w_k v_k^dagger, both
+  // triangles (the panel matvec reads whole rows).  The lower triangle's
+  // mt (mt + 1) / 2 entries are dealt out to the threads one at a time: an
+  // FP64 instruction costs the pipe the same with any number of active lanes,
+  // so tiles that straddle the diagonal or the edge would pay for the entries
+  // they skip.  V and W are staged in shared memory in chunks of kch steps
+  // (with V and W already in shared memory they are used in place).
+  auto panel_update = [&](int kb0, int kb1, int jt) {
+    const int mt = n - jt, nk = kb1 - kb0;
+    if (nk <= 0 || mt <= 0) return;
+    const int kch = vw_sm ? nk : min(nk, (int)(HeevSmem<R>::kBytes / (2 * (size_t)mt * sizeof(cpx<R>))));
+    const int ldk = vw_sm ? n : mt;
+    const int ne = mt * (mt + 1) / 2;
+    for (int k0 = 0; k0 < nk; k0 += kch) {
+      const int kc = min(kch, nk - k0);
+      if (!vw_sm) {
+        for (int e = threadIdx.x; e < kc * mt; e += blockDim.x) {
+          const int kk = e / mt, i = e - kk * mt;
+          Lp[e] = Vp[(int64_t)(kb0 + k0 + kk) * n + jt + i];
+          Lp[(int64_t)kch * mt + e] = Wp[(int64_t)(kb0 + k0 + kk) * n + jt + i];
+        }
+      }
+      __syncthreads();
+      const cpx<R>* vs = vw_sm ? Vp + (int64_t)(kb0 + k0) * n + jt : Lp;
+      const cpx<R>* ws = vw_sm ? Wp + (int64_t)(kb0 + k0) * n + jt : Lp + (int64_t)kch * mt;
+      for (int e = threadIdx.x; e < ne; e += blockDim.x) {
+        // entry e = i (i + 1) / 2 + c of the packed lower triangle
+        int i = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+        while (i * (i + 1) / 2 > e) --i;
+        while ((i + 1) * (i + 2) / 2 <= e) ++i;
+        const int c = e - i * (i + 1) / 2;
+        cpx<R> acc = mk<R>(0, 0);
+#pragma unroll 4
+        for (int kk = 0; kk < kc; ++kk) {
+          cfmac(acc, ws[kk * ldk + c], vs[kk * ldk + i]);
+          cfmac(acc, vs[kk * ldk + c], ws[kk * ldk + i]);
+        }
+        cpx<R>* g = G + (int64_t)(jt + i) * n + (jt + c);
+        *g = *g - acc;
+        if (c < i) {
+          cpx<R>* gt = G + (int64_t)(jt + c) * n + (jt + i);
+          *gt = *gt - conj(acc);
+        }
+      }
+      __syncthreads();
+    }
+  };
+  // Panels of kPanelWidth steps (blocked LATRD): the corrections of a column
+  // and of a matvec only involve the steps of the current panel (their cost
+  // grows with the panel width), and G is brought up to date between panels.
+  constexpr int kPanelWidth = 32;
+  int jp = 0;   // first step of the current panel
   for (int j = 0; j < j0 && j + 2 < n; ++j) {
+    if (j - jp == kPanelWidth) {
+      panel_update(jp, j, j);
+      jp = j;
+    }
     const int m = n - j - 1;
     // column j of G_eff below the diagonal, and its diagonal entry
     R part = 0;
     for (int i = threadIdx.x; i < m; i += blockDim.x) {
       const int gi = j + 1 + i;
       cpx<R> x = G[(int64_t)gi * n + j];
-      for (int k = 0; k < j; ++k)
+      for (int k = jp; k < j; ++k)
         x = rank2_sub(x, Vp[(int64_t)k * n + gi], Wp[(int64_t)k * n + j], Wp[(int64_t)k * n + gi], Vp[(int64_t)k * n + j]);
       sv[i] = x;
       if (i > 0) part = fma(x.re, x.re, fma(x.im, x.im, part));
     }
     if (threadIdx.x == 0) {
       R dj = G[(int64_t)j * n + j].re;
-      for (int k = 0; k < j; ++k) dj -= (R)2 * cdot(Wp[(int64_t)k * n + j], Vp[(int64_t)k * n + j]).re;
+      for (int k = jp; k < j; ++k) dj -= (R)2 * cdot(Wp[(int64_t)k * n + j], Vp[(int64_t)k * n + j]).re;
       sd[j] = dj;
     }
     part = warp_sum(part);
@@ -289,7 +350,7 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
     if (threadIdx.x == 0) sec[j] = alpha;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
       const cpx<R> vi = (i > j && reflect) ? sv[i - j - 1] : mk<R>(0, 0);
-      Hv[(int64_t)j * n + i] = vi;
+      Hv[(int64_t)j * n + i] = kSqrt2 * vi;
       Vp[(int64_t)j * n + i] = vi;
     }
     if (!reflect) {
@@ -297,61 +358,66 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
       __syncthreads();
       continue;
     }
-    // corrections c1_k = w_k^dagger v, c2_k = v_k^dagger v (k < j); sph is
-    // free until the end of phase 1 and holds 2 j < 2 j0 <= 256 entries
+    // corrections c1_k = w_k^dagger v, c2_k = v_k^dagger v (jp <= k < j); sph
+    // is free until the end of phase 1 and holds 2 (j - jp) <= 64 entries.
+    // Eight dots per warp, four lanes per dot striding along i (an FP64
+    // instruction costs the same with any number of active lanes, so the lane
+    // mapping keeps the ragged last iteration small), summed over the four
+    // lanes by two butterfly rounds.
     cpx<R>* cc = sph;
-    for (int kk = warp; kk < 2 * j; kk += nwarp) {
-      const cpx<R>* src = (kk < j) ? (Wp + (int64_t)kk * n) : (Vp + (int64_t)(kk - j) * n);
-      cpx<R> acc = mk<R>(0, 0);
-      for (int i = lane; i < m; i += 32) cfmac(acc, src[j + 1 + i], sv[i]);
-      acc.re = warp_sum(acc.re);
-      acc.im = warp_sum(acc.im);
-      if (lane == 0) cc[kk] = acc;
+    const int np = j - jp;   // steps of the current panel before this one
+    for (int kk0 = 8 * warp; kk0 < 2 * np; kk0 += 8 * nwarp) {
+      const int kk = kk0 + (lane >> 2);
+      const bool live = kk < 2 * np;
+      const cpx<R>* src = live ? ((kk < np) ? (Wp + (int64_t)(jp + kk) * n) : (Vp + (int64_t)(jp + kk - np) * n)) + j + 1 : Wp;
+      cpx<R> a0 = mk<R>(0, 0), a1 = mk<R>(0, 0);
+      int i = lane & 3;
+      for (; i + 4 < m; i += 8) {
+        if (live) {
+          cfmac(a0, src[i], sv[i]);
+          cfmac(a1, src[i + 4], sv[i + 4]);
+        }
+      }
+      if (i < m && live) cfmac(a0, src[i], sv[i]);
+      a0 += a1;
+#pragma unroll
+      for (int o = 2; o > 0; o >>= 1) {
+        a0.re += __shfl_xor_sync(0xffffffffu, a0.re, o);
+        a0.im += __shfl_xor_sync(0xffffffffu, a0.im, o);
+      }
+      if (live && (lane & 3) == 0) cc[kk] = a0;
     }
     // y = G_sub v from the original (read-only) G, which is served from L2:
-    // four rows per warp, each lane loading two adjacent entries of a row at
-    // a time (16-byte aligned: the segment starts at the even column c0 <= j +
-    // 1) with two such loads per row in flight; the eight partial sums of the
-    // four rows are reduced by one butterfly.
+    // eight rows per warp, four lanes per row, each lane loading two adjacent
+    // entries of its row at a time (16-byte aligned: the segment starts at
+    // the even column c0 <= j + 1) into two independent accumulators; the
+    // four lanes of a row are summed by two butterfly rounds.
     const int c0 = (j + 1) & ~1;
     const int off = j + 1 - c0;        // 1: column c0 = j lies left of the block (weight 0)
     const int npair = (n - c0) >> 1;
-    for (int r0 = 4 * warp; r0 < m; r0 += 4 * nwarp) {
-      const int nq = min(4, m - r0);
-      const cpx<R>* row = G + (int64_t)(j + 1 + r0) * n + c0;
-      cpx<R> acc[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) acc[q] = mk<R>(0, 0);
+    for (int r0 = 8 * warp; r0 < m; r0 += 8 * nwarp) {
+      const int r = r0 + (lane >> 2);
+      const bool rin = r < m;
+      const cpx<R>* row = G + (int64_t)(j + 1 + (rin ? r : 0)) * n + c0;
+      cpx<R> acc0 = mk<R>(0, 0), acc1 = mk<R>(0, 0);
 #pragma unroll 2
-      for (int p2 = lane; p2 < npair; p2 += 32) {
+      for (int p2 = lane & 3; p2 < npair; p2 += 4) {
         const int c = 2 * p2 - off;    // local index of the first entry of the pair
-        const cpx<R> x0 = (c >= 0) ? sv[c] : mk<R>(0, 0), x1 = sv[c + 1];
-        cpx<R> a0[4], a1[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-          if (q < nq) load_pair(row + (int64_t)q * n + 2 * p2, a0[q], a1[q]);
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-          if (q < nq) {
-            cfma(acc[q], a0[q], x0);
-            cfma(acc[q], a1[q], x1);
-          }
-      }
-      R d[8];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        d[2 * q] = acc[q].re;
-        d[2 * q + 1] = acc[q].im;
-      }
-      const R tot = warp_reduce_scatter<8>(d, lane);
-      if ((lane & 3) == 0) {
-        const int e = Scatter<8>::index(lane);
-        const int r = r0 + (e >> 1);
-        if (r < m) {
-          if (e & 1) sw[r].im = tot;
-          else sw[r].re = tot;
+        if (rin) {
+          const cpx<R> x0 = (c >= 0) ? sv[c] : mk<R>(0, 0), x1 = sv[c + 1];
+          cpx<R> e0, e1;
+          load_pair(row + 2 * p2, e0, e1);
+          cfma(acc0, e0, x0);
+          cfma(acc1, e1, x1);
         }
       }
+      acc0 += acc1;
+#pragma unroll
+      for (int o = 2; o > 0; o >>= 1) {
+        acc0.re += __shfl_xor_sync(0xffffffffu, acc0.re, o);
+        acc0.im += __shfl_xor_sync(0xffffffffu, acc0.im, o);
+      }
+      if (rin && (lane & 3) == 0) sw[r] = acc0;
     }
     __syncthreads();
     // y -= sum_k v_k (w_k^dagger v) + w_k (v_k^dagger v)
@@ -359,9 +425,9 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
     for (int i = threadIdx.x; i < m; i += blockDim.x) {
       const int gi = j + 1 + i;
       cpx<R> y = sw[i];
-      for (int k = 0; k < j; ++k) {
-        cfms(y, Vp[(int64_t)k * n + gi], cc[k]);
-        cfms(y, Wp[(int64_t)k * n + gi], cc[j + k]);
+      for (int k = 0; k < np; ++k) {
+        cfms(y, Vp[(int64_t)(jp + k) * n + gi], cc[k]);
+        cfms(y, Wp[(int64_t)(jp + k) * n + gi], cc[np + k]);
       }
       sw[i] = y;
       sp = fma(sv[i].re, y.re, fma(sv[i].im, y.im, sp));
@@ -373,72 +439,7 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
     }
     __syncthreads();
   }
-  if (j0 > 0) {
-    // G[j0:, j0:] -= sum_k v_k w_k^dagger + w_k v_k^dagger over the panel
-    // (lower triangle only).  V and W are staged in shared memory in chunks
-    // of kch steps; 64 x 64 output tiles, each of the 512 threads (32 x 16)
-    // owns rows ty + 16 r and columns tx + 32 c of a tile.
-    // (With V and W already in shared memory they are used in place.)
-    const int mt = n - j0;
-    const int kch = vw_sm ? j0 : min(j0, (int)(HeevSmem<R>::kBytes / (2 * (size_t)mt * sizeof(cpx<R>))));
-    const int ldk = vw_sm ? n : mt;
-    const cpx<R>* Vs = vw_sm ? Vp + j0 : Lp;
-    const cpx<R>* Ws = vw_sm ? Wp + j0 : Lp + (int64_t)kch * mt;
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    const int ntile = (mt + 63) / 64;
-    for (int k0 = 0; k0 < j0; k0 += kch) {
-      const int kc = min(kch, j0 - k0);
-      if (!vw_sm) {
-        for (int e = threadIdx.x; e < kc * mt; e += blockDim.x) {
-          const int kk = e / mt, i = e - kk * mt;
-          Lp[e] = Vp[(int64_t)(k0 + kk) * n + j0 + i];
-          Lp[(int64_t)kch * mt + e] = Wp[(int64_t)(k0 + kk) * n + j0 + i];
-        }
-      }
-      __syncthreads();
-      for (int ti = 0; ti < ntile; ++ti)
-        for (int tc = 0; tc <= ti; ++tc) {
-          cpx<R> acc[4][2];
-#pragma unroll
-          for (int r = 0; r < 4; ++r)
-#pragma unroll
-            for (int c = 0; c < 2; ++c) acc[r][c] = mk<R>(0, 0);
-          for (int kk = 0; kk < kc; ++kk) {
-            cpx<R> va[4], wa[4], vb[2], wb[2];
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-              const int i = ti * 64 + ty + 16 * r;
-              va[r] = i < mt ? Vs[kk * ldk + i] : mk<R>(0, 0);
-              wa[r] = i < mt ? Ws[kk * ldk + i] : mk<R>(0, 0);
-            }
-#pragma unroll
-            for (int c = 0; c < 2; ++c) {
-              const int i = tc * 64 + tx + 32 * c;
-              vb[c] = i < mt ? Vs[kk * ldk + i] : mk<R>(0, 0);
-              wb[c] = i < mt ? Ws[kk * ldk + i] : mk<R>(0, 0);
-            }
-#pragma unroll
-            for (int r = 0; r < 4; ++r)
-#pragma unroll
-              for (int c = 0; c < 2; ++c) {
-                cfmac(acc[r][c], wb[c], va[r]);
-                cfmac(acc[r][c], vb[c], wa[r]);
-              }
-          }
-#pragma unroll
-          for (int r = 0; r < 4; ++r)
-#pragma unroll
-            for (int c = 0; c < 2; ++c) {
-              const int i = ti * 64 + ty + 16 * r, cc = tc * 64 + tx + 32 * c;
-              if (i < mt && cc <= i) {
-                cpx<R>* g = G + (int64_t)(j0 + i) * n + (j0 + cc);
-                *g = *g - acc[r][c];
-              }
-            }
-        }
-      __syncthreads();
-    }
-  }
+  if (j0 > 0) panel_update(jp, min(j0, n - 2), j0);
   // pack the lower triangle of the trailing block G[j0:, j0:]
   const int M0 = n - j0;
   for (int r = warp; r < M0; r += nwarp)
@@ -512,7 +513,7 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
       vN[jl + 1 + i] = vi;
       yN[jl + 1 + i] = mk<R>(0, 0);
       wP[jl + 1 + i] = wi;
-      Hv[(int64_t)j * n + (j + 1 + i)] = vi;
+      Hv[(int64_t)j * n + (j + 1 + i)] = kSqrt2 * vi;
     }
     if (i <= j) Hv[(int64_t)j * n + i] = mk<R>(0, 0);
     __syncthreads();
@@ -700,119 +701,59 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
   }
   __syncthreads();
   {
-    // G lanes of a warp share eigenvalue k (G = 4 when 128 eigenvalues are
-    // kept on 512 threads; keep <= 128 always gives G >= 4).  Safeguarded
-    // Newton: lane 0 of the group evaluates the Sturm count and S at the
-    // Newton iterate x_n, lanes 1 and 2 the counts at x_n -/+ delta (delta =
-    // twice the last Newton step, which bounds the iterate's error once
-    // Newton converges quadratically), lanes 3.. interior points of the
-    // bracket; every count moves one end of the bracket, and the next iterate
-    // is x_n - 1 / S, or the bracket midpoint when that leaves the bracket.
-    // The eigenvalue is done when its bracket is 4 eps ||T|| wide
-    // (normalized: 4 eps), or when the bracket holds it alone (end counts
-    // differ by one) and the Newton step is below a quarter of that: it is
-    // then as accurate as the backward-stable reduction from G allows (a few
-    // eps ||G|| absolute), which is all that the shifts of the inverse
-    // iteration and the entropies need.  From the 5 % grid brackets this
-    // takes about seven rounds instead of the eighteen of plain multisection.
-    // (G < 4: plain multisection.)
-    int G = 1;
-    while (G < 32 && keep * (2 * G) <= (int)blockDim.x) G *= 2;
-    const int per_warp = 32 / G;
-    const int gi = lane & (G - 1);
-    const int gbase = lane & ~(G - 1);
-    const unsigned gmask = (G == 32) ? 0xffffffffu : ((1u << G) - 1u);
+    // One lane per kept eigenvalue k, on warps 0..3 only (an FP64
+    // instruction costs its SMSP 64 cycles whatever the number of active
+    // lanes, so more lanes per eigenvalue or more warps only add cost).
+    // Safeguarded Newton on det(T - x I) inside the bracket [lo, hi] from the
+    // grid: each round evaluates the Sturm count and S = d/dx ln|det| at the
+    // iterate x_n, moves one end of the bracket to x_n, and steps to x_n -
+    // 1 / S, or to the bracket midpoint when that leaves the bracket.  A
+    // Newton step below tol / 4 only says that x_n is near some eigenvalue,
+    // possibly a neighbour just outside the bracket, so the next point is then
+    // x_n +/- tol / 2 on the side where the count puts eigenvalue k: when it
+    // lands beyond the eigenvalue the bracket closes to that width.  The
+    // eigenvalue is done when its bracket is tol = 4 eps ||T|| wide
+    // (normalized: 4 eps): as accurate as the backward-stable reduction from
+    // G allows (a few eps ||G|| absolute), which is all that the shifts of the
+    // inverse iteration and the entropies need.  From the 5 % grid brackets
+    // this takes about ten rounds (at most fifteen for a warp of 32).
     const double tol = 4.0 * eps + pivmin;
-    for (int kb = 0; kb < keep; kb += nwarp * per_warp) {
-      const int k = kb + warp * per_warp + lane / G;
-      double lo = gl, hi = gu;
-      if (k < keep) {
-        // grid counts do not increase along the grid: a = last point below
-        // eigenvalue k (count > k), b = a + 1 the first at or above it
-        int a = -1, b = (int)blockDim.x;
-        while (b - a > 1) {
-          const int mid = (a + b) >> 1;
-          if (gcnt[mid] > k) a = mid;
-          else b = mid;
-        }
-        if (a >= 0) lo = gx[a];
-        if (b < (int)blockDim.x) hi = gx[b];
-      }
-      bool done = k >= keep;
-      double val = 0.0;   // set when the Newton iteration converges first
-      bool newton_done = false;
-      if (G >= 4) {
-        // counts at the bracket ends: an isolated eigenvalue has c_lo - c_hi = 1
-        int c_lo = n, c_hi = 0;
+    constexpr int kNewtonWarps = 4;
+    if (warp < kNewtonWarps) {
+      for (int kb = 0; kb < keep; kb += 32 * kNewtonWarps) {
+        const int k = kb + warp * 32 + lane;
+        double lo = gl, hi = gu;
         if (k < keep) {
+          // grid counts do not increase along the grid: a = last point below
+          // eigenvalue k (count > k), b = a + 1 the first at or above it
           int a = -1, b = (int)blockDim.x;
           while (b - a > 1) {
             const int mid = (a + b) >> 1;
             if (gcnt[mid] > k) a = mid;
             else b = mid;
           }
-          if (a >= 0) c_lo = gcnt[a];
-          if (b < (int)blockDim.x) c_hi = gcnt[b];
+          if (a >= 0) lo = gx[a];
+          if (b < (int)blockDim.x) hi = gx[b];
         }
-        double xn = 0.5 * (lo + hi), dl = 0.25 * (hi - lo);
-        for (int it = 0; it < 200; ++it) {
+        bool done = k >= keep;
+        double xn = 0.5 * (lo + hi);
+        for (int it = 0; it < 300; ++it) {
           if (hi - lo <= tol) done = true;
           if (__all_sync(0xffffffffu, done)) break;
-          double x;
-          if (gi == 0) x = xn;
-          else if (gi == 1) x = (xn - dl > lo) ? xn - dl : 0.5 * (lo + xn);
-          else if (gi == 2) x = (xn + dl < hi) ? xn + dl : 0.5 * (xn + hi);
-          else x = lo + (hi - lo) * (double)(gi - 2) / (double)(G - 2);
+          if (done) continue;
           double S = 0.0;
-          const int c = done ? 0 : sturm_newton_f64(tdn, te2n, n, x, pivmin, S);
-          const bool above = !done && c > k;   // eigenvalue k lies above x
-          double nlo = above ? x : lo, nhi = (!done && !above) ? x : hi;
-          int nclo = above ? c : c_lo, nchi = (!done && !above) ? c : c_hi;
-          for (int o = 1; o < G; o <<= 1) {
-            nlo = fmax(nlo, __shfl_xor_sync(0xffffffffu, nlo, o));
-            nhi = fmin(nhi, __shfl_xor_sync(0xffffffffu, nhi, o));
-            nclo = min(nclo, __shfl_xor_sync(0xffffffffu, nclo, o));
-            nchi = max(nchi, __shfl_xor_sync(0xffffffffu, nchi, o));
-          }
-          const double S0 = __shfl_sync(0xffffffffu, S, gbase);
-          const double step = (S0 != 0.0) ? -1.0 / S0 : 0.0;
+          const bool up = sturm_newton_f64(tdn, te2n, n, xn, pivmin, S) > k;   // eigenvalue k above x_n
+          if (up) lo = xn;
+          else hi = xn;
+          const double step = (S != 0.0) ? -1.0 / S : 0.0;
           double xnew = xn + step;
-          if (!done) {
-            // converged: the bracket holds eigenvalue k alone, the Newton
-            // step is below a quarter of the tolerance and lands in it
-            if (nclo - nchi == 1 && S0 != 0.0 && fabs(step) <= 0.25 * tol && xnew >= nlo && xnew <= nhi) {
-              val = xnew;
-              newton_done = true;
-              done = true;
-            } else {
-              if (!(S0 != 0.0 && xnew > nlo && xnew < nhi)) xnew = 0.5 * (nlo + nhi);
-              dl = fmin(fmax(2.0 * fabs(xnew - xn), 0.25 * tol), 0.25 * (nhi - nlo));
-              lo = nlo;
-              hi = nhi;
-              c_lo = nclo;
-              c_hi = nchi;
-              xn = xnew;
-            }
-          }
+          if (S != 0.0 && fabs(step) <= 0.25 * tol) xnew = xn + (up ? 0.5 * tol : -0.5 * tol);
+          if (!(S != 0.0 && xnew > lo && xnew < hi)) xnew = 0.5 * (lo + hi);
+          xn = xnew;
         }
-      } else {
-        for (int it = 0; it < 200; ++it) {
-          const double h = (hi - lo) / (double)(G + 1);
-          if (hi - lo <= tol || !(lo + h > lo) || !(hi - h < hi)) done = true;
-          if (__all_sync(0xffffffffu, done)) break;
-          const double x = lo + h * (double)(gi + 1);
-          const bool above = !done && sturm_greater_f64(tdn, te2n, n, x, pivmin) > k;
-          const unsigned grp = (__ballot_sync(0xffffffffu, above) >> gbase) & gmask;
-          const int pcount = __popc(grp);   // interior points below eigenvalue k
-          if (!done) {
-            const double nlo = (pcount > 0) ? lo + h * (double)pcount : lo;
-            const double nhi = (pcount < G) ? lo + h * (double)(pcount + 1) : hi;
-            lo = nlo;
-            hi = nhi;
-          }
-        }
+        const double val = 0.5 * (lo + hi);
+        if (k < keep) ev[k] = val * tnorm;
       }
-      if (k < keep && gi == 0) ev[k] = (newton_done ? val : 0.5 * (lo + hi)) * tnorm;
     }
   }
   if (threadIdx.x == 0) {
