@@ -579,6 +579,7 @@ def main():
     value = total_updates / (ms / 1000.0)
     e2e = None if args.no_e2e else mixed.e2e(min(args.e2e_steps, args.steps))
     prof, work, prof_updates = mixed.profile_step()
+    observables = merged_observables(mixed.measure(), world)
     mixed.destroy()
 
     # FP64 comparator: the same path in complex128 on a batch that fills the
@@ -620,6 +621,7 @@ def main():
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "fp64_value": fp64, "fp64": fp64_info, "mixed_over_fp64": (value / fp64) if fp64 else None,
         "observable_error_mixed_vs_fp64": obs_err,
+        "observables": observables,
         "e2e": None if e2e is None else {"value": e2e["value"], "unit": UNIT, "h2d_bytes_per_step": e2e["h2d"],
                                          "d2h_bytes_per_step": e2e["d2h"], "steps": e2e["steps"]},
         "gpu_launches": gpu_launches(prof, args.steps),
@@ -635,6 +637,25 @@ def main():
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(line))
+
+
+def merged_observables(res, world):
+    """Trajectory averages of the states after the mixed arm's last layer, per
+    system size: <Z> of the middle qubit, the half-chain entropy (nats) and the
+    error bound's mean, merged exactly over the ranks (replicas)."""
+    from paper_2508_05745_gb300 import replicas as RP
+    out = {}
+    for n in sorted(res):
+        r = res[n]
+        cols = np.column_stack([r["z"][:, n // 2], r["s_half"], r["eps_bound"]])
+        if world > 1:
+            import torch.distributed as dist
+            mean, se = RP.merged_observables(dist, [cols])
+        else:
+            mean, se = RP.finalize(RP.exact_sums(cols))
+        out[str(n)] = {"z_mid": [float(mean[0]), float(se[0])], "s_half": [float(mean[1]), float(se[1])],
+                       "eps_hat": float(mean[2]), "trajectories": int(len(cols)) * world}
+    return out
 
 
 def gpu_launches(prof, steps):

@@ -107,6 +107,11 @@ typedef struct {
   lemps_free_fn free;
   void* alloc_ctx;
   int32_t layering;       /* lemps_layering (0 = local) */
+  int64_t max_traj_in_flight; /* trajectories held on the device at once (a
+                             wave); 0 = automatic: as many as fit in 60 % of the
+                             device memory (and 90 % of what is free).  When
+                             n_traj exceeds it, the handle runs in waves (see
+                             measure) */
 } lemps_config;
 
 typedef struct {
@@ -171,8 +176,23 @@ lemps_status sample_branch(lemps_handle h, int64_t gate, int32_t slot, int32_t* 
 
 /* Observables of Sec. III.C / App. C on the current states, mean and standard
  * error over trajectories, and the a-posteriori error estimate of Thm. 1.
- * Moves every trajectory's orthogonality centre; synchronizes the stream. */
+ * Moves every trajectory's orthogonality centre; synchronizes the stream.
+ * Waves (n_traj > max_traj_in_flight): trajectories are independent (Sec.
+ * III), so one wave of at most max_traj_in_flight trajectories is resident
+ * on the device; apply_layer advances it and keeps a host copy of every
+ * layer.  measure measures the resident wave, then puts each other wave in
+ * |0...0> and brings it through the recorded layers before measuring it
+ * (global trajectory ids, so the results equal those of one big handle:
+ * per trajectory bit for bit, means and standard errors merged exactly up to
+ * rounding); the last wave processed stays resident.  The per-trajectory
+ * outputs cover all n_traj trajectories.  sample_branch, sample_bitstrings,
+ * eps_concentrated and sim_export_mps need a single wave (LEMPS_ESTATE
+ * otherwise); sim_sync checks the resident wave. */
 lemps_status measure(lemps_handle h, lemps_measurement* m);
+
+/* The wave size (trajectories held on the device) and the number of waves of
+ * the handle. */
+lemps_status sim_waves(lemps_handle h, int64_t* wave_size, int32_t* n_waves);
 
 /* Output-distribution sampling (Lemma sampling_reduction; Corollary on output
  * distribution sampling): draws n_shots (1..65535) computational-basis

@@ -170,13 +170,27 @@ def induced_decomposition(kraus: np.ndarray, psi: np.ndarray) -> np.ndarray:
 
 # --- Wootters' optimal decomposition, closed-form version (App. F.2) --------
 
+def unitary_sqrt(w: np.ndarray) -> np.ndarray:
+    """Principal square root of a unitary matrix.  A unitary matrix is normal,
+    so its complex Schur form w = Z T Z^dagger has a diagonal T (up to
+    rounding): the root is Z diag(exp(i theta / 2)) Z^dagger with theta =
+    arg T_kk in (-pi, pi], and the branch cut sits at -1, whose root is +i.
+    Taking only the diagonal avoids the triangular recurrence of a general
+    matrix square root, which is ill-conditioned exactly when eigenvalues
+    repeat (the degenerate Takagi values of depolarizing noise)."""
+    t, z = sla.schur(np.asarray(w, dtype=np.complex128), output="complex")
+    theta = np.angle(np.diag(t))
+    theta = np.where(theta <= -math.pi + 1e-12, math.pi, theta)
+    return (z * np.exp(0.5j * theta)) @ z.conj().T
+
+
 def takagi(tau: np.ndarray):
     """Takagi-Autonne factorization tau = U diag(s) U^T of a complex symmetric
-    matrix from its SVD: U = U_M sqrt((U_M^T V_M)^*) (App. F.2, Step 1).
-    Returns (U, s) with s descending."""
+    matrix from its SVD: U = U_M sqrt((U_M^T V_M)^*) (App. F.2, Step 1), with
+    the principal root of that unitary.  Returns (U, s) with s descending."""
     um, s, vmh = np.linalg.svd(tau)
     vm = vmh.conj().T
-    root = sla.sqrtm((um.T @ vm).conj())
+    root = unitary_sqrt((um.T @ vm).conj())
     return um @ root, s
 
 

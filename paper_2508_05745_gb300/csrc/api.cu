@@ -31,10 +31,26 @@ constexpr int kThreads = 256;
 // Layers whose error contributions are kept per trajectory for eps_concentrated.
 constexpr int kEpsHistLayers = 256;
 
+// A layer as applied, kept on the host so that the waves that are not
+// resident can be brought to the same point later.
+struct RecordedLayer {
+  std::vector<int32_t> left_qubit;
+  std::vector<double> gates, kraus;
+  int32_t n_kraus = 0;
+  double coin_p = 1.0;
+};
+
 struct lemps_sim {
   lemps_config cfg;
   int n = 0;
-  int64_t B = 0;
+  int64_t B = 0;             // trajectories of the resident wave (kernel grids, counts)
+  int64_t Bcap = 0;          // wave capacity: allocation and per-trajectory strides
+  int64_t n_total = 0;       // trajectories of the handle (all waves)
+  int n_waves = 1;
+  int wave = 0;              // the resident wave
+  bool wave_current = true;  // the resident wave has every recorded layer applied
+  int64_t wave_offset = 0;   // global id of the resident wave's first trajectory
+  std::vector<RecordedLayer> history;   // every layer applied (multi-wave handles only)
   int chi = 0;
   int cap_max = 0;           // bond capacity: chi (local layering) or 2 chi (global)
   int prec = 0;
@@ -74,6 +90,7 @@ struct lemps_sim {
   double* stats = nullptr;   // reductions
   int64_t gates_done = 0;
   int center = 0;
+  size_t mps_bytes = 0;
   bool profiling = false;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof;  // (kind, (start, stop))
   double prof_ms[LEMPS_NUM_KERNEL_KINDS] = {0};
@@ -164,6 +181,22 @@ lemps_status check_cuda(lemps_sim* h, const char* where) {
   return LEMPS_OK;
 }
 
+// Put wave w (global trajectory ids traj_offset + w Bcap onwards) in
+// |0...0>, discarding the resident state; the wave then has no layer applied.
+void reset_wave(lemps_sim* h, int w) {
+  h->wave = w;
+  h->wave_offset = h->cfg.traj_offset + (int64_t)w * h->Bcap;
+  h->B = std::min<int64_t>(h->Bcap, h->n_total - (int64_t)w * h->Bcap);
+  h->center = 0;
+  h->gates_done = 0;
+  h->layers_done = 0;
+  h->wave_current = h->history.empty();
+  cudaMemsetAsync(h->mps, 0, h->mps_bytes, h->stream);
+  if (h->log_cap > 0) cudaMemsetAsync(h->blog, 0xff, h->log_cap * 2 * h->Bcap, h->stream);
+  if (h->prec == LEMPS_FP64) k_init_state<double><<<(unsigned)h->B, 64, 0, h->stream>>>(h->view<double>());
+  else k_init_state<float><<<(unsigned)h->B, 64, 0, h->stream>>>(h->view<float>());
+}
+
 template <class R>
 void launch_move(lemps_sim* h, int k, int dir) {
   const size_t smem = sizeof(QrSmem<R>);
@@ -250,7 +283,7 @@ lemps_status apply_layer_t(lemps_sim* h, const lemps_layer* L) {
     ld.coin_p = coin_p;
     ld.mode = kmode;
     ld.seed = h->cfg.seed;
-    ld.traj_offset = h->cfg.traj_offset;
+    ld.traj_offset = h->wave_offset;
     ld.gate_global = gate_global;
     ld.gate_local = gate_local;
     ld.blog = (log && gate_global < h->log_cap) ? h->blog + gate_global * 2 * h->B : nullptr;
@@ -404,10 +437,11 @@ lemps_status sim_create(const lemps_config* cfg, lemps_handle* out) {
   if (cfg->layering == LEMPS_LAYER_GLOBAL && cfg->chi_max > 64)
     return fail(LEMPS_EINVAL, "sim_create: global layering holds bonds of 2 chi_max, so chi_max must be <= 64");
   if ((cfg->alloc == nullptr) != (cfg->free == nullptr)) return fail(LEMPS_EINVAL, "sim_create: alloc and free go together");
+  if (cfg->max_traj_in_flight < 0) return fail(LEMPS_EINVAL, "sim_create: max_traj_in_flight must be >= 0");
   lemps_sim* h = new lemps_sim();
   h->cfg = *cfg;
   h->n = cfg->n_qubits;
-  h->B = cfg->n_traj;
+  h->n_total = cfg->n_traj;
   h->chi = cfg->chi_max;
   h->cap_max = (cfg->layering == LEMPS_LAYER_GLOBAL) ? 2 * cfg->chi_max : cfg->chi_max;
   h->prec = cfg->precision;
@@ -420,14 +454,38 @@ lemps_status sim_create(const lemps_config* cfg, lemps_handle* out) {
     int64_t c = (e >= 30) ? (int64_t)1 << 30 : ((int64_t)1 << e);
     h->cap_h[k] = (int32_t)std::min<int64_t>(c, h->cap_max);
   }
+  h->ws_stride = (int64_t)(2 * h->cap_max) * (2 * h->cap_max);
+  h->log_cap = cfg->log_capacity > 0 ? cfg->log_capacity : 0;
+  // Waves: the device holds Bcap trajectories at a time.  Bytes per
+  // trajectory: the MPS slots, the four workspaces (the last three in
+  // complex128), and the per-trajectory scalars and logs.
+  {
+    int64_t slot = 0;
+    for (int k = 0; k < n; ++k) slot += (int64_t)h->cap_h[k] * 2 * h->cap_h[k + 1];
+    const double per = (double)h->elem * (double)slot + (double)(h->elem + 3 * sizeof(zd)) * (double)h->ws_stride +
+                       8.0 * (2 * h->cap_max + 2 * n + 1 + kEpsHistLayers + 8) + 4.0 * (n + 4) + 32.0 * 16 +
+                       2.0 * (double)h->log_cap;
+    int64_t cap = cfg->max_traj_in_flight;
+    if (cap == 0) {
+      // automatic: at most 60 % of the device's memory, and of what is free
+      size_t fr = 0, totm = 0;
+      if (cudaMemGetInfo(&fr, &totm) != cudaSuccess) {
+        delete h;
+        return fail(LEMPS_ECUDA, "sim_create: cudaMemGetInfo failed");
+      }
+      const double budget = std::min(0.6 * (double)totm, 0.9 * (double)fr);
+      cap = std::max<int64_t>(1, (int64_t)(budget / per));
+    }
+    h->Bcap = std::min<int64_t>(cap, h->n_total);
+    h->n_waves = (int)((h->n_total + h->Bcap - 1) / h->Bcap);
+    h->B = h->Bcap;
+  }
   h->off_h.resize(n);
   int64_t tot = 0;
   for (int k = 0; k < n; ++k) {
     h->off_h[k] = tot;
-    tot += (int64_t)h->cap_h[k] * 2 * h->cap_h[k + 1] * h->B;
+    tot += (int64_t)h->cap_h[k] * 2 * h->cap_h[k + 1] * h->Bcap;
   }
-  h->ws_stride = (int64_t)(2 * h->cap_max) * (2 * h->cap_max);
-  h->log_cap = cfg->log_capacity > 0 ? cfg->log_capacity : 0;
   h->layer_cap = (int64_t)(n / 2 + 1) * 16 + 4 * kMaxKraus;
   bool ok = true, aligned = true;
   auto A = [&](size_t bytes) {
@@ -439,26 +497,26 @@ lemps_status sim_create(const lemps_config* cfg, lemps_handle* out) {
   h->mps = A(h->elem * tot);
   h->site_off = (int64_t*)A(sizeof(int64_t) * n);
   h->cap = (int32_t*)A(sizeof(int32_t) * (n + 1));
-  h->bond = (int32_t*)A(sizeof(int32_t) * (n + 1) * h->B);
+  h->bond = (int32_t*)A(sizeof(int32_t) * (n + 1) * h->Bcap);
   // ws0 (two-site tensor) in the storage precision; ws1..ws3 at 16 bytes per
   // entry: the Gram matrix, eigenvectors and reflectors are complex128
-  h->ws[0] = A(h->elem * h->ws_stride * h->B);
-  for (int i = 1; i < 4; ++i) h->ws[i] = A(sizeof(zd) * h->ws_stride * h->B);
-  h->evals = (double*)A(sizeof(double) * 2 * h->cap_max * h->B);
-  h->rho12 = (zd*)A(sizeof(zd) * 16 * h->B);
-  h->top = (zd*)A(sizeof(zd) * 16 * h->B);
-  h->eps_layer = (double*)A(sizeof(double) * h->B);
-  h->eps_tot = (double*)A(sizeof(double) * h->B);
-  h->disc_last = (double*)A(sizeof(double) * h->B);
-  h->status = (int32_t*)A(sizeof(int32_t) * h->B);
-  h->kept = (int32_t*)A(sizeof(int32_t) * h->B);
-  h->trace = (double*)A(sizeof(double) * h->B);
-  h->blog = (int8_t*)A(std::max<int64_t>(1, h->log_cap * 2 * h->B));
+  h->ws[0] = A(h->elem * h->ws_stride * h->Bcap);
+  for (int i = 1; i < 4; ++i) h->ws[i] = A(sizeof(zd) * h->ws_stride * h->Bcap);
+  h->evals = (double*)A(sizeof(double) * 2 * h->cap_max * h->Bcap);
+  h->rho12 = (zd*)A(sizeof(zd) * 16 * h->Bcap);
+  h->top = (zd*)A(sizeof(zd) * 16 * h->Bcap);
+  h->eps_layer = (double*)A(sizeof(double) * h->Bcap);
+  h->eps_tot = (double*)A(sizeof(double) * h->Bcap);
+  h->disc_last = (double*)A(sizeof(double) * h->Bcap);
+  h->status = (int32_t*)A(sizeof(int32_t) * h->Bcap);
+  h->kept = (int32_t*)A(sizeof(int32_t) * h->Bcap);
+  h->trace = (double*)A(sizeof(double) * h->Bcap);
+  h->blog = (int8_t*)A(std::max<int64_t>(1, h->log_cap * 2 * h->Bcap));
   h->layer_buf = (zd*)A(sizeof(zd) * h->layer_cap);
   h->haar = (zd*)A(sizeof(zd) * 21);
   h->eye4 = (zd*)A(sizeof(zd) * 16);
-  h->eps_hist = (double*)A(sizeof(double) * kEpsHistLayers * h->B);
-  h->obs = (double*)A(sizeof(double) * h->B * (2 * n + 1));
+  h->eps_hist = (double*)A(sizeof(double) * kEpsHistLayers * h->Bcap);
+  h->obs = (double*)A(sizeof(double) * h->Bcap * (2 * n + 1));
   h->stats = (double*)A(sizeof(double) * (4 * n + 4));
   if (!ok || !aligned) {
     h->release();
@@ -466,8 +524,7 @@ lemps_status sim_create(const lemps_config* cfg, lemps_handle* out) {
     return ok ? fail(LEMPS_EINVAL, "sim_create: the allocator returned a block that is not 16-byte aligned")
               : fail(LEMPS_ENOMEM, "sim_create: device allocation failed");
   }
-  cudaMemsetAsync(h->mps, 0, h->elem * tot, h->stream);
-  if (h->log_cap > 0) cudaMemsetAsync(h->blog, 0xff, h->log_cap * 2 * h->B, h->stream);
+  h->mps_bytes = h->elem * tot;
   cudaMemcpyAsync(h->site_off, h->off_h.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice, h->stream);
   cudaMemcpyAsync(h->cap, h->cap_h.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice, h->stream);
   {
@@ -478,8 +535,7 @@ lemps_status sim_create(const lemps_config* cfg, lemps_handle* out) {
                                  {0, 0}, {0, 0}, {1, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}, {1, 0}};
     cudaMemcpyAsync(h->eye4, kEye4, sizeof(kEye4), cudaMemcpyHostToDevice, h->stream);
   }
-  if (h->prec == LEMPS_FP64) k_init_state<double><<<(unsigned)h->B, 64, 0, h->stream>>>(h->view<double>());
-  else k_init_state<float><<<(unsigned)h->B, 64, 0, h->stream>>>(h->view<float>());
+  reset_wave(h, 0);
   lemps_status st = check_cuda(h, "sim_create");
   if (st != LEMPS_OK) {
     h->release();
@@ -526,6 +582,16 @@ lemps_status apply_layer(lemps_handle h, const lemps_layer* layer) {
   double dev = std::fabs(s[0] - 1) + std::fabs(s[6] - 1) + std::fabs(s[1]) + std::fabs(s[7]) + std::fabs(s[2]) +
                std::fabs(s[3]) + std::fabs(s[4]) + std::fabs(s[5]);
   if (!(dev < 1e-9)) return fail(LEMPS_EINVAL, "apply_layer: Kraus set is not trace preserving");
+  if (h->n_waves > 1) {
+    // kept for the waves that are not resident (replayed by measure)
+    RecordedLayer r;
+    r.left_qubit.assign(layer->left_qubit, layer->left_qubit + layer->n_gates);
+    r.gates.assign(layer->gates, layer->gates + 32 * (size_t)layer->n_gates);
+    r.kraus.assign(layer->kraus, layer->kraus + 8 * (size_t)layer->n_kraus);
+    r.n_kraus = layer->n_kraus;
+    r.coin_p = layer->coin_p;
+    h->history.push_back(std::move(r));
+  }
   if (h->prec == LEMPS_FP64) return apply_layer_t<double>(h, layer);
   return apply_layer_t<float>(h, layer);
 }
@@ -541,6 +607,7 @@ lemps_status unravel_opt(const double* rho_a, const double* kraus, int32_t n_kra
 
 lemps_status sample_branch(lemps_handle h, int64_t gate, int32_t slot, int32_t* branch_out) {
   if (!h || !branch_out || slot < 0 || slot > 1) return fail(LEMPS_EINVAL, "sample_branch: bad argument");
+  if (h->n_waves > 1) return fail(LEMPS_ESTATE, "sample_branch: the handle runs in waves; per-trajectory inspection needs n_traj <= max_traj_in_flight");
   if (h->sticky) return fail(LEMPS_ECUDA, "sample_branch: sticky CUDA error");
   if (gate < 0 || gate >= h->gates_done) return fail(LEMPS_ESTATE, "sample_branch: gate not applied yet");
   if (gate >= h->log_cap) return fail(LEMPS_ESTATE, "sample_branch: gate beyond log_capacity");
@@ -555,6 +622,7 @@ lemps_status sample_branch(lemps_handle h, int64_t gate, int32_t slot, int32_t* 
 
 lemps_status sample_bitstrings(lemps_handle h, int32_t n_shots, uint8_t* bits_out) {
   if (!h || !bits_out || n_shots < 1 || n_shots > 65535) return fail(LEMPS_EINVAL, "sample_bitstrings: bad argument");
+  if (h->n_waves > 1) return fail(LEMPS_ESTATE, "sample_bitstrings: the handle runs in waves; per-trajectory inspection needs n_traj <= max_traj_in_flight");
   if (h->sticky) return fail(LEMPS_ECUDA, "sample_bitstrings: sticky CUDA error");
   const size_t bytes = (size_t)h->B * (size_t)n_shots * (size_t)h->n;
   if (bytes > h->bits_cap) {
@@ -581,6 +649,7 @@ lemps_status sample_bitstrings(lemps_handle h, int32_t n_shots, uint8_t* bits_ou
 
 lemps_status eps_concentrated(lemps_handle h, int32_t kind, double param, double* eps_out, double* eps_hat) {
   if (!h || !eps_hat) return fail(LEMPS_EINVAL, "eps_concentrated: null argument");
+  if (h->n_waves > 1) return fail(LEMPS_ESTATE, "eps_concentrated: the handle runs in waves; per-trajectory inspection needs n_traj <= max_traj_in_flight");
   if (h->sticky) return fail(LEMPS_ECUDA, "eps_concentrated: sticky CUDA error");
   if (kind == 0 ? !(param > 0.0 && param <= 1.0) : (kind == 1 ? !(param >= 0.0 && param <= 1.0) : true))
     return fail(LEMPS_EINVAL, "eps_concentrated: kind 0 needs 0 < alpha <= 1, kind 1 needs 0 <= p <= 1");
@@ -606,12 +675,93 @@ lemps_status eps_concentrated(lemps_handle h, int32_t kind, double param, double
 lemps_status measure(lemps_handle h, lemps_measurement* m) {
   if (!h || !m || !m->z_mean || !m->z_stderr || !m->zz_mean || !m->zz_stderr) return fail(LEMPS_EINVAL, "measure: bad argument");
   if (h->sticky) return fail(LEMPS_ECUDA, "measure: sticky CUDA error");
-  if (h->prec == LEMPS_FP64) return measure_t<double>(h, m);
-  return measure_t<float>(h, m);
+  auto measure_resident = [&](lemps_measurement* mw) {
+    return (h->prec == LEMPS_FP64) ? measure_t<double>(h, mw) : measure_t<float>(h, mw);
+  };
+  if (h->n_waves == 1) return measure_resident(m);
+  // Waves: the resident wave is measured as it stands, every other wave is
+  // put in |0...0> and brought through the recorded layers first.  The
+  // per-wave means and standard errors are merged exactly (sums of squared
+  // deviations combined pairwise); the last wave processed stays resident.
+  const int n = h->n;
+  const int ncol = 2 * n + 1;   // z (n), zz (n - 1), s_half (1), eps_bound (1)
+  std::vector<double> mean(ncol, 0.0), m2(ncol, 0.0);
+  int64_t count = 0, failed = 0;
+  std::vector<int> order;
+  order.push_back(h->wave);
+  for (int w = 0; w < h->n_waves; ++w)
+    if (w != h->wave) order.push_back(w);
+  for (int w : order) {
+    if (w != h->wave || !h->wave_current) {
+      reset_wave(h, w);
+      for (const RecordedLayer& r : h->history) {
+        lemps_layer L;
+        L.n_gates = (int32_t)r.left_qubit.size();
+        L.left_qubit = r.left_qubit.data();
+        L.gates = r.gates.data();
+        L.n_kraus = r.n_kraus;
+        L.kraus = r.kraus.data();
+        L.coin_p = r.coin_p;
+        const lemps_status st = (h->prec == LEMPS_FP64) ? apply_layer_t<double>(h, &L) : apply_layer_t<float>(h, &L);
+        if (st != LEMPS_OK) return st;
+      }
+      h->wave_current = true;
+    }
+    const int64_t off = (int64_t)w * h->Bcap, bw = h->B;
+    std::vector<double> zm(n), zs(n), zzm(n > 1 ? n - 1 : 1), zzs(n > 1 ? n - 1 : 1);
+    lemps_measurement mw{};
+    mw.z = m->z ? m->z + off * n : nullptr;
+    mw.zz = m->zz ? m->zz + off * (n - 1) : nullptr;
+    mw.s_half = m->s_half ? m->s_half + off : nullptr;
+    mw.eps_bound = m->eps_bound ? m->eps_bound + off : nullptr;
+    mw.status = m->status ? m->status + off : nullptr;
+    mw.z_mean = zm.data();
+    mw.z_stderr = zs.data();
+    mw.zz_mean = zzm.data();
+    mw.zz_stderr = zzs.data();
+    const lemps_status st = measure_resident(&mw);
+    if (st != LEMPS_OK && st != LEMPS_ENUMERIC) return st;
+    failed += mw.n_failed;
+    // the wave's column statistics: mean and M2 = se^2 (B - 1) B
+    std::vector<double> wm(ncol), ws(ncol);
+    for (int i = 0; i < n; ++i) { wm[i] = zm[i]; ws[i] = zs[i]; }
+    for (int i = 0; i + 1 < n; ++i) { wm[n + i] = zzm[i]; ws[n + i] = zzs[i]; }
+    wm[2 * n - 1] = mw.s_half_mean; ws[2 * n - 1] = mw.s_half_stderr;
+    wm[2 * n] = mw.eps_hat; ws[2 * n] = 0.0;
+    for (int c = 0; c < ncol; ++c) {
+      const double m2w = ws[c] * ws[c] * (double)(bw - 1) * (double)bw;
+      if (count == 0) {
+        mean[c] = wm[c];
+        m2[c] = m2w;
+      } else {
+        const double tot = (double)(count + bw), d = wm[c] - mean[c];
+        mean[c] += d * (double)bw / tot;
+        m2[c] += m2w + d * d * (double)count * (double)bw / tot;
+      }
+    }
+    count += bw;
+  }
+  auto se = [&](int c) { return count > 1 ? std::sqrt(m2[c] / (double)(count - 1) / (double)count) : 0.0; };
+  for (int i = 0; i < n; ++i) { m->z_mean[i] = mean[i]; m->z_stderr[i] = se(i); }
+  for (int i = 0; i + 1 < n; ++i) { m->zz_mean[i] = mean[n + i]; m->zz_stderr[i] = se(n + i); }
+  m->s_half_mean = mean[2 * n - 1];
+  m->s_half_stderr = se(2 * n - 1);
+  m->eps_hat = mean[2 * n];
+  m->eps_buffer = std::sqrt(h->cfg.eps_max * h->cfg.eps_max / (2.0 * (double)count) * std::log(1.0 / 0.05));
+  m->n_failed = failed;
+  return failed ? fail(LEMPS_ENUMERIC, "measure: some trajectories flagged a numerical failure") : LEMPS_OK;
+}
+
+lemps_status sim_waves(lemps_handle h, int64_t* wave_size, int32_t* n_waves) {
+  if (!h || !wave_size || !n_waves) return fail(LEMPS_EINVAL, "sim_waves: null argument");
+  *wave_size = h->Bcap;
+  *n_waves = h->n_waves;
+  return LEMPS_OK;
 }
 
 lemps_status sim_export_mps(lemps_handle h, int64_t traj, int32_t* bond_dims, double* tensors) {
   if (!h || !bond_dims || !tensors || traj < 0 || traj >= h->B) return fail(LEMPS_EINVAL, "sim_export_mps: bad argument");
+  if (h->n_waves > 1) return fail(LEMPS_ESTATE, "sim_export_mps: the handle runs in waves; per-trajectory inspection needs n_traj <= max_traj_in_flight");
   if (h->sticky) return fail(LEMPS_ECUDA, "sim_export_mps: sticky CUDA error");
   const int n = h->n;
   if (cudaMemcpyAsync(bond_dims, h->bond + traj * (n + 1), sizeof(int32_t) * (n + 1), cudaMemcpyDeviceToHost, h->stream) !=

@@ -26,7 +26,7 @@ UNRAVEL_MODES = {"optimal": LEMPS_UNRAVEL_OPTIMAL, "given": LEMPS_UNRAVEL_GIVEN,
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 
-EXPORTED = ["sim_create", "apply_layer", "unravel_opt", "sample_branch", "measure", "sim_export_mps",
+EXPORTED = ["sim_create", "apply_layer", "unravel_opt", "sample_branch", "measure", "sim_export_mps", "sim_waves",
             "sim_sync", "sim_profile", "destroy", "unravel_grad", "unravel_descend", "unravel_grad_noalloc",
             "sample_bitstrings", "eps_concentrated", "lemps_last_error"]
 KERNEL_KINDS = ["move", "contract", "unravel", "gram", "eig", "split", "other"]
@@ -43,7 +43,8 @@ class Config(ctypes.Structure):
                 ("n_traj", ctypes.c_int64), ("traj_offset", ctypes.c_int64), ("seed", ctypes.c_uint64),
                 ("precision", ctypes.c_int32), ("unravel_mode", ctypes.c_int32), ("log_capacity", ctypes.c_int32),
                 ("eps_max", ctypes.c_double), ("cuda_stream", ctypes.c_void_p), ("alloc", ALLOC_FN),
-                ("free", FREE_FN), ("alloc_ctx", ctypes.c_void_p), ("layering", ctypes.c_int32)]
+                ("free", FREE_FN), ("alloc_ctx", ctypes.c_void_p), ("layering", ctypes.c_int32),
+                ("max_traj_in_flight", ctypes.c_int64)]
 
 
 class LayerStruct(ctypes.Structure):
@@ -91,6 +92,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     lib.sample_bitstrings.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_uint8)]
     lib.eps_concentrated.argtypes = [vp, i32, ctypes.c_double, dp, dp]
     lib.sim_sync.argtypes = [vp]
+    lib.sim_waves.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i32)]
     lib.sim_profile.argtypes = [vp, i32, dp, ctypes.POINTER(i64)]
     lib.destroy.argtypes = [vp]
     lib.unravel_grad.argtypes = [vp, i32, i64, i32, vp, vp, vp, vp, vp, vp]
@@ -125,7 +127,7 @@ class Simulation:
     def __init__(self, n_qubits: int, chi_max: int, n_traj: int, seed: int = 0, precision: str = "fp64",
                  unravel: str = "optimal", cutoff: Optional[float] = None, traj_offset: int = 0,
                  log_capacity: int = 0, eps_max: float = 4.0, stream=None, torch_allocator: bool = True,
-                 layering: str = "local"):
+                 layering: str = "local", max_traj_in_flight: int = 0):
         torch = _require_cuda()
         lib = load()
         self.n, self.chi, self.B = int(n_qubits), int(chi_max), int(n_traj)
@@ -145,6 +147,7 @@ class Simulation:
         cfg.layering = LAYERINGS[layering]
         cfg.log_capacity = int(log_capacity)
         cfg.eps_max = float(eps_max)
+        cfg.max_traj_in_flight = int(max_traj_in_flight)
         cfg.cuda_stream = self.stream.cuda_stream
         self._cb = None
         if torch_allocator:
@@ -228,6 +231,12 @@ class Simulation:
             out.append(z[off:off + size].reshape(bonds[k], 2, bonds[k + 1]).copy())
             off += size
         return out, bonds
+
+    def waves(self):
+        """(wave size, number of waves) of the handle (sim_waves)."""
+        size, count = ctypes.c_int64(0), ctypes.c_int32(0)
+        _check(load().sim_waves(self._h, ctypes.byref(size), ctypes.byref(count)), "sim_waves")
+        return size.value, count.value
 
     def sync(self) -> int:
         return load().sim_sync(self._h)

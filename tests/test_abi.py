@@ -77,7 +77,8 @@ def test_misaligned_allocator_blocks_are_refused_and_freed(lib_path):
     cb = (L.ALLOC_FN(alloc), L.FREE_FN(free))
     cfg = L.Config(n_qubits=8, chi_max=16, trunc_cutoff=1e-12, n_traj=4, traj_offset=0, seed=1,
                    precision=L.LEMPS_MIXED, unravel_mode=L.LEMPS_UNRAVEL_OPTIMAL, log_capacity=0, eps_max=2.0,
-                   cuda_stream=None, alloc=cb[0], free=cb[1], alloc_ctx=None, layering=L.LEMPS_LAYER_LOCAL)
+                   cuda_stream=None, alloc=cb[0], free=cb[1], alloc_ctx=None, layering=L.LEMPS_LAYER_LOCAL,
+                   max_traj_in_flight=4)
     h = ctypes.c_void_p()
     assert lib.sim_create(ctypes.byref(cfg), ctypes.byref(h)) == L.LEMPS_EINVAL
     assert b"16-byte aligned" in lib.lemps_last_error()

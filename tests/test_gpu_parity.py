@@ -403,6 +403,42 @@ def test_traj_offset_shards_reproduce_the_full_run(L):
     assert np.array_equal(np.concatenate([a["z"], b["z"]]), full["z"])
 
 
+# --- waves ------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_waves_equal_one_big_handle(L, precision):
+    """Waves (max_traj_in_flight = 8 of 20 trajectories: waves of 8, 8 and 4)
+    give the results of one handle holding all 20, per trajectory bit for bit
+    (global trajectory ids key the Philox counters), means and standard errors
+    to rounding; a layer applied after a measurement reaches every wave."""
+    circ = I.random_brickwork(8, 6, I.depolarizing_kraus(0.05), seed=3)
+    extra = I.random_brickwork(8, 7, I.depolarizing_kraus(0.05), seed=3).layers[6]
+    cut = 1e-14 if precision == "fp64" else 1e-12
+    one = L.Simulation(8, 8, 20, seed=7, precision=precision, cutoff=cut, traj_offset=5)
+    wav = L.Simulation(8, 8, 20, seed=7, precision=precision, cutoff=cut, traj_offset=5, max_traj_in_flight=8)
+    assert one.waves() == (20, 1) and wav.waves() == (8, 3)
+    for step in range(2):
+        if step == 0:
+            one.run(circ)
+            wav.run(circ)
+        else:
+            one.apply_layer(extra)
+            wav.apply_layer(extra)
+        a, b = one.measure(), wav.measure()
+        for key in ("z", "zz", "s_half", "eps_bound", "status"):
+            assert np.array_equal(a[key], b[key]), (step, key)
+        for key in ("z_mean", "z_stderr", "zz_mean", "zz_stderr"):
+            assert np.allclose(a[key], b[key], rtol=1e-12, atol=1e-14), (step, key)
+        for key in ("s_half_mean", "s_half_stderr", "eps_hat", "eps_buffer"):
+            assert abs(a[key] - b[key]) <= 1e-12 * max(1.0, abs(a[key])), (step, key)
+        assert a["eps_hat"] > 0
+    with pytest.raises(L.LempsError) as e:
+        wav.export_mps(0)
+    assert e.value.status == L.LEMPS_ESTATE
+    one.destroy()
+    wav.destroy()
+
+
 # --- edge cases ---------------------------------------------------------------------
 
 def test_two_qubits_single_trajectory(L):

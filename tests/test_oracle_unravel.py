@@ -189,6 +189,40 @@ def test_takagi_residual(rng):
         assert np.all(np.diff(s) <= 1e-15)
 
 
+def test_unitary_sqrt_is_the_principal_root(rng):
+    """The unitary root squares back, its eigenvalues have arguments in
+    (-pi/2, pi/2] (principal branch, -1 -> +i), and repeated eigenvalues (the
+    degenerate Takagi values of depolarizing noise) cause no loss of accuracy."""
+    cases = [I.haar_unitary(rng, 4) for _ in range(20)]
+    q = I.haar_unitary(rng, 4)
+    cases.append(q @ np.diag(np.exp(1j * np.array([0.3, 0.3, 0.3, -2.0]))) @ q.conj().T)
+    cases.append(q @ np.diag([-1.0, -1.0, 1.0, 1j]) @ q.conj().T)
+    cases.append(np.eye(4, dtype=complex))
+    for w in cases:
+        r = U.unitary_sqrt(w)
+        assert np.allclose(r @ r, w, atol=1e-13)
+        assert np.allclose(r.conj().T @ r, np.eye(4), atol=1e-13)
+        ang = np.angle(np.linalg.eigvals(r))
+        assert np.all(ang > -np.pi / 2 - 1e-9) and np.all(ang <= np.pi / 2 + 1e-9)
+    r = U.unitary_sqrt(-np.eye(2, dtype=complex))
+    assert np.allclose(r, 1j * np.eye(2), atol=1e-15)
+
+
+def test_degenerate_depolarizing_inputs_raise_no_warning():
+    """Bell target (reduced state I/2) and depolarizing channels, whose Takagi
+    values are degenerate by construction: the optimal unraveling is computed
+    without any numerical warning and reaches the closed-form E_oF."""
+    import warnings
+    for p in (0.02, 0.3, 1.0):
+        kr = I.depolarizing_kraus(p)
+        with warnings.catch_warnings():
+            warnings.simplefilter("error")
+            out, _ = U.optimal_unraveling(np.eye(2, dtype=complex) / 2, kr)
+            e = U.unraveling_entropy(out, np.eye(2, dtype=complex) / 2)
+        assert np.allclose(sum(k.conj().T @ k for k in out), np.eye(2), atol=1e-12)
+        assert e >= -1e-14
+
+
 def test_separable_angles_close_the_polygon(rng):
     """sum_j exp(2 i theta_j) lam_j = 0 (Eq. separating_angles_condition) for
     descending lam with lam_1 <= lam_2 + lam_3 + lam_4, including triangles

@@ -59,3 +59,49 @@ def test_replica_ranges_and_reduction():
         spans = sorted(span for ranks in gathered for span in ranks)
         for (a0, a1), (b0, b1) in zip(spans, spans[1:]):
             assert a1 <= b0, spans
+
+
+def _merge_worker(rank, world, port, out):
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    from paper_2508_05745_gb300 import replicas as RP
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        rng = np.random.default_rng(17)
+        data = rng.standard_normal((20, 6)) * np.logspace(-8, 2, 6)   # per-trajectory observables
+        split = [0, 7, 20]                                            # uneven: 7 and 13 trajectories
+        mine = data[split[rank]:split[rank + 1]]
+        # the rank's trajectories sit in two handles (sizes of a batch)
+        mean, se = RP.merged_observables(dist, [mine[:3], mine[3:]])
+        out.put((rank, mean, se))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_observable_merge_is_exact_over_ranks():
+    """Two gloo ranks hold 7 and 13 trajectories of synthetic per-trajectory
+    observables (spread over two handles each); the merged mean and standard
+    error equal the single-process merge bit for bit, and a plain numpy
+    estimate to rounding."""
+    import numpy as np
+    from paper_2508_05745_gb300 import replicas as RP
+    world = 2
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_merge_worker, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    results = [q.get(timeout=120) for _ in range(world)]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    rng = np.random.default_rng(17)
+    data = rng.standard_normal((20, 6)) * np.logspace(-8, 2, 6)
+    ref_mean, ref_se = RP.finalize(RP.exact_sums(data))
+    for rank, mean, se in results:
+        assert np.array_equal(mean, ref_mean) and np.array_equal(se, ref_se), rank
+    assert np.allclose(ref_mean, data.mean(axis=0), rtol=1e-14, atol=0)
+    assert np.allclose(ref_se, data.std(axis=0, ddof=1) / np.sqrt(20), rtol=1e-12, atol=0)
