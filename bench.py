@@ -337,15 +337,33 @@ class Arm:
         self.sims = {}
 
 
-def observable_error(res_m, res_d):
-    """Per-observable |mixed - FP64| over trajectories with the same ids, and
-    the largest |mean_mixed - mean_FP64| / combined standard error."""
+def branch_logs(arm):
+    """Sampled branch of every noise site since the handles were created,
+    [B, 2 gates] per size."""
+    out = {}
+    for n, s in arm.sims.items():
+        cols = [s.sample_branch(g, slot) for g in range(s.gates_applied) for slot in (0, 1)]
+        out[n] = np.stack(cols, axis=1) if cols else np.zeros((s.B, 0), np.int32)
+    return out
+
+
+def observable_error(res_m, res_d, br_m=None, br_d=None):
+    """Per-observable |mixed - FP64| over trajectories with the same ids whose
+    sampled branches agree at every noise site (a branch can flip where a
+    uniform falls within rounding of a cumulative weight), the number of
+    trajectories whose branches differ, and the largest |mean_mixed -
+    mean_FP64| / combined standard error over all trajectories."""
     errs = {"z": [], "zz": [], "s_half": []}
     zmax = 0.0
+    divergent = 0
     for n, rd in res_d.items():
         rm = res_m[n]
+        same = np.ones(len(rd["z"]), bool)
+        if br_m is not None:
+            same = np.all(br_m[n] == br_d[n], axis=1)
+            divergent += int(np.sum(~same))
         for k in errs:
-            errs[k].append(np.abs(rm[k] - rd[k]).ravel())
+            errs[k].append(np.abs(rm[k] - rd[k])[same].ravel())
         for k, km, ks in (("z", "z_mean", "z_stderr"), ("zz", "zz_mean", "zz_stderr")):
             se = np.sqrt(rm[ks] ** 2 + rd[ks] ** 2)
             ok = se > 0
@@ -359,6 +377,7 @@ def observable_error(res_m, res_d):
         v = np.concatenate(v) if v else np.zeros(1)
         out[k] = {"median_abs": float(np.median(v)), "max_abs": float(np.max(v))}
     out["max_mean_z_score"] = zmax
+    out["branch_divergent_trajectories"] = divergent
     return out
 
 
@@ -600,13 +619,15 @@ def main():
         fp64_info = {"trajectories": sum(bf.values()), "by_n": bf, "timed_steps": k64, "ms_per_step": d_ms / k64}
         log(f"fp64 arm: {d_upd} updates in {d_ms:.1f} ms")
         res_d = d.measure()
+        br_d = branch_logs(d)
         d.destroy()
         mm = Arm(L, torch, w, bf, "mixed", args, offsets=offsets)
         mm.warmup(min(args.warmup, 1))
         mm.timed(k64)
         res_m = mm.measure()
+        br_m = branch_logs(mm)
         mm.destroy()
-        obs_err = observable_error(res_m, res_d)
+        obs_err = observable_error(res_m, res_d, br_m, br_d)
         log("observable error done")
     rl = roofline(prof, work, MIXED_PIPE)
     total_prof = sum(v[0] for v in prof.values())

@@ -266,7 +266,10 @@ lemps_status unravel_descend(const double* rho_a, const double* p, int64_t batch
  * at most 16384 problems (1 MiB), which every GPU that loads the library holds
  * until the process exits.  batch > 16384 returns LEMPS_EINVAL.  The first call
  * on a device looks up the array's device address (cudaGetSymbolAddress) with
- * that device current, so make that first call before any stream capture.  All
+ * that device current, so make that first call before any stream capture.  The
+ * address is kept for the life of the process: after a cudaDeviceReset (or
+ * anything else that recreates the device's primary context) it is stale, so
+ * do not call this entry point again on that device in the same process.  All
  * calls on one device share its copy of the array, which keeps the last call's
  * contents: calls that overlap on the same GPU (e.g. on different streams) race
  * and must be ordered by the caller.  No cudaMalloc, cudaFree or other

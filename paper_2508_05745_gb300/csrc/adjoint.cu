@@ -85,7 +85,9 @@ extern "C" lemps_status unravel_grad_noalloc(const void* theta, int32_t theta_fp
   void* scratch = nullptr;
   {
     // First call on a device: look up the array's device address with that
-    // device current.  In host code the symbol itself is only a stand-in.
+    // device current.  In host code the symbol itself is only a stand-in.  The
+    // address is cached for the process: a cudaDeviceReset would leave it
+    // stale (the header tells callers not to use this entry point after one).
     std::lock_guard<std::mutex> lk(g_noalloc_mu);
     if (!g_noalloc_ptr[dev]) {
       e = cudaGetSymbolAddress(&scratch, g_noalloc_rho);

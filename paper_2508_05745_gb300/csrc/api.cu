@@ -32,12 +32,15 @@ constexpr int kThreads = 256;
 constexpr int kEpsHistLayers = 256;
 
 // A layer as applied, kept on the host so that the waves that are not
-// resident can be brought to the same point later.
+// resident can be brought to the same point later; centre_sweep marks a
+// measurement instead, whose centre moves (to site 0, then along the chain)
+// the replay repeats so that every wave sees the same sequence of operations.
 struct RecordedLayer {
   std::vector<int32_t> left_qubit;
   std::vector<double> gates, kraus;
   int32_t n_kraus = 0;
   double coin_p = 1.0;
+  bool centre_sweep = false;
 };
 
 struct lemps_sim {
@@ -695,6 +698,11 @@ lemps_status measure(lemps_handle h, lemps_measurement* m) {
     if (w != h->wave || !h->wave_current) {
       reset_wave(h, w);
       for (const RecordedLayer& r : h->history) {
+        if (r.centre_sweep) {
+          if (h->prec == LEMPS_FP64) { move_center_to<double>(h, 0); move_center_to<double>(h, h->n - 1); }
+          else { move_center_to<float>(h, 0); move_center_to<float>(h, h->n - 1); }
+          continue;
+        }
         lemps_layer L;
         L.n_gates = (int32_t)r.left_qubit.size();
         L.left_qubit = r.left_qubit.data();
@@ -740,6 +748,11 @@ lemps_status measure(lemps_handle h, lemps_measurement* m) {
       }
     }
     count += bw;
+  }
+  {
+    RecordedLayer sweep;
+    sweep.centre_sweep = true;
+    h->history.push_back(std::move(sweep));
   }
   auto se = [&](int c) { return count > 1 ? std::sqrt(m2[c] / (double)(count - 1) / (double)count) : 0.0; };
   for (int i = 0; i < n; ++i) { m->z_mean[i] = mean[i]; m->z_stderr[i] = se(i); }

@@ -707,7 +707,10 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
     // Safeguarded Newton on det(T - x I) inside the bracket [lo, hi] from the
     // grid: each round evaluates the Sturm count and S = d/dx ln|det| at the
     // iterate x_n, moves one end of the bracket to x_n, and steps to x_n -
-    // 1 / S, or to the bracket midpoint when that leaves the bracket.  A
+    // 1 / S, or to the bracket midpoint when that leaves the bracket or does
+    // not at least halve the previous step (at a repeated eigenvalue Newton
+    // converges only linearly, from one side, and the far end of the bracket
+    // would never move).  A
     // Newton step below tol / 4 only says that x_n is near some eigenvalue,
     // possibly a neighbour just outside the bracket, so the next point is then
     // x_n +/- tol / 2 on the side where the count puts eigenvalue k: when it
@@ -716,7 +719,8 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
     // (normalized: 4 eps): as accurate as the backward-stable reduction from
     // G allows (a few eps ||G|| absolute), which is all that the shifts of the
     // inverse iteration and the entropies need.  From the 5 % grid brackets
-    // this takes about ten rounds (at most fifteen for a warp of 32).
+    // this takes about nine rounds (at most twelve for a warp of 32); a
+    // multiplicity of 32 takes about seventy.
     const double tol = 4.0 * eps + pivmin;
     constexpr int kNewtonWarps = 4;
     if (warp < kNewtonWarps) {
@@ -736,7 +740,7 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
           if (b < (int)blockDim.x) hi = gx[b];
         }
         bool done = k >= keep;
-        double xn = 0.5 * (lo + hi);
+        double xn = 0.5 * (lo + hi), prev = INFINITY;   // prev: the last accepted Newton step
         for (int it = 0; it < 300; ++it) {
           if (hi - lo <= tol) done = true;
           if (__all_sync(0xffffffffu, done)) break;
@@ -747,8 +751,18 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
           else hi = xn;
           const double step = (S != 0.0) ? -1.0 / S : 0.0;
           double xnew = xn + step;
-          if (S != 0.0 && fabs(step) <= 0.25 * tol) xnew = xn + (up ? 0.5 * tol : -0.5 * tol);
-          if (!(S != 0.0 && xnew > lo && xnew < hi)) xnew = 0.5 * (lo + hi);
+          if (S != 0.0 && fabs(step) <= 0.25 * tol) {
+            xnew = xn + (up ? 0.5 * tol : -0.5 * tol);
+            prev = INFINITY;
+            if (!(xnew > lo && xnew < hi)) xnew = 0.5 * (lo + hi);
+          } else if (S != 0.0 && xnew > lo && xnew < hi && fabs(step) <= 0.5 * prev) {
+            prev = fabs(step);
+          } else {
+            // Newton left the bracket or did not halve its step (a repeated
+            // eigenvalue, where it converges only linearly from one side): bisect
+            xnew = 0.5 * (lo + hi);
+            prev = INFINITY;
+          }
           xn = xnew;
         }
         const double val = 0.5 * (lo + hi);

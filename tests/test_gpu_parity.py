@@ -403,6 +403,46 @@ def test_traj_offset_shards_reproduce_the_full_run(L):
     assert np.array_equal(np.concatenate([a["z"], b["z"]]), full["z"])
 
 
+# --- degenerate entanglement spectrum ---------------------------------------------------
+
+def nested_bell_circuit(n_pairs):
+    """2 n_pairs qubits; pair i (qubits i, 2 n_pairs - 1 - i) in a Bell state for
+    every i, so all n_pairs pairs cross the middle bond: its Schmidt spectrum
+    is 2^n_pairs equal values and S(n/2) = n_pairs ln 2.  Each pair is made
+    on the middle bond (H, then CNOT) and swapped outwards; no noise (the
+    identity as the one Kraus operator, sampled as given)."""
+    n = 2 * n_pairs
+    mid = n_pairs - 1
+    h = np.array([[1, 1], [1, -1]], dtype=complex) / np.sqrt(2)
+    cnot = np.array([[1, 0, 0, 0], [0, 1, 0, 0], [0, 0, 0, 1], [0, 0, 1, 0]], dtype=complex)
+    bell = cnot @ np.kron(h, np.eye(2))
+    swap = np.array([[1, 0, 0, 0], [0, 0, 1, 0], [0, 1, 0, 0], [0, 0, 0, 1]], dtype=complex)
+    ident = np.eye(2, dtype=complex)[None]
+    layers = []
+    for r in range(n_pairs):
+        layers.append(I.Layer(np.array([mid], np.int32), bell[None], ident))
+        target = r   # the pair moves out to (r, n - 1 - r)
+        for step in range(mid - target):
+            a, b = mid - 1 - step, mid + 1 + step
+            layers.append(I.Layer(np.array([a, b], np.int32), np.stack([swap, swap]), ident))
+    return I.Circuit(n, layers)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("mixed", 1e-4)])
+def test_half_chain_entropy_of_a_flat_spectrum(L, precision, tol):
+    """Six Bell pairs across the middle bond: 64 equal Schmidt values, S(n/2) =
+    6 ln 2 and <Z_i> = 0 exactly (a closed form; the eigensolver meets an
+    eigenvalue of multiplicity 64)."""
+    circ = nested_bell_circuit(6)
+    sim = L.Simulation(12, 64, 4, seed=1, precision=precision, unravel="given")
+    sim.run(circ)
+    res = sim.measure()
+    sim.destroy()
+    assert res["n_failed"] == 0
+    assert np.allclose(res["s_half"], 6 * np.log(2), atol=tol, rtol=0), res["s_half"] - 6 * np.log(2)
+    assert np.allclose(res["z"], 0.0, atol=tol)
+
+
 # --- waves ------------------------------------------------------------------------------
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
