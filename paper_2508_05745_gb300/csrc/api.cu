@@ -1,6 +1,7 @@
 // C ABI of the library (include/lemps.h): device allocation, layer
 // orchestration and the measure/export calls.  All arithmetic runs in the
 // kernels of mps_kernels.cuh and unravel.cuh; the host only schedules them.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -94,6 +95,11 @@ struct lemps_sim {
   int64_t gates_done = 0;
   int center = 0;
   size_t mps_bytes = 0;
+  // Tensor-core contraction (mixed precision): TMA maps of every site k with
+  // cap[k], cap[k+1] >= 64, viewed as [2 cap[k]][cap[k+1]] complex64 rows over
+  // all trajectories, with the A box (16 x 128) and the B box (cap[k+1] x 32).
+  std::vector<CUtensorMap> map_a, map_b;
+  std::vector<char> tc_site;
   bool profiling = false;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof;  // (kind, (start, stop))
   double prof_ms[LEMPS_NUM_KERNEL_KINDS] = {0};
@@ -175,6 +181,40 @@ struct lemps_sim {
 
 namespace {
 
+typedef CUresult (*TensorMapEncodeFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                      const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                      CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library).
+TensorMapEncodeFn tensor_map_encoder() {
+  static TensorMapEncodeFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    cudaDriverEntryPointQueryResult q;
+    void* p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<TensorMapEncodeFn>(p);
+  }
+  return fn;
+}
+
+// 3-D map over (column, row, trajectory) of the complex64 rows of one site:
+// cols x rows per trajectory, 8-byte elements, trajectory stride cols * rows.
+bool encode_site_map(CUtensorMap* m, void* base, int cols, int rows, int64_t ntraj, int box0, int box1) {
+  TensorMapEncodeFn fn = tensor_map_encoder();
+  if (!fn) return false;
+  const cuuint64_t dim[3] = {(cuuint64_t)cols, (cuuint64_t)rows, (cuuint64_t)ntraj};
+  const cuuint64_t str[2] = {(cuuint64_t)cols * 8, (cuuint64_t)cols * 8 * (cuuint64_t)rows};
+  const cuuint32_t box[3] = {(cuuint32_t)box0, (cuuint32_t)box1, 1};
+  const cuuint32_t es[3] = {1, 1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_INT64, 3, base, dim, str, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+         CUDA_SUCCESS;
+}
+
 lemps_status check_cuda(lemps_sim* h, const char* where) {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
@@ -237,6 +277,26 @@ void launch_heev(lemps_sim* h, int q, int mode, double cutoff, int keep_max, int
   });
 }
 
+// Two-site contraction of the pair (q, q+1): on the tensor cores in mixed
+// precision when all three site capacities are >= 64, else the SIMT kernel.
+template <class R>
+void launch_contract(lemps_sim* h, int q) {
+  SimView<R> sv = h->view<R>();
+  if (sizeof(R) == 4 && !h->tc_site.empty() && h->tc_site[q] && h->tc_site[q + 1]) {
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_contract_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kSmemBytes);
+      attr = true;
+    }
+    h->timed(LEMPS_K_CONTRACT, [&] {
+      k_contract_tc<<<(unsigned)h->B, tc::kThreads, tc::kSmemBytes, h->stream>>>(
+          h->map_a[q], h->map_b[q + 1], h->view<float>(), q);
+    });
+    return;
+  }
+  h->timed(LEMPS_K_CONTRACT, [&] { k_contract<R><<<(unsigned)h->B, kThreads, 0, h->stream>>>(sv, q); });
+}
+
 template <class R>
 lemps_status apply_layer_t(lemps_sim* h, const lemps_layer* L) {
   const int ng = L->n_gates;
@@ -278,7 +338,7 @@ lemps_status apply_layer_t(lemps_sim* h, const lemps_layer* L) {
                        int keep_max, int side) {
     if (h->center < q) move_center_to<R>(h, q);
     else if (h->center > q + 1) move_center_to<R>(h, q + 1);
-    h->timed(LEMPS_K_CONTRACT, [&] { k_contract<R><<<(unsigned)h->B, kThreads, 0, h->stream>>>(sv, q); });
+    launch_contract<R>(h, q);
     LayerDev ld;
     ld.gates = gate;
     ld.kraus = kset_d;
@@ -371,7 +431,7 @@ lemps_status measure_t(lemps_sim* h, lemps_measurement* m) {
   move_center_to<R>(h, 0);
   const int hb = n / 2;  // bond n/2 lies between sites hb-1 and hb
   for (int q = 0; q + 1 < n; ++q) {
-    k_contract<R><<<(unsigned)B, kThreads, 0, h->stream>>>(sv, q);
+    launch_contract<R>(h, q);
     k_obs_from_rho12<<<grid_t, kThreads, 0, h->stream>>>(h->rho12, B, n, q, z, zz);
     if (q == hb - 1) {
       k_site_gram<R><<<(unsigned)B, kThreads, 0, h->stream>>>(sv, q);
@@ -528,6 +588,24 @@ lemps_status sim_create(const lemps_config* cfg, lemps_handle* out) {
               : fail(LEMPS_ENOMEM, "sim_create: device allocation failed");
   }
   h->mps_bytes = h->elem * tot;
+  if (h->prec == LEMPS_MIXED) {
+    // tensor maps of the sites the tensor-core contraction can take
+    h->map_a.resize(n);
+    h->map_b.resize(n);
+    h->tc_site.assign(n, 0);
+    for (int k = 0; k < n; ++k) {
+      const int rows = 2 * h->cap_h[k], cols = h->cap_h[k + 1];
+      if (h->cap_h[k] < 64 || cols < 64 || cols > 128) continue;
+      void* base = (char*)h->mps + h->off_h[k] * h->elem;
+      if (!encode_site_map(&h->map_a[k], base, cols, rows, h->Bcap, tc::kKC, tc::kM) ||
+          !encode_site_map(&h->map_b[k], base, cols, rows, h->Bcap, cols, 2 * tc::kKC)) {
+        h->release();
+        delete h;
+        return fail(LEMPS_ECUDA, "sim_create: cuTensorMapEncodeTiled is unavailable or refused a site map");
+      }
+      h->tc_site[k] = 1;
+    }
+  }
   cudaMemcpyAsync(h->site_off, h->off_h.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice, h->stream);
   cudaMemcpyAsync(h->cap, h->cap_h.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice, h->stream);
   {

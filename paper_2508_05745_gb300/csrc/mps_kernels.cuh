@@ -12,6 +12,7 @@
 #include "common.cuh"
 #include "heev.cuh"
 #include "gemm.cuh"
+#include "tc_contract.cuh"
 
 namespace lemps {
 
@@ -481,27 +482,12 @@ __global__ void __launch_bounds__(kGemmThreads, sizeof(R) == 4 ? 2 : 1) k_move_c
 // Theta[a][s1][s2][b] = sum_m A_q[a][s1][m] A_{q+1}[m][s2][b] into ws0 as a
 // (2 dl) x (2 dr) row-major matrix; rho12[(s1 s2), (t1 t2)] =
 // sum_{a,b} Theta[a,s1,s2,b] conj(Theta[a,t1,t2,b]) in FP64.
+// rho12[(s1 s2), (t1 t2)] = sum_{a,b} Theta[a,s1,s2,b] conj(Theta[a,t1,t2,b]) in
+// FP64 from the two-site tensor in ws0 (row-major, ld = 2 dr).
 template <class R>
-__global__ void __launch_bounds__(kGemmThreads) k_contract(SimView<R> s, int q) {
-  const int64_t t = blockIdx.x;
-  if (t >= s.B) return;
-  __shared__ double red[32];
-  __shared__ GemmSmem<R> sm;
-  const int32_t* bd = s.bond + t * (s.n + 1);
-  const int dl = bd[q], dm = bd[q + 1], dr = bd[q + 2];
-  const int capm = s.cap[q + 1], capr = s.cap[q + 2];
-  const cpx<R>* A = site_ptr(s, q, t);
-  const cpx<R>* B = site_ptr(s, q + 1, t);
-  cpx<R>* th = s.ws0 + t * s.ws_stride;
+__device__ __forceinline__ void contract_rho12(const SimView<R>& s, int64_t t, const cpx<R>* th, int dl, int dr,
+                                               double* red) {
   const int64_t ld = 2 * dr;
-  cta_gemm<R, true, false>(
-      2 * dl, 2 * dr, dm, [&](int i, int k) { return A[(int64_t)i * capm + k]; },
-      [&](int k, int j) {
-        const int s2 = j >= dr, b = j - s2 * dr;   // j < 2 dr
-        return B[(int64_t)(2 * k + s2) * capr + b];
-      },
-      [&](int i, int j, cpx<R> v) { th[(int64_t)i * ld + j] = v; }, sm);
-  __syncthreads();
   // rho12 is Hermitian: the 10 entries i <= j are formed.  Products in the
   // storage precision, partial sums over 8 entries of Theta in that
   // precision, accumulated in FP64 (FP64 throughput is ~1/64 of FP32 here).
@@ -549,6 +535,78 @@ __global__ void __launch_bounds__(kGemmThreads) k_contract(SimView<R> s, int q) 
         if (j != i) s.rho12[t * 16 + j * 4 + i] = mk(re, -im);
       }
     }
+}
+
+template <class R>
+__global__ void __launch_bounds__(kGemmThreads) k_contract(SimView<R> s, int q) {
+  const int64_t t = blockIdx.x;
+  if (t >= s.B) return;
+  __shared__ double red[32];
+  __shared__ GemmSmem<R> sm;
+  const int32_t* bd = s.bond + t * (s.n + 1);
+  const int dl = bd[q], dm = bd[q + 1], dr = bd[q + 2];
+  const int capm = s.cap[q + 1], capr = s.cap[q + 2];
+  const cpx<R>* A = site_ptr(s, q, t);
+  const cpx<R>* B = site_ptr(s, q + 1, t);
+  cpx<R>* th = s.ws0 + t * s.ws_stride;
+  const int64_t ld = 2 * dr;
+  cta_gemm<R, true, false>(
+      2 * dl, 2 * dr, dm, [&](int i, int k) { return A[(int64_t)i * capm + k]; },
+      [&](int k, int j) {
+        const int s2 = j >= dr, b = j - s2 * dr;   // j < 2 dr
+        return B[(int64_t)(2 * k + s2) * capr + b];
+      },
+      [&](int i, int j, cpx<R> v) { th[(int64_t)i * ld + j] = v; }, sm);
+  __syncthreads();
+  contract_rho12(s, t, th, dl, dr, red);
+}
+
+// The same contraction on the tensor cores (mixed precision; 3xTF32 complex
+// GEMM, tc_contract.cuh) for gates whose site capacities are all >= 64: mapA
+// views site q as [2 cap_q][cap_{q+1}] complex64 rows, mapB site q + 1 as
+// [2 cap_{q+1}][cap_{q+2}], both over all trajectories.  One CTA per
+// trajectory holding all 512 tensor-memory columns (at most one CTA per SM).
+__global__ void __launch_bounds__(tc::kThreads, 1) k_contract_tc(const __grid_constant__ CUtensorMap mapA,
+                                                                 const __grid_constant__ CUtensorMap mapB,
+                                                                 SimView<float> s, int q) {
+  const int64_t t = blockIdx.x;
+  if (t >= s.B) return;
+  extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
+  unsigned char* sm = reinterpret_cast<unsigned char*>(((uintptr_t)tc_smem_raw + 1023) & ~(uintptr_t)1023);
+  __shared__ __align__(8) uint64_t bars[2];
+  __shared__ uint32_t s_tmem;
+  __shared__ double red[32];
+  const int warp = threadIdx.x >> 5;
+  const int32_t* bd = s.bond + t * (s.n + 1);
+  const int dl = bd[q], dm = bd[q + 1], dr = bd[q + 2];
+  const int capr = s.cap[q + 2];
+  cpx<float>* th = s.ws0 + t * s.ws_stride;
+  if (threadIdx.x == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_addr(&s_tmem))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_for_bulk_copies();
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = s_tmem;
+  uint32_t phase[2] = {0u, 0u};
+  bool ok = true;
+  const int M = 2 * dl;
+  for (int m0 = 0; m0 < M && ok; m0 += tc::kM)
+    ok = tc::gemm_tile(&mapA, &mapB, (int)t, m0, M, dm, dr, capr, sm, bars, phase, tmem, th, 2 * dr);
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
+  if (!ok) {
+    if (threadIdx.x == 0) atomicOr(s.status + t, (int32_t)TS_COPY);
+    return;
+  }
+  contract_rho12(s, t, th, dl, dr, red);
 }
 
 // ---- apply T to Theta and build the Gram matrix ------------------------------
