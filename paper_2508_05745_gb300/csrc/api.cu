@@ -203,16 +203,16 @@ TensorMapEncodeFn tensor_map_encoder() {
 
 // 3-D map over (column, row, trajectory) of the complex64 rows of one site:
 // cols x rows per trajectory, 8-byte elements, trajectory stride cols * rows.
-bool encode_site_map(CUtensorMap* m, void* base, int cols, int rows, int64_t ntraj, int box0, int box1) {
+bool encode_site_map(CUtensorMap* m, void* base, int cols, int rows, int64_t ntraj, int box0, int box1,
+                     CUtensorMapSwizzle swizzle) {
   TensorMapEncodeFn fn = tensor_map_encoder();
   if (!fn) return false;
   const cuuint64_t dim[3] = {(cuuint64_t)cols, (cuuint64_t)rows, (cuuint64_t)ntraj};
   const cuuint64_t str[2] = {(cuuint64_t)cols * 8, (cuuint64_t)cols * 8 * (cuuint64_t)rows};
   const cuuint32_t box[3] = {(cuuint32_t)box0, (cuuint32_t)box1, 1};
   const cuuint32_t es[3] = {1, 1, 1};
-  return fn(m, CU_TENSOR_MAP_DATA_TYPE_INT64, 3, base, dim, str, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
-         CUDA_SUCCESS;
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_INT64, 3, base, dim, str, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 lemps_status check_cuda(lemps_sim* h, const char* where) {
@@ -278,7 +278,8 @@ void launch_heev(lemps_sim* h, int q, int mode, double cutoff, int keep_max, int
 }
 
 // Two-site contraction of the pair (q, q+1): on the tensor cores in mixed
-// precision when all three site capacities are >= 64, else the SIMT kernel.
+// precision when all three site capacities lie in [64, 128] (and are even),
+// else the SIMT kernel.
 template <class R>
 void launch_contract(lemps_sim* h, int q) {
   SimView<R> sv = h->view<R>();
@@ -589,16 +590,19 @@ lemps_status sim_create(const lemps_config* cfg, lemps_handle* out) {
   }
   h->mps_bytes = h->elem * tot;
   if (h->prec == LEMPS_MIXED) {
-    // tensor maps of the sites the tensor-core contraction can take
+    // tensor maps of the sites the tensor-core contraction can take: site k
+    // as the left operand (box of 8 complex columns x 128 rows, 64-byte
+    // swizzle: two M tiles cover 2 cap_k <= 256 rows) and as the right
+    // operand (box of all cap_{k+1} <= 128 columns x 16 rows 2k' + s)
     h->map_a.resize(n);
     h->map_b.resize(n);
     h->tc_site.assign(n, 0);
     for (int k = 0; k < n; ++k) {
       const int rows = 2 * h->cap_h[k], cols = h->cap_h[k + 1];
-      if (h->cap_h[k] < 64 || cols < 64 || cols > 128) continue;
+      if (h->cap_h[k] < 64 || h->cap_h[k] > 128 || cols < 64 || cols > 128 || cols % 2) continue;
       void* base = (char*)h->mps + h->off_h[k] * h->elem;
-      if (!encode_site_map(&h->map_a[k], base, cols, rows, h->Bcap, tc::kKC, tc::kM) ||
-          !encode_site_map(&h->map_b[k], base, cols, rows, h->Bcap, cols, 2 * tc::kKC)) {
+      if (!encode_site_map(&h->map_a[k], base, cols, rows, h->Bcap, tc::kKC, 128, CU_TENSOR_MAP_SWIZZLE_64B) ||
+          !encode_site_map(&h->map_b[k], base, cols, rows, h->Bcap, cols, 2 * tc::kKC, CU_TENSOR_MAP_SWIZZLE_NONE)) {
         h->release();
         delete h;
         return fail(LEMPS_ECUDA, "sim_create: cuTensorMapEncodeTiled is unavailable or refused a site map");

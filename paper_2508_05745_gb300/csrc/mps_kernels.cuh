@@ -562,9 +562,9 @@ __global__ void __launch_bounds__(kGemmThreads) k_contract(SimView<R> s, int q) 
 }
 
 // The same contraction on the tensor cores (mixed precision; 3xTF32 complex
-// GEMM, tc_contract.cuh) for gates whose site capacities are all >= 64: mapA
-// views site q as [2 cap_q][cap_{q+1}] complex64 rows, mapB site q + 1 as
-// [2 cap_{q+1}][cap_{q+2}], both over all trajectories.  One CTA per
+// GEMM, tc_contract.cuh) for gates whose three site capacities lie in [64,
+// 128]: mapA views site q as [2 cap_q][cap_{q+1}] complex64 rows, mapB site q
+// + 1 as [2 cap_{q+1}][cap_{q+2}], both over all trajectories.  One CTA per
 // trajectory holding all 512 tensor-memory columns (at most one CTA per SM).
 __global__ void __launch_bounds__(tc::kThreads, 1) k_contract_tc(const __grid_constant__ CUtensorMap mapA,
                                                                  const __grid_constant__ CUtensorMap mapB,
@@ -573,8 +573,9 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_contract_tc(const __grid_co
   if (t >= s.B) return;
   extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
   unsigned char* sm = reinterpret_cast<unsigned char*>(((uintptr_t)tc_smem_raw + 1023) & ~(uintptr_t)1023);
-  __shared__ __align__(8) uint64_t bars[2];
+  __shared__ __align__(8) uint64_t bars[tc::kNumBars];
   __shared__ uint32_t s_tmem;
+  __shared__ int s_err;
   __shared__ double red[32];
   const int warp = threadIdx.x >> 5;
   const int32_t* bd = s.bond + t * (s.n + 1);
@@ -582,8 +583,8 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_contract_tc(const __grid_co
   const int capr = s.cap[q + 2];
   cpx<float>* th = s.ws0 + t * s.ws_stride;
   if (threadIdx.x == 0) {
-    mbar_init(&bars[0], 1);
-    mbar_init(&bars[1], 1);
+    tc::init_bars(bars);
+    s_err = 0;
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_addr(&s_tmem))
@@ -595,12 +596,7 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_contract_tc(const __grid_co
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = s_tmem;
-  uint32_t phase[2] = {0u, 0u};
-  bool ok = true;
-  const int M = 2 * dl;
-  for (int m0 = 0; m0 < M && ok; m0 += tc::kM)
-    ok = tc::gemm_tile(&mapA, &mapB, (int)t, m0, M, dm, dr, capr, sm, bars, phase, tmem, th, 2 * dr);
-  __syncthreads();
+  const bool ok = tc::gemm(&mapA, &mapB, (int)t, 2 * dl, dm, dr, capr, sm, bars, tmem, th, 2 * dr, &s_err);
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
   if (!ok) {
     if (threadIdx.x == 0) atomicOr(s.status + t, (int32_t)TS_COPY);

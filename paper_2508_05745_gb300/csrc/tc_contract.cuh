@@ -1,32 +1,42 @@
 // Two-site contraction on the tensor cores (mixed precision, sm_103a):
-// Theta = A_q A_{q+1} as a (2 dl x dm)(dm x 2 dr) complex GEMM, complex FP32
-// built from 3xTF32 split products with FP32 accumulation in tensor memory
-// (the contraction of Sec. IV.A; the path's precision pattern for the
-// contractions).  Each complex64 operand x is split into tf32 parts x = hi +
-// lo (hi = x rounded to tf32, lo = the rest rounded to tf32), and a real
-// product X Y is taken as Xhi Yhi + Xhi Ylo + Xlo Yhi, so
-//   Re Theta = Ar Br - Ai Bi,   Im Theta = Ar Bi + Ai Br
-// takes 12 tcgen05.mma (kind::tf32, M = 128, N = 2 dr rounded up to 16, K = 8)
-// per 8 columns of A; the minus sign is the MMA's negate-A bit.
+// Theta = A_q A_{q+1} as a (2 dl x dm)(dm x 2 dr) complex GEMM (the
+// contraction of Sec. IV.A) in complex FP32, from 3xTF32 split products with
+// FP32 accumulation in tensor memory.
 //
-// Data flow per trajectory (one CTA of 256 threads; at most one CTA per SM):
-//  - the raw complex64 tiles of A (128 rows x 16 k) and of B (32 rows (2k + s)
-//    x cap columns) are fetched by TMA tensor copies (cp.async.bulk.tensor,
-//    3-D maps over the site slots of all trajectories) onto an mbarrier;
-//  - the threads split them into hi/lo tf32 planes of Re and Im in the
-//    canonical K-major layout without swizzle (8 x 16-byte core matrices;
-//    LBO = 128 bytes between core matrices along K, SBO = 512 bytes between
-//    8-row groups), zeroing the rows and columns beyond the actual bond
-//    dimensions;
-//  - one thread issues the MMAs into two accumulators in tensor memory (Re at
-//    column 0, Im at column 256; 512 columns allocated) and commits them to an
-//    mbarrier;
-//  - after the last K chunk the accumulators are read back (tcgen05.ld
-//    32x32b) and Theta is stored to the two-site workspace.
-// Every mbarrier wait is bounded (about two seconds) and its outcome is agreed
-// by the whole CTA; on a timeout the operations in flight get a second bounded
-// wait, the trajectory is flagged TS_COPY, and the CTA frees its tensor memory
-// and returns.
+// The complex GEMM is taken in its real embedding: a complex64 row of A is a
+// real row of (re, im) pairs, so with
+//   Br'[2k][n] = Re B[k][n], Br'[2k+1][n] = -Im B[k][n],
+//   Bi'[2k][n] = Im B[k][n], Bi'[2k+1][n] =  Re B[k][n]
+// Re Theta = A_real Br' and Im Theta = A_real Bi'.  Each operand x is split
+// into x = hi + lo with hi, lo in tf32, and a real product X Y is taken as
+// Xhi Yhi + Xhi Ylo + Xlo Yhi.
+//  - A_real needs no rearrangement: TMA tensor copies (cp.async.bulk.tensor,
+//    3-D maps over the site slots of all trajectories) write it straight into
+//    the 64-byte-swizzled K-major layout that tcgen05.mma reads.  The tensor
+//    core reads an FP32 operand as tf32 by dropping its 13 low mantissa bits,
+//    so the raw tile is the high part as it stands and only the low part A -
+//    trunc(A) is formed, elementwise.
+//  - B is split per half of N (128 columns of Theta) into a high and a low
+//    plane whose rows are [Br' columns | Bi' columns] (K-major, no swizzle:
+//    8 x 16-byte core matrices, LBO = 128 bytes along K, SBO = 512 bytes
+//    between 8-row groups), so one MMA of N = 2 x 128 yields Re and Im side by
+//    side.  Both M tiles of A share the planes; the accumulators (2 M tiles x
+//    256 columns) fill the 512 tensor-memory columns.
+//  - Per chunk of 8 complex k: 2 M tiles x 3 products x 2 k-steps = 12
+//    tcgen05.mma (kind::tf32) of 128 x 256 x 8.
+//
+// One CTA of kThreads per trajectory, specialised by warp: warps 0-7 split the
+// operands and read the accumulators back (tcgen05.ld 32x32b, staged through
+// shared memory into 128-byte row segments); one lane of warp 8 issues the TMA
+// copies and the MMAs.  Hand-offs are mbarriers:
+//   tma_full[s]   copy of a chunk landed in TMA stage s (kNTma stages)
+//   split_full[s] the 256 split threads filled split stage s (2 stages)
+//   mma_done[s]   the MMAs that read split stage s finished (tcgen05.commit)
+//   acc_empty     the 256 readout threads are done with the accumulators
+// Every wait is bounded (about two seconds) and gives up once another thread
+// has flagged an error; the issuing lane then waits (bounded) for its copies
+// and MMAs still in flight so that the CTA can free its tensor memory, and the
+// trajectory is flagged TS_COPY by the caller.
 #pragma once
 
 #include <cuda.h>
@@ -35,22 +45,6 @@
 
 namespace lemps {
 namespace tc {
-
-constexpr int kKC = 16;            // columns of A (rows of B) per chunk
-constexpr int kM = 128;            // MMA M (one M tile)
-constexpr int kNmax = 256;         // MMA N limit: 2 dr <= 256
-constexpr int kThreads = 256;
-
-// Shared-memory layout (bytes from a 1024-aligned base).
-constexpr int kArawBytes = kM * kKC * 8;                  // 16 KB: A tile, complex64
-constexpr int kBrawBytes = 2 * kKC * 128 * 8;             // 32 KB: B tile, 32 rows x cap (<= 128) complex64
-constexpr int kAopBytes = (kM / 8) * 512;                 // 8 KB per tf32 plane of A (16 row groups)
-constexpr int kBopBytes = (kNmax / 8) * 512;              // 16 KB per tf32 plane of B^T (32 row groups)
-constexpr int kOffAraw = 0;
-constexpr int kOffBraw = kOffAraw + kArawBytes;
-constexpr int kOffAop = kOffBraw + kBrawBytes;            // 4 planes: Re hi, Re lo, Im hi, Im lo
-constexpr int kOffBop = kOffAop + 4 * kAopBytes;          // 4 planes: Re hi, Re lo, Im hi, Im lo
-constexpr int kSmemBytes = kOffBop + 4 * kBopBytes + 1024;   // + alignment slack
 
 // Byte offset of element (row r, k) of a K-major tile without swizzle: 8-row
 // groups 512 bytes apart (SBO), 16-byte core-matrix columns 128 bytes apart
@@ -118,128 +112,248 @@ __device__ __forceinline__ void ld_32x32b_x16(uint32_t taddr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// C[i][j] (i < M, j < N), row-major with leading dimension ldc, = A B with
-// A[i][k] = sA[(m0 + i) * lda + k] (rows m0..m0+127 of the A map's tile) and
-// B[k][j] = the B map's row 2k + s, column b for j = s * dr + b.  Both maps
-// are 3-D over (column, row, trajectory t).  Returns false on a timeout.
-// Called by all 256 threads; tmem holds the 512-column allocation.
-__device__ __forceinline__ bool gemm_tile(const CUtensorMap* mapA, const CUtensorMap* mapB, int t, int m0, int M,
-                                          int K, int dr, int capr, unsigned char* sm, uint64_t* bars,
-                                          uint32_t* phase, uint32_t tmem, cpx<float>* C, int ldc) {
-  const int tid = threadIdx.x;
-  const int N = 2 * dr, Npad = (N + 15) & ~15;
-  const cpx<float>* Araw = reinterpret_cast<const cpx<float>*>(sm + kOffAraw);
-  const cpx<float>* Braw = reinterpret_cast<const cpx<float>*>(sm + kOffBraw);
-  unsigned char* Aop = sm + kOffAop;
-  unsigned char* Bop = sm + kOffBop;
-  const uint32_t sAop = smem_addr(Aop), sBop = smem_addr(Bop);
-  const uint32_t id_pos = idesc_tf32(kM, Npad, false), id_neg = idesc_tf32(kM, Npad, true);
-  const int nchunk = (K + kKC - 1) / kKC;
-  for (int c = 0; c < nchunk; ++c) {
-    const int k0 = c * kKC;
-    if (tid == 0) {
-      // the raw tiles were last read by the threads (generic proxy)
+constexpr int kKC = 8;                          // complex k per chunk (16 real: one 64-byte row)
+constexpr int kNH = 128;                        // Theta columns per N half
+constexpr int kWorkers = 256;                   // split / readout threads (warps 0-7)
+constexpr int kThreads = kWorkers + 32;         // + the issuing warp
+constexpr int kNTma = 4;                        // TMA stages
+constexpr int kAtile = 128 * 64;                // 8 KB: one M tile of A, 128 rows x 64 bytes
+constexpr int kAhiBytes = 2 * kAtile;           // both M tiles
+constexpr int kBrawBytes = 2 * kKC * 128 * 8;   // 16 KB: rows 2k + s of B, cap <= 128 columns
+constexpr int kTmaStage = kAhiBytes + kBrawBytes;              // 32 KB
+constexpr int kBplane = (2 * kNH / 8) * 512;                   // 16 KB: 256 rows x 16 real k
+constexpr int kSplitStage = kAhiBytes + 2 * kBplane;           // A lo (16 KB) + B hi, lo (32 KB)
+constexpr int kOffSplit = kNTma * kTmaStage;                   // 128 KB
+constexpr int kSmemBytes = kOffSplit + 2 * kSplitStage + 1024;  // 224 KB + alignment slack
+constexpr int kNumBars = kNTma + 5;
+
+// K-major, 64-byte swizzle: 8-row atoms of 512 bytes (SBO), layout type 4
+// (the leading byte offset is not used by swizzled K-major layouts).
+__device__ __forceinline__ uint64_t desc_sw64(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(512 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)4 << 61;
+  return d;
+}
+
+// low part of x for the 3xTF32 split when the high part is x with its 13 low
+// mantissa bits dropped (how the tensor core reads an FP32 operand)
+__device__ __forceinline__ float lo_of_trunc(float x) {
+  const float hi = __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
+  return __uint_as_float(to_tf32(x - hi));
+}
+
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+               : "=r"(ok)
+               : "r"(smem_addr(bar)), "r"(parity)
+               : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+// Bounded wait that also gives up once *err is set; a timeout sets *err.
+__device__ __forceinline__ bool wait_or_err(uint64_t* bar, uint32_t parity, volatile int* err) {
+  const long long t0 = clock64();
+  for (;;) {
+    if (mbar_try(bar, parity)) return true;
+    if (*err) return false;
+    if (clock64() - t0 > (1LL << 32)) {
+      *err = 1;
+      return false;
+    }
+  }
+}
+
+// Initialises the kNumBars mbarriers of gemm (one thread, before the CTA
+// synchronises).
+__device__ __forceinline__ void init_bars(uint64_t* bars) {
+  for (int i = 0; i < kNTma; ++i) mbar_init(&bars[i], 1);
+  mbar_init(&bars[kNTma + 0], kWorkers);   // split_full
+  mbar_init(&bars[kNTma + 1], kWorkers);
+  mbar_init(&bars[kNTma + 2], 1);          // mma_done
+  mbar_init(&bars[kNTma + 3], 1);
+  mbar_init(&bars[kNTma + 4], kWorkers);   // acc_empty
+}
+
+// Theta (M x N = 2 dr, row-major, ldc even, C 16-byte aligned; M <= 256,
+// N <= 256) = A B for one trajectory t: A from the A map (site q as [2 cap_q][cap_{q+1}] complex64,
+// box 8 x 128, 64-byte swizzle), B from the B map (site q + 1 as [2
+// cap_{q+1}][cap_{q+2}], box cap_{q+2} x 16; cap_{q+2} <= 128 and even).  Called by all kThreads threads
+// once per CTA; bars: kNumBars mbarriers initialised by init_bars; tmem: the
+// 512-column allocation; err: a shared int set to 0.  Returns false on a
+// timeout (uniform over the CTA).
+__device__ __noinline__ bool gemm(const CUtensorMap* mapA, const CUtensorMap* mapB, int t, int M, int K, int dr,
+                                  int capr, unsigned char* sm, uint64_t* bars, uint32_t tmem, cpx<float>* C,
+                                  int ldc, volatile int* err) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int N = 2 * dr, nhalf = (N + kNH - 1) / kNH;
+  const int nchunk = (K + kKC - 1) / kKC, G = nhalf * nchunk;
+  const int nmt = (M + 127) / 128;              // M tiles (1 or 2)
+  uint64_t* tma_full = bars;
+  uint64_t* split_full = bars + kNTma;
+  uint64_t* mma_done = bars + kNTma + 2;
+  uint64_t* acc_empty = bars + kNTma + 4;
+  if (warp == kWorkers / 32) {
+    // ---- issuing lane: TMA copies and MMAs ----
+    if (lane == 0) {
+      const uint32_t sbase = smem_addr(sm);
+      const uint32_t abytes = (uint32_t)(nmt * kAtile), bbytes = (uint32_t)(2 * kKC * capr * 8);
+      auto issue_tma = [&](int x) {                // chunk x (K chunk x % nchunk) into stage x % kNTma
+        const int st = x % kNTma, c = x % nchunk;
+        unsigned char* dst = sm + st * kTmaStage;
+        mbar_expect_tx(&tma_full[st], abytes + bbytes);
+        for (int mt = 0; mt < nmt; ++mt) tma_load_3d(dst + mt * kAtile, mapA, c * kKC, mt * 128, t, &tma_full[st]);
+        tma_load_3d(dst + kAhiBytes, mapB, 0, 2 * c * kKC, t, &tma_full[st]);
+      };
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      mbar_expect_tx(&bars[0], (uint32_t)(kArawBytes + 2 * kKC * capr * 8));
-      tma_load_3d(sm + kOffAraw, mapA, k0, m0, t, &bars[0]);
-      tma_load_3d(sm + kOffBraw, mapB, 0, 2 * k0, t, &bars[0]);
-    }
-    if (!__syncthreads_and(mbar_wait(&bars[0], phase[0]))) {
-      // a copy missed its time limit: give it a second bounded wait before the
-      // shared memory is given up
-      if (tid == 0) mbar_wait(&bars[0], phase[0]);
-      __syncthreads();
-      return false;
-    }
-    phase[0] ^= 1u;
-    // split into hi/lo tf32 planes, K-major, zero beyond the bond dimensions
-    for (int e = tid; e < kM * kKC; e += kThreads) {
-      const int i = e / kKC, k = e % kKC;
-      cpx<float> x = mk(0.f, 0.f);
-      if (m0 + i < M && k0 + k < K) x = Araw[i * kKC + k];
-      const uint32_t rh = to_tf32(x.re), ih = to_tf32(x.im);
-      const uint32_t rl = to_tf32(x.re - __uint_as_float(rh)), il = to_tf32(x.im - __uint_as_float(ih));
-      const uint32_t o = kmajor_off(i, k);
-      *reinterpret_cast<uint32_t*>(Aop + 0 * kAopBytes + o) = rh;
-      *reinterpret_cast<uint32_t*>(Aop + 1 * kAopBytes + o) = rl;
-      *reinterpret_cast<uint32_t*>(Aop + 2 * kAopBytes + o) = ih;
-      *reinterpret_cast<uint32_t*>(Aop + 3 * kAopBytes + o) = il;
-    }
-    for (int e = tid; e < Npad * kKC; e += kThreads) {
-      const int j = e / kKC, k = e % kKC;
-      cpx<float> x = mk(0.f, 0.f);
-      if (j < N && k0 + k < K) {
-        const int s2 = j >= dr, b = j - s2 * dr;
-        x = Braw[(2 * k + s2) * capr + b];
+      int issued = 0, committed = 0;
+      for (; issued < G && issued < kNTma - 1; ++issued) issue_tma(issued);
+      for (int g = 0; g < G; ++g) {
+        const int h = g / nchunk, c = g - h * nchunk;
+        if (c == 0 && h > 0 && !wait_or_err(acc_empty, (uint32_t)((h - 1) & 1), err)) break;
+        if (!wait_or_err(&split_full[g & 1], (uint32_t)((g >> 1) & 1), err)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const int nh = min(kNH, N - h * kNH), nhp = (nh + 15) & ~15;
+        const uint32_t idesc = idesc_tf32(128, 2 * nhp, false);
+        const uint32_t sA = sbase + (uint32_t)((g % kNTma) * kTmaStage);
+        const uint32_t sAl = sbase + (uint32_t)(kOffSplit + (g & 1) * kSplitStage);
+        const uint32_t sBh = sAl + (uint32_t)kAhiBytes, sBl = sBh + (uint32_t)kBplane;
+        for (int mt = 0; mt < nmt; ++mt) {
+          const uint32_t d = tmem + (uint32_t)(mt * 256);
+#pragma unroll
+          for (int s = 0; s < 2; ++s) {              // two k-steps of 8 real k (32 bytes)
+            const uint64_t ah = desc_sw64(sA + mt * kAtile + s * 32), al = desc_sw64(sAl + mt * kAtile + s * 32);
+            const uint64_t bh = smem_desc(sBh + s * 256, 128, 512), bl = smem_desc(sBl + s * 256, 128, 512);
+            mma_tf32(d, ah, bh, idesc, (c > 0 || s > 0) ? 1u : 0u);
+            mma_tf32(d, ah, bl, idesc, 1u);
+            mma_tf32(d, al, bh, idesc, 1u);
+          }
+        }
+        mma_commit(&mma_done[g & 1]);
+        committed = g + 1;
+        // the stage of chunk g - 1 takes chunk g + kNTma - 1 once its MMAs are done
+        if (g >= 1 && !wait_or_err(&mma_done[(g - 1) & 1], (uint32_t)(((g - 1) >> 1) & 1), err)) break;
+        if (issued < G) issue_tma(issued++);
       }
-      const uint32_t rh = to_tf32(x.re), ih = to_tf32(x.im);
-      const uint32_t rl = to_tf32(x.re - __uint_as_float(rh)), il = to_tf32(x.im - __uint_as_float(ih));
-      const uint32_t o = kmajor_off(j, k);
-      *reinterpret_cast<uint32_t*>(Bop + 0 * kBopBytes + o) = rh;
-      *reinterpret_cast<uint32_t*>(Bop + 1 * kBopBytes + o) = rl;
-      *reinterpret_cast<uint32_t*>(Bop + 2 * kBopBytes + o) = ih;
-      *reinterpret_cast<uint32_t*>(Bop + 3 * kBopBytes + o) = il;
+      // drain whatever is still in flight (bounded waits that do not give up on *err)
+      if (committed > 0) mbar_wait(&mma_done[(committed - 1) & 1], (uint32_t)(((committed - 1) >> 1) & 1));
+      for (int x = max(0, issued - kNTma); x < issued; ++x) mbar_wait(&tma_full[x % kNTma], (uint32_t)((x / kNTma) & 1));
     }
-    // the planes were written by the generic proxy and are read by the MMA
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (tid == 0) {
+    __syncwarp();
+  } else {
+    // ---- warps 0-7: operand split and accumulator readout ----
+    int g = 0;
+    bool ok = true;
+    for (int h = 0; h < nhalf && ok; ++h) {
+      const int n0 = h * kNH, nh = min(kNH, N - n0), nhp = (nh + 15) & ~15;
+      if (h > 0 && !wait_or_err(acc_empty, (uint32_t)((h - 1) & 1), err)) break;   // staging reuse
+      for (int c = 0; c < nchunk; ++c, ++g) {
+        unsigned char* tst = sm + (g % kNTma) * kTmaStage;
+        unsigned char* sst = sm + kOffSplit + (g & 1) * kSplitStage;
+        if (!wait_or_err(&tma_full[g % kNTma], (uint32_t)((g / kNTma) & 1), err) ||
+            (g >= 2 && !wait_or_err(&mma_done[g & 1], (uint32_t)(((g - 2) >> 1) & 1), err))) {
+          ok = false;
+          break;
+        }
+        // A low parts, elementwise over the swizzled tiles; entries with
+        // complex k >= K (stale slot columns beyond the bond dimension) are
+        // zeroed in both parts.  Rows beyond M only feed output rows that are
+        // not stored.  In a 64-byte-swizzled tile the 16-byte chunk at
+        // position p of row r holds logical chunk p ^ ((r >> 1) & 3), i.e.
+        // complex k0 + 2j and k0 + 2j + 1.
+        const int k0 = c * kKC;
+        {
+          float4* hi = reinterpret_cast<float4*>(tst);
+          float4* dst = reinterpret_cast<float4*>(sst);
+          const bool ragged = k0 + kKC > K;
+          for (int e = tid; e < nmt * kAtile / 16; e += kWorkers) {
+            float4 x = hi[e];
+            if (ragged) {
+              const int r = e >> 2, j = (e & 3) ^ ((r >> 1) & 3);
+              const int kc = k0 + 2 * j;
+              if (kc >= K) x.x = x.y = 0.f;
+              if (kc + 1 >= K) {
+                x.z = x.w = 0.f;
+                hi[e] = x;
+              }
+            }
+            x.x = lo_of_trunc(x.x); x.y = lo_of_trunc(x.y);
+            x.z = lo_of_trunc(x.z); x.w = lo_of_trunc(x.w);
+            dst[e] = x;
+          }
+        }
+        // B planes of this half, K-major without swizzle: row n < nhp holds
+        // Br' column n0 + n, row nhp + n holds Bi' column n0 + n.  A warp
+        // covers 8 n x 4 k, which spreads its 8-byte stores over all banks.
+        {
+          const cpx<float>* braw = reinterpret_cast<const cpx<float>*>(tst + kAhiBytes);
+          unsigned char* bh = sst + kAhiBytes;
+          unsigned char* bl = bh + kBplane;
+          for (int e = tid; e < nhp * kKC; e += kWorkers) {
+            const int n = ((e >> 6) << 3) | (e & 7), kk = (e >> 3) & 7;
+            const int j = n0 + n;
+            cpx<float> x = mk(0.f, 0.f);
+            if (n < nh && k0 + kk < K) {
+              const int s2 = j >= dr, b = j - s2 * dr;
+              x = braw[(2 * kk + s2) * capr + b];
+            }
+            const float rh = __uint_as_float(to_tf32(x.re)), ih = __uint_as_float(to_tf32(x.im));
+            const float rl = __uint_as_float(to_tf32(x.re - rh)), il = __uint_as_float(to_tf32(x.im - ih));
+            const uint32_t o = kmajor_off(n, 2 * kk), oi = kmajor_off(nhp + n, 2 * kk);
+            *reinterpret_cast<float2*>(bh + o) = make_float2(rh, -ih);    // Br' high
+            *reinterpret_cast<float2*>(bh + oi) = make_float2(ih, rh);    // Bi' high
+            *reinterpret_cast<float2*>(bl + o) = make_float2(rl, -il);    // Br' low
+            *reinterpret_cast<float2*>(bl + oi) = make_float2(il, rl);    // Bi' low
+          }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive(&split_full[g & 1]);
+      }
+      if (!ok || !wait_or_err(&mma_done[(g - 1) & 1], (uint32_t)(((g - 1) >> 1) & 1), err)) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t dre = tmem, dim = tmem + 256;
+      // readout: warp w reads tensor-memory lanes 32 (w % 4) .. of M tile w / 4
+      // (row = lane), stages each 32-row x 16-column block in its own 4 KB of
+      // the (idle) split stages with 16-byte chunks XOR-swizzled by row, and
+      // stores it as 128-byte row segments.
+      {
+        const int mt = warp >> 2, rbase = mt * 128 + 32 * (warp & 3);
+        const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+        float4* stg = reinterpret_cast<float4*>(sm + kOffSplit + warp * 4096);
+        if (mt < nmt && rbase < M) {
+          for (int c0 = 0; c0 < nhp; c0 += 16) {
+            float re[16], im[16];
+            ld_32x32b_x16(tmem + lane_base + (uint32_t)(mt * 256 + c0), re);
+            ld_32x32b_x16(tmem + lane_base + (uint32_t)(mt * 256 + nhp + c0), im);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-      for (int s = 0; s < kKC / 8; ++s) {
-        auto A = [&](int p) { return smem_desc(sAop + p * kAopBytes + s * 256, 128, 512); };
-        auto B = [&](int p) { return smem_desc(sBop + p * kBopBytes + s * 256, 128, 512); };
-        const uint32_t acc = (c > 0 || s > 0) ? 1u : 0u;
-        // Re: Ar Br - Ai Bi (3xTF32 each)
-        mma_tf32(dre, A(0), B(0), id_pos, acc);
-        mma_tf32(dre, A(0), B(1), id_pos, 1u);
-        mma_tf32(dre, A(1), B(0), id_pos, 1u);
-        mma_tf32(dre, A(2), B(2), id_neg, 1u);
-        mma_tf32(dre, A(2), B(3), id_neg, 1u);
-        mma_tf32(dre, A(3), B(2), id_neg, 1u);
-        // Im: Ar Bi + Ai Br
-        mma_tf32(dim, A(0), B(2), id_pos, acc);
-        mma_tf32(dim, A(0), B(3), id_pos, 1u);
-        mma_tf32(dim, A(1), B(2), id_pos, 1u);
-        mma_tf32(dim, A(2), B(0), id_pos, 1u);
-        mma_tf32(dim, A(2), B(1), id_pos, 1u);
-        mma_tf32(dim, A(3), B(0), id_pos, 1u);
-      }
-      mma_commit(&bars[1]);
-    }
-    // the planes and raw tiles are reused by the next chunk: wait for the MMAs
-    if (!__syncthreads_and(mbar_wait(&bars[1], phase[1]))) {
-      if (tid == 0) mbar_wait(&bars[1], phase[1]);   // MMAs still in flight: bounded wait
-      __syncthreads();
-      return false;
-    }
-    phase[1] ^= 1u;
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  }
-  // read the accumulators back: warp w reads TMEM lanes 32 (w % 4) ..,
-  // columns of half w / 4
-  const int warp = tid >> 5, lane = tid & 31;
-  const int row = 32 * (warp & 3) + lane, half = warp >> 2;
-  const int ncols = Npad / 2;   // a multiple of 8; read in 16s (the last may overhang into padding)
-  for (int c0 = half * ncols; c0 < (half + 1) * ncols; c0 += 16) {
-    float re[16], im[16];
-    const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
-    ld_32x32b_x16(tmem + lane_base + (uint32_t)c0, re);
-    ld_32x32b_x16(tmem + lane_base + 256u + (uint32_t)c0, im);
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-    const int i = m0 + row;
-    if (i < M) {
+            for (int q = 0; q < 8; ++q)
+              stg[lane * 8 + (q ^ (lane & 7))] = make_float4(re[2 * q], im[2 * q], re[2 * q + 1], im[2 * q + 1]);
+            __syncwarp();
 #pragma unroll
-      for (int jj = 0; jj < 16; ++jj) {
-        const int j = c0 + jj;
-        if (j < N && j < (half + 1) * ncols) C[(int64_t)i * ldc + j] = mk(re[jj], im[jj]);
+            for (int it = 0; it < 8; ++it) {
+              const int rr = it * 4 + (lane >> 3), q = lane & 7, row = rbase + rr, col = n0 + c0 + 2 * q;
+              const float4 v = stg[rr * 8 + (q ^ (rr & 7))];
+              if (row < M) {
+                if (c0 + 2 * q + 1 < nh) *reinterpret_cast<float4*>(C + (int64_t)row * ldc + col) = v;
+                else if (c0 + 2 * q < nh) C[(int64_t)row * ldc + col] = mk(v.x, v.y);
+              }
+            }
+            __syncwarp();
+          }
+        }
       }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      mbar_arrive(acc_empty);
     }
   }
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  return true;
+  return *err == 0;
 }
 
 }  // namespace tc
