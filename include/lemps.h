@@ -51,9 +51,12 @@ typedef enum {
   LEMPS_FP64 = 0,      /* complex128 storage and arithmetic everywhere */
   LEMPS_MIXED = 1      /* complex64 MPS storage and contractions (two-site
                           tensor, Gram matrix, projections, centre moves);
-                          the Gram eigensolve of the split, reduced densities,
-                          unraveling, branch weights, discarded weights and
-                          entropies in FP64 (complex128) */
+                          the Gram eigensolve of the split (tridiagonal form,
+                          eigenvalues, tridiagonal eigenvectors), reduced
+                          densities, unraveling, branch weights, discarded
+                          weights and entropies in FP64 (complex128); the
+                          kept eigenvectors are back-transformed in complex64,
+                          the precision they are used in */
 } lemps_precision;
 
 typedef enum {

@@ -260,7 +260,9 @@ void move_center_to(lemps_sim* h, int target) {
 
 constexpr int kHeevThreads = 512;
 
-// Hermitian eigensolve of the Gram matrix, in complex128 in both precisions;
+// Hermitian eigensolve of the Gram matrix: tridiagonalization, eigenvalues and
+// tridiagonal eigenvectors in complex128 in both precisions, the
+// back-transformation (and U) in the storage precision;
 // keeps the top min(chi_max, #{l > cutoff * trace}) eigenpairs (vectors = 1)
 // or computes every eigenvalue (vectors = 0, cutoff = 0).
 template <class R>
@@ -268,11 +270,11 @@ void launch_heev(lemps_sim* h, int q, int mode, double cutoff, int keep_max, int
   const size_t smem = HeevSmem<double>::kBytes;
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_heev<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_heev<double, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr = true;
   }
   h->timed(LEMPS_K_EIG, [&] {
-    k_heev<double><<<(unsigned)h->B, kHeevThreads, smem, h->stream>>>(heev_view(h->view<R>()), q, mode, cutoff,
+    k_heev<double, R><<<(unsigned)h->B, kHeevThreads, smem, h->stream>>>(heev_view(h->view<R>()), q, mode, cutoff,
                                                                        keep_max, vectors);
   });
 }

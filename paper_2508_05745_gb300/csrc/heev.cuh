@@ -9,8 +9,9 @@
 //
 // Layout (buffers 16-byte aligned, n even): G (n x n row-major, Hermitian)
 // in ws1, overwritten.  Householder vectors in ws3 (row j holds sqrt(2) v_j,
-// v_j of unit norm, entries > j).  Eigenvectors are written column-major to ws2:
-// U[k * n + i], k < keep.  Eigenvalues (double, descending) to
+// v_j of unit norm, entries > j), in the back-transformation type.
+// Eigenvectors are written column-major to ws2 in that type: U[k * n + i],
+// k < keep.  Eigenvalues (double, descending) to
 // evals[0..keep), keep and the trace to kept[] / trace[].
 #pragma once
 
@@ -194,8 +195,14 @@ __device__ __forceinline__ void bt_reflector(cpx<R> (&y)[NCOL][PER], const cpx<R
 }
 
 // mode / q select the matrix size as in gram_size(); want_vectors = 0 returns
-// eigenvalues only (all n of them when cutoff = 0).
-template <class R>
+// eigenvalues only (all n of them when cutoff = 0).  R is the arithmetic of
+// the tridiagonalization, the eigenvalues and the tridiagonal eigenvectors;
+// RB that of the back-transformation U = Q D z: the reflectors are stored
+// and applied, and U is written, in cpx<RB> (each trajectory's slots of ws3
+// and ws2, of ws_stride complex128 entries, viewed as cpx<RB> arrays).  Applying the reflectors is
+// backward stable, so its rounding error (about n eps_RB relative) does not
+// depend on the eigenvalue gaps, unlike the eigenpairs of a perturbed Gram.
+template <class R, class RB = R>
 __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, double cutoff, int keep_max,
                                                int want_vectors) {
   const int64_t t = blockIdx.x;
@@ -203,8 +210,11 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
   const int32_t* bd = s.bond + t * (s.nq + 1);
   const int n = mode == 0 ? 2 * bd[q] : (mode == 1 ? 2 * bd[q + 2] : bd[q + 1]);
   cpx<R>* G = s.ws1 + t * s.ws_stride;
-  cpx<R>* Hv = s.ws3 + t * s.ws_stride;
-  cpx<R>* U = s.ws2 + t * s.ws_stride;
+  // the cpx<RB> views start at this trajectory's own slot: the slot of the
+  // next trajectories stays untouched whatever RB is (the phase-1 scratch of
+  // another CTA may live there)
+  cpx<RB>* Hv = reinterpret_cast<cpx<RB>*>(s.ws3 + t * s.ws_stride);
+  cpx<RB>* U = reinterpret_cast<cpx<RB>*>(s.ws2 + t * s.ws_stride);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   extern __shared__ __align__(16) unsigned char heev_smem[];
   cpx<R>* Lp = reinterpret_cast<cpx<R>*>(heev_smem);   // packed lower triangle (trailing block)
@@ -239,7 +249,7 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
   while ((n - j0) * (n - j0 + 1) / 2 > HeevSmem<R>::kCap) ++j0;
   // V and W sit in shared memory (unused until the packing) when they fit
   const bool vw_sm = 2 * (size_t)j0 * n * sizeof(cpx<R>) <= (size_t)HeevSmem<R>::kBytes;
-  cpx<R>* Vp = vw_sm ? Lp : U;
+  cpx<R>* Vp = vw_sm ? Lp : s.ws2 + t * s.ws_stride;   // ws2 in R until U is written
   cpx<R>* Wp = Vp + (int64_t)j0 * n;
   // G[jt:, jt:] -= sum_{k in [kb0, kb1)} v_k w_k^dagger + w_k v_k^dagger, both
   // triangles (the panel matvec reads whole rows).  The lower triangle's
@@ -350,7 +360,7 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
     if (threadIdx.x == 0) sec[j] = alpha;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
       const cpx<R> vi = (i > j && reflect) ? sv[i - j - 1] : mk<R>(0, 0);
-      Hv[(int64_t)j * n + i] = kSqrt2 * vi;
+      Hv[(int64_t)j * n + i] = cast<RB>(kSqrt2 * vi);
       Vp[(int64_t)j * n + i] = vi;
     }
     if (!reflect) {
@@ -513,9 +523,9 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
       vN[jl + 1 + i] = vi;
       yN[jl + 1 + i] = mk<R>(0, 0);
       wP[jl + 1 + i] = wi;
-      Hv[(int64_t)j * n + (j + 1 + i)] = kSqrt2 * vi;
+      Hv[(int64_t)j * n + (j + 1 + i)] = cast<RB>(kSqrt2 * vi);
     }
-    if (i <= j) Hv[(int64_t)j * n + i] = mk<R>(0, 0);
+    if (i <= j) Hv[(int64_t)j * n + i] = mk<RB>(0, 0);
     __syncthreads();
     // One pass over 32 x QW slices of the trailing triangle's 32 x 32 tiles
     // (aligned to multiples of 32 in local index), lane = row r.  It applies
@@ -1107,17 +1117,17 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
   // Reflector j is zero in rows <= j, so the 32-row groups above it are
   // skipped (bt_reflector, specialized on the first live group).
   constexpr int PER = 8;  // n <= 256 -> 8 elements per lane
-  constexpr int NCOL = sizeof(R) == 4 ? 4 : 2;
+  constexpr int NCOL = sizeof(RB) == 4 ? 4 : 2;
   const int nper = (n + 31) >> 5;
   const int ldv = 32 * nper;
   const size_t zbytes = 0;   // the vectors are read from Zg
-  const int rc = min(32, (int)((HeevSmem<R>::kBytes - zbytes) / (2 * (size_t)ldv * sizeof(cpx<R>))));
+  const int rc = min(32, (int)((HeevSmem<R>::kBytes - zbytes) / (2 * (size_t)ldv * sizeof(cpx<RB>))));
   if (rc < 1) {   // cannot happen for n <= 256 (the z copy leaves >= 8 n entries)
     if (threadIdx.x == 0) atomicOr(s.status + t, (int32_t)TS_SHAPE);
     return;
   }
-  cpx<R>* vbuf[2];
-  vbuf[0] = reinterpret_cast<cpx<R>*>(heev_smem + zbytes);
+  cpx<RB>* vbuf[2];
+  vbuf[0] = reinterpret_cast<cpx<RB>*>(heev_smem + zbytes);
   vbuf[1] = vbuf[0] + (size_t)rc * ldv;
   __shared__ __align__(8) uint64_t s_bar[2];
   const int nch = (n >= 3) ? (n - 3) / rc + 1 : 0;   // chunks per pass
@@ -1128,18 +1138,18 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
     const int c = g % nch;
     const int jtop = n - 3 - c * rc, jlo = max(0, jtop - rc + 1), rows = jtop - jlo + 1;
     uint64_t* bar = &s_bar[g & 1];
-    mbar_expect_tx(bar, (uint32_t)(rows * n * sizeof(cpx<R>)));
+    mbar_expect_tx(bar, (uint32_t)(rows * n * sizeof(cpx<RB>)));
     if (ldv == n) {
-      bulk_g2s(vbuf[g & 1], Hv + (int64_t)jlo * n, (uint32_t)(rows * n * sizeof(cpx<R>)), bar);
+      bulk_g2s(vbuf[g & 1], Hv + (int64_t)jlo * n, (uint32_t)(rows * n * sizeof(cpx<RB>)), bar);
     } else {
       for (int rr = 0; rr < rows; ++rr)
-        bulk_g2s(vbuf[g & 1] + (size_t)rr * ldv, Hv + (int64_t)(jlo + rr) * n, (uint32_t)(n * sizeof(cpx<R>)), bar);
+        bulk_g2s(vbuf[g & 1] + (size_t)rr * ldv, Hv + (int64_t)(jlo + rr) * n, (uint32_t)(n * sizeof(cpx<RB>)), bar);
     }
   };
   if (ldv != n)   // padding columns n .. ldv-1 of both buffers, never copied over
     for (int e = threadIdx.x; e < 2 * rc * (ldv - n); e += blockDim.x) {
       const int r = e / (ldv - n), i = n + e % (ldv - n);
-      vbuf[0][(size_t)r * ldv + i] = mk<R>(0, 0);
+      vbuf[0][(size_t)r * ldv + i] = mk<RB>(0, 0);
     }
   if (threadIdx.x == 0) {
     mbar_init(&s_bar[0], 1);
@@ -1150,7 +1160,7 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
   __syncthreads();
   if (threadIdx.x == 0)
     for (int g = 0; g < min(2, nchunk); ++g) issue(g);
-  cpx<R> y[NCOL][PER];
+  cpx<RB> y[NCOL][PER];
   for (int pass = 0; pass < passes; ++pass) {
     const int k0 = NCOL * (warp + pass * nwarp);
     const bool act = k0 < keep;
@@ -1159,25 +1169,25 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
 #pragma unroll
       for (int a = 0; a < PER; ++a) {
         const int i = lane + 32 * a;
-        y[c][a] = (i < n && k0 + c < keep) ? sph[i] * Zg[(size_t)(k0 + c) * n + i] : mk<R>(0, 0);
+        y[c][a] = (i < n && k0 + c < keep) ? cast<RB>(sph[i] * Zg[(size_t)(k0 + c) * n + i]) : mk<RB>(0, 0);
       }
     for (int c = 0; c < nch; ++c) {
       const int g = pass * nch + c;
       const int jtop = n - 3 - c * rc, jlo = max(0, jtop - rc + 1);
-      const cpx<R>* vst = vbuf[g & 1];
+      const cpx<RB>* vst = vbuf[g & 1];
       const bool ready = mbar_wait(&s_bar[g & 1], (uint32_t)((g >> 1) & 1));
       if (act && ready) {
         for (int j = jtop; j >= jlo; --j) {
-          const cpx<R>* v = vst + (j - jlo) * ldv;
+          const cpx<RB>* v = vst + (j - jlo) * ldv;
           switch ((j + 1) >> 5) {   // groups a < (j + 1) / 32 hold rows <= j only
-            case 0: bt_reflector<R, NCOL, PER, 0>(y, v, lane, nper); break;
-            case 1: bt_reflector<R, NCOL, PER, 1>(y, v, lane, nper); break;
-            case 2: bt_reflector<R, NCOL, PER, 2>(y, v, lane, nper); break;
-            case 3: bt_reflector<R, NCOL, PER, 3>(y, v, lane, nper); break;
-            case 4: bt_reflector<R, NCOL, PER, 4>(y, v, lane, nper); break;
-            case 5: bt_reflector<R, NCOL, PER, 5>(y, v, lane, nper); break;
-            case 6: bt_reflector<R, NCOL, PER, 6>(y, v, lane, nper); break;
-            default: bt_reflector<R, NCOL, PER, 7>(y, v, lane, nper); break;
+            case 0: bt_reflector<RB, NCOL, PER, 0>(y, v, lane, nper); break;
+            case 1: bt_reflector<RB, NCOL, PER, 1>(y, v, lane, nper); break;
+            case 2: bt_reflector<RB, NCOL, PER, 2>(y, v, lane, nper); break;
+            case 3: bt_reflector<RB, NCOL, PER, 3>(y, v, lane, nper); break;
+            case 4: bt_reflector<RB, NCOL, PER, 4>(y, v, lane, nper); break;
+            case 5: bt_reflector<RB, NCOL, PER, 5>(y, v, lane, nper); break;
+            case 6: bt_reflector<RB, NCOL, PER, 6>(y, v, lane, nper); break;
+            default: bt_reflector<RB, NCOL, PER, 7>(y, v, lane, nper); break;
           }
         }
       }

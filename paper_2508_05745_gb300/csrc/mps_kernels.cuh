@@ -596,7 +596,8 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_contract_tc(const __grid_co
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = s_tmem;
-  const bool ok = tc::gemm(&mapA, &mapB, (int)t, 2 * dl, dm, dr, capr, sm, bars, tmem, th, 2 * dr, &s_err);
+  const bool ok = tc::gemm(&mapA, &mapB, (int)t, 2 * dl, dm, dr, capr, site_ptr(s, q, t), s.cap[q + 1],
+                           site_ptr(s, q + 1, t), sm, bars, tmem, th, 2 * dr, &s_err);
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
   if (!ok) {
     if (threadIdx.x == 0) atomicOr(s.status + t, (int32_t)TS_COPY);
@@ -678,8 +679,8 @@ HeevView<double> heev_view(const SimView<R>& s) {
 }
 
 // ---- split and truncate ------------------------------------------------------
-// U (ws2, complex128, column-major, ng x keep) holds the kept eigenvectors of
-// the Gram matrix; they enter the products in the storage precision.  side 0 (left Gram, centre -> q+1):
+// U (ws2, column-major, ng x keep, in the storage precision: the eigensolver
+// back-transforms in it) holds the kept eigenvectors of the Gram matrix.  side 0 (left Gram, centre -> q+1):
 //   A_q = U (left-orthonormal), B = U^dagger Theta, R = Theta - U B,
 //   A_{q+1} = B / ||B||.
 // side 1 (right Gram, centre -> q):
@@ -700,8 +701,10 @@ __global__ void __launch_bounds__(kGemmThreads) k_split(SimView<R> s, int q, int
   const int keep = s.kept[t];
   const double tot = s.trace[t];
   const cpx<R>* th = s.ws0 + t * s.ws_stride;
-  const zd* U64 = s.u64 + t * s.ws_stride;
-  auto U = [&](int64_t e) { return cast<R>(U64[e]); };
+  // the eigensolver writes U in the storage precision at the start of this
+  // trajectory's complex128 slot of ws2
+  const cpx<R>* Us = reinterpret_cast<const cpx<R>*>(s.u64 + t * s.ws_stride);
+  auto U = [&](int64_t e) { return Us[e]; };
   const int64_t ld = 2 * dr;
   cpx<R>* A = site_ptr(s, q, t);
   cpx<R>* B = site_ptr(s, q + 1, t);

@@ -157,6 +157,15 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
+// L2 prefetch of bytes (a multiple of 16) from a 16-byte-aligned address, in
+// pieces of at most 32 KB.
+__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
+  const char* c = static_cast<const char*>(p);
+  for (uint32_t o = 0; o < bytes; o += 32768u) {
+    const uint32_t n = min(32768u, bytes - o);
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(c + o), "r"(n) : "memory");
+  }
+}
 // Bounded wait that also gives up once *err is set; a timeout sets *err.
 __device__ __forceinline__ bool wait_or_err(uint64_t* bar, uint32_t parity, volatile int* err) {
   const long long t0 = clock64();
@@ -184,13 +193,17 @@ __device__ __forceinline__ void init_bars(uint64_t* bars) {
 // Theta (M x N = 2 dr, row-major, ldc even, C 16-byte aligned; M <= 256,
 // N <= 256) = A B for one trajectory t: A from the A map (site q as [2 cap_q][cap_{q+1}] complex64,
 // box 8 x 128, 64-byte swizzle), B from the B map (site q + 1 as [2
-// cap_{q+1}][cap_{q+2}], box cap_{q+2} x 16; cap_{q+2} <= 128 and even).  Called by all kThreads threads
+// cap_{q+1}][cap_{q+2}], box cap_{q+2} x 16; cap_{q+2} <= 128 and even);
+// a_slot, b_slot: the same two site slots of trajectory t (capm = cap_{q+1}
+// columns of A; their first M and 2 K rows are prefetched into L2 at the start
+// of each half of N, ahead of the tile copies).  Called by all kThreads threads
 // once per CTA; bars: kNumBars mbarriers initialised by init_bars; tmem: the
 // 512-column allocation; err: a shared int set to 0.  Returns false on a
 // timeout (uniform over the CTA).
 __device__ __noinline__ bool gemm(const CUtensorMap* mapA, const CUtensorMap* mapB, int t, int M, int K, int dr,
-                                  int capr, unsigned char* sm, uint64_t* bars, uint32_t tmem, cpx<float>* C,
-                                  int ldc, volatile int* err) {
+                                  int capr, const cpx<float>* a_slot, int capm, const cpx<float>* b_slot,
+                                  unsigned char* sm, uint64_t* bars, uint32_t tmem, cpx<float>* C, int ldc,
+                                  volatile int* err) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int N = 2 * dr, nhalf = (N + kNH - 1) / kNH;
   const int nchunk = (K + kKC - 1) / kKC, G = nhalf * nchunk;
@@ -206,6 +219,10 @@ __device__ __noinline__ bool gemm(const CUtensorMap* mapA, const CUtensorMap* ma
       const uint32_t abytes = (uint32_t)(nmt * kAtile), bbytes = (uint32_t)(2 * kKC * capr * 8);
       auto issue_tma = [&](int x) {                // chunk x (K chunk x % nchunk) into stage x % kNTma
         const int st = x % kNTma, c = x % nchunk;
+        if (c == 0) {                              // first chunk of a half: operands into L2
+          prefetch_l2(a_slot, (uint32_t)M * (uint32_t)capm * 8u);
+          prefetch_l2(b_slot, (uint32_t)(2 * K) * (uint32_t)capr * 8u);
+        }
         unsigned char* dst = sm + st * kTmaStage;
         mbar_expect_tx(&tma_full[st], abytes + bbytes);
         for (int mt = 0; mt < nmt; ++mt) tma_load_3d(dst + mt * kAtile, mapA, c * kKC, mt * 128, t, &tma_full[st]);
