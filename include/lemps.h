@@ -115,6 +115,13 @@ typedef struct {
                              device memory (and 90 % of what is free).  When
                              n_traj exceeds it, the handle runs in waves (see
                              measure) */
+  int32_t eigvec_fp64;    /* LEMPS_MIXED only: 1 = back-transform the kept
+                             eigenvectors of the split in FP64 as well (FP64-
+                             accurate eigenpairs, rounded to complex64 when the
+                             split uses them); 0 = back-transform them in
+                             complex64, the precision they are used in (the
+                             eigenvalues, the truncation and the tridiagonal
+                             eigenvectors are FP64 either way) */
 } lemps_config;
 
 typedef struct {

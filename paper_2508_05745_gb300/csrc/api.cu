@@ -165,6 +165,8 @@ struct lemps_sim {
     v.g64 = reinterpret_cast<zd*>(ws[1]);
     v.u64 = reinterpret_cast<zd*>(ws[2]);
     v.h64 = reinterpret_cast<zd*>(ws[3]);
+    // complex128 eigenvectors in the FP64 mode, and in the mixed one on request
+    v.u_fp64 = (sizeof(R) == 8 || cfg.eigvec_fp64) ? 1 : 0;
     v.ws_stride = ws_stride;
     v.evals = evals;
     v.rho12 = rho12;
@@ -265,18 +267,25 @@ constexpr int kHeevThreads = 512;
 // back-transformation (and U) in the storage precision;
 // keeps the top min(chi_max, #{l > cutoff * trace}) eigenpairs (vectors = 1)
 // or computes every eigenvalue (vectors = 0, cutoff = 0).
-template <class R>
-void launch_heev(lemps_sim* h, int q, int mode, double cutoff, int keep_max, int vectors) {
+template <class RB>
+void launch_heev_as(lemps_sim* h, const HeevView<double>& v, int q, int mode, double cutoff, int keep_max,
+                    int vectors) {
   const size_t smem = HeevSmem<double>::kBytes;
-  static bool attr = false;
+  static bool attr = false;  // one opt-in per instantiation
   if (!attr) {
-    cudaFuncSetAttribute(k_heev<double, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_heev<double, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr = true;
   }
   h->timed(LEMPS_K_EIG, [&] {
-    k_heev<double, R><<<(unsigned)h->B, kHeevThreads, smem, h->stream>>>(heev_view(h->view<R>()), q, mode, cutoff,
-                                                                       keep_max, vectors);
+    k_heev<double, RB><<<(unsigned)h->B, kHeevThreads, smem, h->stream>>>(v, q, mode, cutoff, keep_max, vectors);
   });
+}
+
+template <class R>
+void launch_heev(lemps_sim* h, int q, int mode, double cutoff, int keep_max, int vectors) {
+  const SimView<R> sv = h->view<R>();
+  if (sv.u_fp64) launch_heev_as<double>(h, heev_view(sv), q, mode, cutoff, keep_max, vectors);
+  else launch_heev_as<float>(h, heev_view(sv), q, mode, cutoff, keep_max, vectors);
 }
 
 // Two-site contraction of the pair (q, q+1): on the tensor cores in mixed
@@ -504,6 +513,7 @@ lemps_status sim_create(const lemps_config* cfg, lemps_handle* out) {
     return fail(LEMPS_EINVAL, "sim_create: global layering holds bonds of 2 chi_max, so chi_max must be <= 64");
   if ((cfg->alloc == nullptr) != (cfg->free == nullptr)) return fail(LEMPS_EINVAL, "sim_create: alloc and free go together");
   if (cfg->max_traj_in_flight < 0) return fail(LEMPS_EINVAL, "sim_create: max_traj_in_flight must be >= 0");
+  if (cfg->eigvec_fp64 != 0 && cfg->eigvec_fp64 != 1) return fail(LEMPS_EINVAL, "sim_create: eigvec_fp64 must be 0 or 1");
   lemps_sim* h = new lemps_sim();
   h->cfg = *cfg;
   h->n = cfg->n_qubits;

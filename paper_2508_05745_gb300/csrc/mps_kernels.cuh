@@ -30,11 +30,14 @@ struct SimView {
   cpx<R>* ws2;               // [B][ws_stride] eigenvectors / Q factor
   cpx<R>* ws3;               // [B][ws_stride] scratch
   // complex128 views of ws1..ws3 (allocated at 16 bytes per entry in both
-  // precisions): the Gram matrix, its eigenvectors and the eigensolver's
-  // reflectors are FP64 in both modes
+  // precisions): the Gram matrix and the eigensolver's tridiagonalization
+  // are FP64 in both modes; the reflectors and the kept eigenvectors are
+  // complex128 when u_fp64 is set, else cpx<R> at the start of each
+  // trajectory's complex128 slot
   zd* g64;
   zd* u64;
   zd* h64;
+  int32_t u_fp64;
   int64_t ws_stride;         // (2 chi)^2
   double* evals;             // [B][2 chi]
   zd* rho12;                 // [B][16]
@@ -679,8 +682,9 @@ HeevView<double> heev_view(const SimView<R>& s) {
 }
 
 // ---- split and truncate ------------------------------------------------------
-// U (ws2, column-major, ng x keep, in the storage precision: the eigensolver
-// back-transforms in it) holds the kept eigenvectors of the Gram matrix.  side 0 (left Gram, centre -> q+1):
+// U (ws2, column-major, ng x keep; complex128 or the storage precision, as
+// the eigensolver back-transformed it) holds the kept eigenvectors of the
+// Gram matrix; they enter the products in the storage precision.  side 0 (left Gram, centre -> q+1):
 //   A_q = U (left-orthonormal), B = U^dagger Theta, R = Theta - U B,
 //   A_{q+1} = B / ||B||.
 // side 1 (right Gram, centre -> q):
@@ -701,10 +705,12 @@ __global__ void __launch_bounds__(kGemmThreads) k_split(SimView<R> s, int q, int
   const int keep = s.kept[t];
   const double tot = s.trace[t];
   const cpx<R>* th = s.ws0 + t * s.ws_stride;
-  // the eigensolver writes U in the storage precision at the start of this
-  // trajectory's complex128 slot of ws2
-  const cpx<R>* Us = reinterpret_cast<const cpx<R>*>(s.u64 + t * s.ws_stride);
-  auto U = [&](int64_t e) { return Us[e]; };
+  // the eigensolver writes U in complex128 (u_fp64) or in the storage
+  // precision, at the start of this trajectory's complex128 slot of ws2
+  const zd* U64 = s.u64 + t * s.ws_stride;
+  const cpx<R>* Us = reinterpret_cast<const cpx<R>*>(U64);
+  const bool u64 = s.u_fp64 != 0;
+  auto U = [&](int64_t e) { return u64 ? cast<R>(U64[e]) : Us[e]; };
   const int64_t ld = 2 * dr;
   cpx<R>* A = site_ptr(s, q, t);
   cpx<R>* B = site_ptr(s, q + 1, t);

@@ -44,7 +44,7 @@ class Config(ctypes.Structure):
                 ("precision", ctypes.c_int32), ("unravel_mode", ctypes.c_int32), ("log_capacity", ctypes.c_int32),
                 ("eps_max", ctypes.c_double), ("cuda_stream", ctypes.c_void_p), ("alloc", ALLOC_FN),
                 ("free", FREE_FN), ("alloc_ctx", ctypes.c_void_p), ("layering", ctypes.c_int32),
-                ("max_traj_in_flight", ctypes.c_int64)]
+                ("max_traj_in_flight", ctypes.c_int64), ("eigvec_fp64", ctypes.c_int32)]
 
 
 class LayerStruct(ctypes.Structure):
@@ -127,7 +127,7 @@ class Simulation:
     def __init__(self, n_qubits: int, chi_max: int, n_traj: int, seed: int = 0, precision: str = "fp64",
                  unravel: str = "optimal", cutoff: Optional[float] = None, traj_offset: int = 0,
                  log_capacity: int = 0, eps_max: float = 4.0, stream=None, torch_allocator: bool = True,
-                 layering: str = "local", max_traj_in_flight: int = 0):
+                 layering: str = "local", max_traj_in_flight: int = 0, eigvec_fp64: bool = False):
         torch = _require_cuda()
         lib = load()
         self.n, self.chi, self.B = int(n_qubits), int(chi_max), int(n_traj)
@@ -148,6 +148,7 @@ class Simulation:
         cfg.log_capacity = int(log_capacity)
         cfg.eps_max = float(eps_max)
         cfg.max_traj_in_flight = int(max_traj_in_flight)
+        cfg.eigvec_fp64 = 1 if eigvec_fp64 else 0
         cfg.cuda_stream = self.stream.cuda_stream
         self._cb = None
         if torch_allocator:

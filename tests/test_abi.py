@@ -84,3 +84,19 @@ def test_misaligned_allocator_blocks_are_refused_and_freed(lib_path):
     assert b"16-byte aligned" in lib.lemps_last_error()
     assert h.value is None
     assert len(handed) > 3 and sorted(freed) == sorted(handed)
+
+
+def test_eigvec_fp64_flag_is_validated(lib_path):
+    """lemps_config.eigvec_fp64 takes 0 or 1; any other value fails sim_create
+    with LEMPS_EINVAL before any device call (host only)."""
+    import ctypes
+    from paper_2508_05745_gb300 import lemps as L
+    lib = L.load()
+    cfg = L.Config(n_qubits=8, chi_max=16, trunc_cutoff=1e-12, n_traj=4, traj_offset=0, seed=1,
+                   precision=L.LEMPS_MIXED, unravel_mode=L.LEMPS_UNRAVEL_OPTIMAL, log_capacity=0, eps_max=2.0,
+                   cuda_stream=None, alloc=L.ALLOC_FN(0), free=L.FREE_FN(0), alloc_ctx=None,
+                   layering=L.LEMPS_LAYER_LOCAL, max_traj_in_flight=4, eigvec_fp64=2)
+    h = ctypes.c_void_p()
+    assert lib.sim_create(ctypes.byref(cfg), ctypes.byref(h)) == L.LEMPS_EINVAL
+    assert b"eigvec_fp64" in lib.lemps_last_error()
+    assert h.value is None

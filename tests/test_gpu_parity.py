@@ -34,9 +34,10 @@ def L():
 
 
 def run_gpu(L, circ, chi, n_traj, seed, precision="fp64", unravel="optimal", cutoff=None, traj_offset=0,
-            layering="local"):
+            layering="local", eigvec_fp64=False):
     sim = L.Simulation(circ.n_qubits, chi, n_traj, seed=seed, precision=precision, unravel=unravel,
-                       cutoff=cutoff, log_capacity=circ.n_gates, traj_offset=traj_offset, layering=layering)
+                       cutoff=cutoff, log_capacity=circ.n_gates, traj_offset=traj_offset, layering=layering,
+                       eigvec_fp64=eigvec_fp64)
     sim.run(circ)
     res = sim.measure()
     branches = np.zeros((n_traj, 2 * circ.n_gates), dtype=np.int32)
@@ -174,17 +175,18 @@ def mixed_tol(ref):
     return max(1e-4, 1e-6 / max(g, 1e-300))
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed", 1e-4)])
-def test_truncated_run_matches_oracle_mps(L, precision, tol):
+@pytest.mark.parametrize("precision,tol,vec64", [("fp64", 1e-10, True), ("mixed", 1e-4, False), ("mixed", 1e-4, True)])
+def test_truncated_run_matches_oracle_mps(L, precision, tol, vec64):
     """Heavy truncation (chi=4, cutoff 1e-14) on a 10-qubit depolarizing
     brickwork: every trajectory has the oracle's branch sequence, and its
     observables and error bound match the oracle's FP64 MPS trajectory (FP64:
     1e-10; mixed: 1e-4, or 1e-6 over the smallest relative cut gap where the
-    cut falls between close Schmidt values, see mixed_tol; the Gram eigensolve
-    is FP64 in both modes)."""
+    cut falls between close Schmidt values, see mixed_tol).  The Gram
+    eigensolve is FP64 in both modes; the mixed mode is run with its kept
+    eigenvectors back-transformed in complex64 (default) and in FP64."""
     circ = I.random_brickwork(10, 10, I.depolarizing_kraus(0.05), seed=4)
     n_traj = 16
-    sim, res, br = run_gpu(L, circ, 4, n_traj, seed=3, precision=precision, cutoff=1e-14)
+    sim, res, br = run_gpu(L, circ, 4, n_traj, seed=3, precision=precision, cutoff=1e-14, eigvec_fp64=vec64)
     sim.destroy()
     errs = []
     loose = 0
@@ -622,6 +624,28 @@ def test_canonical_form_after_truncation(L, precision, tol):
                    if all(left[k] < tol for k in range(c)) and all(right[k] < tol for k in range(c + 1, n))]
         assert centres, (precision, t, np.max(left), np.max(right))
     sim.destroy()
+
+
+def test_mixed_eigenvector_back_transform_precisions_agree(L):
+    """Mixed mode at chi=128 (Gram matrices of size 256) with the kept
+    eigenvectors back-transformed in complex64 (default) and in FP64: the same
+    branch sequences, and observables that differ by far less than the mixed
+    tolerance (the back-transformation adds about n eps_32 to vectors that the
+    split rounds to complex64 in either case)."""
+    circ = I.random_brickwork(16, 16, I.depolarizing_kraus(1.0), 5, coin_p=0.005)
+    out = {}
+    for vec64 in (False, True):
+        sim, res, br = run_gpu(L, circ, 128, 8, seed=5, precision="mixed", cutoff=1e-12, eigvec_fp64=vec64)
+        assert res["n_failed"] == 0
+        tensors, bonds = sim.export_mps(0)
+        assert bonds.max() == 128
+        sim.destroy()
+        out[vec64] = (res, br)
+    (ra, ba), (rb, bb) = out[False], out[True]
+    assert np.array_equal(ba, bb)
+    d = max(np.abs(ra["z"] - rb["z"]).max(), np.abs(ra["zz"] - rb["zz"]).max(), np.abs(ra["s_half"] - rb["s_half"]).max())
+    print(f"complex64 vs FP64 back-transformation: max observable difference {d:.2e}")
+    assert d < 1e-5
 
 
 # --- the chi=128 benchmark configuration, sampled -------------------------------------
