@@ -18,8 +18,9 @@ created afresh and pre-evolved again, untimed (`layer_plan`).  One bond update
 = one gate on one trajectory.  The MPS state of the batch is far larger than
 the 129 MB L2, so every step streams it from HBM.
 
---impl reference runs the CPU oracle (oracle/, FP64) on the host cores for a
-bounded sample of the same workload and prints its own line.
+--impl reference runs the C++ FP64 oracle (oracle/mps_oracle.cpp, OpenMP) on
+the host cores for a bounded sample of the same workload and prints its own
+line; the CPU baseline of the main line is the same oracle.
 --gpus N without a launcher-provided WORLD_SIZE starts N ranks itself through
 torch.distributed.run (replicas, one GPU each).
 """
@@ -60,7 +61,8 @@ def parse(argv=None):
     ap.add_argument("--depth", type=int, default=32)
     ap.add_argument("--chi", type=int, default=128)
     ap.add_argument("--seed", type=int, default=0)
-    ap.add_argument("--cpu-sample-s", type=float, default=20.0, help="target CPU seconds for the oracle baseline")
+    ap.add_argument("--cpu-sample-s", type=float, default=20.0,
+                    help="target timed seconds of the CPU oracle baseline (after its untimed pre-evolution)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -383,58 +385,64 @@ def observable_error(res_m, res_d, br_m=None, br_d=None):
 
 # --- CPU oracle baseline -------------------------------------------------------------------
 
-def _oracle_worker(job):
-    n, traj, seed, chi, depth, pre, budget_s = job
-    from oracle import trajectories as T
+def _oracle_batches(args, sizes, pre_layers, cores):
+    """One C++ oracle batch per system size of the workload (the same seeded
+    circuits as the GPU arm), one trajectory per host core, evolved untimed
+    through the pre-evolution layers so that the middle bonds sit at chi_max."""
+    from oracle import cpp
     from paper_2508_05745_gb300 import inputs as I
-    w = I.workload_uneven(seed=seed, n_traj=16, depth=depth)
-    circ = w["circuits"][n]
-    marks = []
-
-    class Stop(Exception):
-        pass
-
-    def cb(_):
-        marks.append(time.perf_counter())
-        if len(marks) > pre and marks[-1] - marks[pre - 1] > budget_s:
-            raise Stop
-
-    try:
-        T.mps_trajectory(circ, traj, seed, chi_max=chi, cutoff=1e-20, layer_callback=cb)
-    except Stop:
-        pass
-    done = len(marks)
-    if done <= pre:
-        return 0, 0.0
-    upd = sum(len(circ.layers[l].left_qubits) for l in range(pre, done))
-    return upd, marks[done - 1] - marks[pre - 1]
+    w = I.workload_uneven(seed=args.seed, n_traj=cores, depth=args.depth)
+    batches = {}
+    for n in sizes:
+        b = cpp.Batch(w["circuits"][n], 0, cores, args.seed, args.chi, 1e-20)
+        b.run(0, pre_layers, cores)
+        batches[n] = b
+    return w, batches
 
 
 def cpu_baseline(args, pre_layers, budget_s):
-    import multiprocessing as mp
+    """The C++17 FP64 oracle (oracle/mps_oracle.cpp, OpenMP, one trajectory per
+    core) on the host cores: for each system size, layers after the untimed
+    pre-evolution are timed with all cores until about budget_s / #sizes
+    seconds have passed (at least one layer); then one further layer of one
+    trajectory of the middle size with one thread gives the 1-core figure.
+    rate = bond updates / wall seconds."""
     cores = os.cpu_count() or 1
-    # one BLAS thread per worker: set before the spawned children import numpy
-    saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
-    for k in saved:
-        os.environ[k] = "1"
-    jobs = [(48, t, args.seed, args.chi, args.depth, pre_layers, budget_s) for t in range(cores)]
-    ctx = mp.get_context("spawn")
+    sizes = [int(x) for x in args.sizes.split(",")]
+    w, batches = _oracle_batches(args, sizes, pre_layers, cores)
+    by_n, upd_tot, t_tot = {}, 0, 0.0
     try:
-        with ctx.Pool(cores) as pool:
-            res = pool.map(_oracle_worker, jobs)
+        for n in sizes:
+            circ, b = w["circuits"][n], batches[n]
+            l, upd, t = pre_layers, 0, 0.0
+            while l < args.depth and (l == pre_layers or t < budget_s / len(sizes)):
+                t0 = time.perf_counter()
+                b.run(l, l + 1, cores)
+                t += time.perf_counter() - t0
+                upd += cores * len(circ.layers[l].left_qubits)
+                l += 1
+            by_n[str(n)] = {"bond_updates": upd, "seconds": round(t, 3), "rate": upd / t, "layers": [pre_layers, l]}
+            upd_tot += upd
+            t_tot += t
+        n1 = sizes[len(sizes) // 2]
+        l1 = by_n[str(n1)]["layers"][1]
+        one = None
+        if l1 < args.depth:
+            t0 = time.perf_counter()
+            batches[n1].run_range(0, 1, l1, l1 + 1, 1)
+            t1 = time.perf_counter() - t0
+            u1 = len(w["circuits"][n1].layers[l1].left_qubits)
+            one = {"value": u1 / t1, "unit": UNIT, "cores": 1, "n": n1, "layer": l1, "bond_updates": u1,
+                   "seconds": round(t1, 3)}
     finally:
-        for k, v in saved.items():
-            if v is None:
-                os.environ.pop(k, None)
-            else:
-                os.environ[k] = v
-    upd = sum(r[0] for r in res)
-    secs = sum(r[1] for r in res)
-    rate = upd / (secs / cores) if secs > 0 else 0.0
-    return {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{cores} trajectories of the n=48 circuit run in parallel (spawn pool, 1 thread each); "
-                      f"layers {pre_layers}.. timed per layer for ~{budget_s:.0f} s each; "
-                      f"rate = updates / (summed timed seconds / cores)"}
+        for b in batches.values():
+            b.close()
+    return {"value": upd_tot / t_tot, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "impl": "C++17 FP64 oracle (oracle/mps_oracle.cpp), OpenMP over trajectories",
+            "by_n": by_n, "one_core": one,
+            "sample": f"per n in {sizes}: {cores} trajectories (one per core) pre-evolved untimed through "
+                      f"{pre_layers} layers, then whole layers timed with all cores (~{budget_s:.0f} s in all); "
+                      f"1-core: one more layer of one n={n1} trajectory on one thread"}
 
 
 # --- roofline -------------------------------------------------------------------------------
@@ -694,16 +702,48 @@ def gpu_launches(prof, steps):
 
 
 def main_reference(args):
+    """The reference arm: the C++ FP64 oracle on the host cores, --warmup W
+    untimed and --steps K timed steps on the same workload; a step is one layer
+    of one system size for one trajectory per core (sizes taken in turn, after
+    an untimed pre-evolution).  Rank 0 only."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    cb = cpu_baseline(args, args.pre_layers, args.cpu_sample_s)
-    line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": 0,
-            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD},
+    cores = os.cpu_count() or 1
+    sizes = [int(x) for x in args.sizes.split(",")]
+    w, batches = _oracle_batches(args, sizes, args.pre_layers, cores)
+    nxt = {n: args.pre_layers for n in sizes}
+
+    def step(i):
+        n = sizes[i % len(sizes)]
+        l = nxt[n]
+        if l >= args.depth:
+            raise SystemExit("reference arm: more steps than the depth-32 circuit has layers after the pre-evolution")
+        batches[n].run(l, l + 1, cores)
+        nxt[n] = l + 1
+        return cores * len(w["circuits"][n].layers[l].left_qubits)
+
+    try:
+        for i in range(args.warmup):
+            step(i)
+        t0 = time.perf_counter()
+        upd = sum(step(args.warmup + i) for i in range(args.steps))
+        el = time.perf_counter() - t0
+    finally:
+        for b in batches.values():
+            b.close()
+    value = upd / el
+    cb = {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+          "impl": "C++17 FP64 oracle (oracle/mps_oracle.cpp), OpenMP over trajectories",
+          "sample": f"{args.steps} timed steps (after {args.warmup} untimed), each one layer of one n in {sizes} "
+                    f"(in turn) for {cores} trajectories, one per core, after {args.pre_layers} untimed layers"}
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * el / max(args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "trajectories": cores * len(sizes), "by_n": {str(n): cores for n in sizes},
+                       "pre_layers": args.pre_layers},
             "cpu_baseline": cb,
-            "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
 
