@@ -487,24 +487,29 @@ __global__ void __launch_bounds__(kGemmThreads, sizeof(R) == 4 ? 2 : 1) k_move_c
 // sum_{a,b} Theta[a,s1,s2,b] conj(Theta[a,t1,t2,b]) in FP64.
 // rho12[(s1 s2), (t1 t2)] = sum_{a,b} Theta[a,s1,s2,b] conj(Theta[a,t1,t2,b]) in
 // FP64 from the two-site tensor in ws0 (row-major, ld = 2 dr).
+// Compensated FP32 sum (s, c): TwoSum (Knuth) keeps each addition's rounding
+// error in c, so s + c carries about twice FP32's precision.
+__device__ __forceinline__ void comp_add(float& s, float& c, float x) {
+  const float t = s + x, bp = t - s;
+  c += (s - (t - bp)) + (x - bp);
+  s = t;
+}
+
 template <class R>
 __device__ __forceinline__ void contract_rho12(const SimView<R>& s, int64_t t, const cpx<R>* th, int dl, int dr,
-                                               double* red) {
+                                               double* red, double* scratch) {
   const int64_t ld = 2 * dr;
-  // rho12 is Hermitian: the 10 entries i <= j are formed.  Products in the
-  // storage precision, partial sums over 8 entries of Theta in that
-  // precision, accumulated in FP64 (FP64 throughput is ~1/64 of FP32 here).
-  double acc[10][2];
-#pragma unroll
-  for (int p = 0; p < 10; ++p) acc[p][0] = acc[p][1] = 0.0;
   const int nel = dl * dr;
-  for (int e0 = threadIdx.x; e0 < nel; e0 += 8 * blockDim.x) {
-    R part[10][2];
+  if constexpr (sizeof(R) == 4) {
+    // rho12 is Hermitian: the 10 entries i <= j are formed.  Products in
+    // complex64, each thread's sums in compensated FP32 (an FP64 instruction
+    // costs the FP64 pipe 64 cycles per warp here), combined over the warp with
+    // FP32 shuffles; only the per-warp partials are added in FP64.  scratch:
+    // 20 x (warps) doubles of shared memory.
+    float sum[20], cmp[20];
 #pragma unroll
-    for (int p = 0; p < 10; ++p) part[p][0] = part[p][1] = 0;
-    for (int u = 0; u < 8; ++u) {
-      const int e = e0 + u * blockDim.x;
-      if (e >= nel) break;
+    for (int p = 0; p < 20; ++p) sum[p] = cmp[p] = 0.f;
+    for (int e = threadIdx.x; e < nel; e += blockDim.x) {
       const int a = e / dr, b = e - a * dr;
       cpx<R> v[4];
       v[0] = th[(int64_t)(2 * a) * ld + b];
@@ -516,28 +521,81 @@ __device__ __forceinline__ void contract_rho12(const SimView<R>& s, int64_t t, c
       for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = i; j < 4; ++j, ++p) {
-          part[p][0] += v[i].re * v[j].re + v[i].im * v[j].im;
-          part[p][1] += v[i].im * v[j].re - v[i].re * v[j].im;
+          comp_add(sum[2 * p], cmp[2 * p], v[i].re * v[j].re + v[i].im * v[j].im);
+          comp_add(sum[2 * p + 1], cmp[2 * p + 1], v[i].im * v[j].re - v[i].re * v[j].im);
         }
     }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    // butterfly: every lane ends with the warp's totals; lane p keeps value p
+    float ms = 0.f, mc = 0.f;
 #pragma unroll
-    for (int p = 0; p < 10; ++p) {
-      acc[p][0] += (double)part[p][0];
-      acc[p][1] += (double)part[p][1];
-    }
-  }
-  int p = 0;
+    for (int p = 0; p < 20; ++p) {
+      float sv = sum[p], cv = cmp[p];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = i; j < 4; ++j, ++p) {
-      double re = block_sum(acc[p][0], red);
-      double im = block_sum(acc[p][1], red);
-      if (threadIdx.x == 0) {
-        s.rho12[t * 16 + i * 4 + j] = mk(re, im);
-        if (j != i) s.rho12[t * 16 + j * 4 + i] = mk(re, -im);
+      for (int o = 16; o > 0; o >>= 1) {
+        const float s2 = __shfl_xor_sync(0xffffffffu, sv, o), c2 = __shfl_xor_sync(0xffffffffu, cv, o);
+        cv += c2;
+        comp_add(sv, cv, s2);
+      }
+      if (lane == p) {
+        ms = sv;
+        mc = cv;
       }
     }
+    if (lane < 20) scratch[lane * nw + warp] = (double)ms + (double)mc;
+    __syncthreads();
+    if (threadIdx.x < 10) {
+      const int p = threadIdx.x;
+      double re = 0.0, im = 0.0;
+      for (int w = 0; w < nw; ++w) {
+        re += scratch[(2 * p) * nw + w];
+        im += scratch[(2 * p + 1) * nw + w];
+      }
+      int i = 0, j = p;   // p-th pair i <= j in row order
+      while (j >= 4 - i) {
+        j -= 4 - i;
+        ++i;
+      }
+      j += i;
+      s.rho12[t * 16 + i * 4 + j] = mk(re, im);
+      if (j != i) s.rho12[t * 16 + j * 4 + i] = mk(re, -im);
+    }
+    return;
+  } else {
+    (void)scratch;
+    // rho12 is Hermitian: the 10 entries i <= j are formed, in FP64.
+    double acc[10][2];
+#pragma unroll
+    for (int p = 0; p < 10; ++p) acc[p][0] = acc[p][1] = 0.0;
+    for (int e = threadIdx.x; e < nel; e += blockDim.x) {
+      const int a = e / dr, b = e - a * dr;
+      cpx<R> v[4];
+      v[0] = th[(int64_t)(2 * a) * ld + b];
+      v[1] = th[(int64_t)(2 * a) * ld + dr + b];
+      v[2] = th[(int64_t)(2 * a + 1) * ld + b];
+      v[3] = th[(int64_t)(2 * a + 1) * ld + dr + b];
+      int p = 0;
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = i; j < 4; ++j, ++p) {
+          acc[p][0] += v[i].re * v[j].re + v[i].im * v[j].im;
+          acc[p][1] += v[i].im * v[j].re - v[i].re * v[j].im;
+        }
+    }
+    int p = 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = i; j < 4; ++j, ++p) {
+        double re = block_sum(acc[p][0], red);
+        double im = block_sum(acc[p][1], red);
+        if (threadIdx.x == 0) {
+          s.rho12[t * 16 + i * 4 + j] = mk(re, im);
+          if (j != i) s.rho12[t * 16 + j * 4 + i] = mk(re, -im);
+        }
+      }
+  }
 }
 
 template <class R>
@@ -561,7 +619,7 @@ __global__ void __launch_bounds__(kGemmThreads) k_contract(SimView<R> s, int q) 
       },
       [&](int i, int j, cpx<R> v) { th[(int64_t)i * ld + j] = v; }, sm);
   __syncthreads();
-  contract_rho12(s, t, th, dl, dr, red);
+  contract_rho12(s, t, th, dl, dr, red, reinterpret_cast<double*>(&sm));
 }
 
 // The same contraction on the tensor cores (mixed precision; 3xTF32 complex
@@ -606,7 +664,8 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_contract_tc(const __grid_co
     if (threadIdx.x == 0) atomicOr(s.status + t, (int32_t)TS_COPY);
     return;
   }
-  contract_rho12(s, t, th, dl, dr, red);
+  // the stages of the GEMM are free: scratch for the epilogue's partial sums
+  contract_rho12(s, t, th, dl, dr, red, reinterpret_cast<double*>(sm));
 }
 
 // ---- apply T to Theta and build the Gram matrix ------------------------------
@@ -720,46 +779,74 @@ __global__ void __launch_bounds__(kGemmThreads) k_split(SimView<R> s, int q, int
     return B[(int64_t)(k * 2 + s2) * capr + b];
   };
   double bn = 0.0, rn = 0.0;
+  // The projection B and the residual are formed one block of Theta at a time
+  // (kBlk = 64 columns for side 0, 64 rows for side 1): the block is read by
+  // both products while it is still in L2, and so is U, instead of re-reading
+  // Theta once per output tile row of a whole-matrix product (measured at
+  // chi = 128: 1.54 MB of DRAM traffic per trajectory against 1.28 MB of
+  // operands and outputs; 1.85 MB with blocks of 128, 2.78 MB unblocked).
+  constexpr int kBlk = kGemmBN;
   if (side == 0) {
-    for (int e = threadIdx.x; e < 2 * dl * keep; e += blockDim.x) {
-      const int row = e / keep, k = e % keep;
-      A[(int64_t)row * capm + k] = U((int64_t)k * ng + row);
+    // A_q = U: U is column-major (ng rows), A_q row-major; 32 x 32 tiles
+    // through shared memory keep both sides of the copy contiguous
+    static_assert(sizeof(GemmSmem<R>) >= 32 * 33 * sizeof(cpx<R>), "transpose tile");
+    cpx<R>* tile = reinterpret_cast<cpx<R>*>(&sm);   // 32 x 33
+    for (int r0 = 0; r0 < 2 * dl; r0 += 32)
+      for (int k0 = 0; k0 < keep; k0 += 32) {
+        for (int e = threadIdx.x; e < 1024; e += blockDim.x) {
+          const int kk = e >> 5, rr = e & 31;
+          if (r0 + rr < 2 * dl && k0 + kk < keep) tile[kk * 33 + rr] = U((int64_t)(k0 + kk) * ng + r0 + rr);
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < 1024; e += blockDim.x) {
+          const int rr = e >> 5, kk = e & 31;
+          if (r0 + rr < 2 * dl && k0 + kk < keep) A[(int64_t)(r0 + rr) * capm + k0 + kk] = tile[kk * 33 + rr];
+        }
+        __syncthreads();
+      }
+    for (int j0 = 0; j0 < 2 * dr; j0 += kBlk) {
+      const int nb = min(kBlk, 2 * dr - j0);
+      // B[:, block] = U^dagger Theta[:, block]  (keep x nb)
+      cta_gemm<R, true, false>(
+          keep, nb, 2 * dl, [&](int i, int k) { return conj(U((int64_t)i * ng + k)); },
+          [&](int k, int j) { return th[(int64_t)k * ld + j0 + j]; },
+          [&](int i, int j, cpx<R> v) {
+            bslot(i, j0 + j) = v;
+            bn += (double)norm2(v);
+          },
+          sm);
+      __syncthreads();
+      // residual Theta[:, block] - U B[:, block]
+      cta_gemm<R, false, false>(
+          2 * dl, nb, keep, [&](int i, int k) { return U((int64_t)k * ng + i); },
+          [&](int k, int j) { return bslot(k, j0 + j); },
+          [&](int i, int j, cpx<R> v) { rn += (double)norm2(th[(int64_t)i * ld + j0 + j] - v); }, sm);
+      __syncthreads();
     }
-    // B = U^dagger Theta  (keep x 2dr)
-    cta_gemm<R, true, false>(
-        keep, 2 * dr, 2 * dl, [&](int i, int k) { return conj(U((int64_t)i * ng + k)); },
-        [&](int k, int j) { return th[(int64_t)k * ld + j]; },
-        [&](int i, int j, cpx<R> v) {
-          bslot(i, j) = v;
-          bn += (double)norm2(v);
-        },
-        sm);
-    __syncthreads();
-    // residual Theta - U B
-    cta_gemm<R, false, false>(
-        2 * dl, 2 * dr, keep, [&](int i, int k) { return U((int64_t)k * ng + i); },
-        [&](int k, int j) { return bslot(k, j); },
-        [&](int i, int j, cpx<R> v) { rn += (double)norm2(th[(int64_t)i * ld + j] - v); }, sm);
   } else {
     for (int e = threadIdx.x; e < keep * 2 * dr; e += blockDim.x) {
       const int k = e / (2 * dr), c = e % (2 * dr);
       bslot(k, c) = conj(U((int64_t)k * ng + c));
     }
-    // B = Theta U  (2dl x keep) into A_q
-    cta_gemm<R, true, true>(
-        2 * dl, keep, 2 * dr, [&](int i, int k) { return th[(int64_t)i * ld + k]; },
-        [&](int k, int j) { return U((int64_t)j * ng + k); },
-        [&](int i, int j, cpx<R> v) {
-          A[(int64_t)i * capm + j] = v;
-          bn += (double)norm2(v);
-        },
-        sm);
-    __syncthreads();
-    // residual Theta - B U^dagger
-    cta_gemm<R, true, false>(
-        2 * dl, 2 * dr, keep, [&](int i, int k) { return A[(int64_t)i * capm + k]; },
-        [&](int k, int j) { return conj(U((int64_t)k * ng + j)); },
-        [&](int i, int j, cpx<R> v) { rn += (double)norm2(th[(int64_t)i * ld + j] - v); }, sm);
+    for (int i0 = 0; i0 < 2 * dl; i0 += kBlk) {
+      const int mb = min(kBlk, 2 * dl - i0);
+      // B[block, :] = Theta[block, :] U  (mb x keep) into A_q
+      cta_gemm<R, true, true>(
+          mb, keep, 2 * dr, [&](int i, int k) { return th[(int64_t)(i0 + i) * ld + k]; },
+          [&](int k, int j) { return U((int64_t)j * ng + k); },
+          [&](int i, int j, cpx<R> v) {
+            A[(int64_t)(i0 + i) * capm + j] = v;
+            bn += (double)norm2(v);
+          },
+          sm);
+      __syncthreads();
+      // residual Theta[block, :] - B[block, :] U^dagger
+      cta_gemm<R, true, false>(
+          mb, 2 * dr, keep, [&](int i, int k) { return A[(int64_t)(i0 + i) * capm + k]; },
+          [&](int k, int j) { return conj(U((int64_t)k * ng + j)); },
+          [&](int i, int j, cpx<R> v) { rn += (double)norm2(th[(int64_t)(i0 + i) * ld + j] - v); }, sm);
+      __syncthreads();
+    }
   }
   rn = block_sum(rn, redd);
   bn = block_sum(bn, redd);
