@@ -294,10 +294,13 @@ lemps_status unravel_grad_noalloc(const void* theta, int32_t theta_fp64, int64_t
  * time in milliseconds and the launch count since recording started. */
 enum {
   LEMPS_K_MOVE = 0,      /* centre move (Householder QR / LQ + merge) */
-  LEMPS_K_CONTRACT = 1,  /* two-site contraction + 4x4 reduced density */
+  LEMPS_K_CONTRACT = 1,  /* two-site contraction (tensor cores in mixed mode for
+                            site capacities 64-128) + 4x4 reduced density */
   LEMPS_K_UNRAVEL = 2,   /* noise sites: optimal unraveling + sampling */
   LEMPS_K_GRAM = 3,      /* apply gate and Kraus operators, Gram matrix */
-  LEMPS_K_EIG = 4,       /* Hermitian Jacobi eigensolver */
+  LEMPS_K_EIG = 4,       /* Hermitian eigensolver: Householder tridiagonalization,
+                            Sturm/Newton eigenvalues, inverse iteration,
+                            back-transformation */
   LEMPS_K_SPLIT = 5,     /* truncation and new site tensors */
   LEMPS_K_OTHER = 6,     /* layer bookkeeping */
   LEMPS_NUM_KERNEL_KINDS = 7
