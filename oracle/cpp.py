@@ -60,7 +60,7 @@ def load() -> ctypes.CDLL:
     lib.oracle_batch_run_range.restype = I
     lib.oracle_batch_run_range.argtypes = [P, I64, I64, I, I, I]
     lib.oracle_batch_results.restype = I
-    lib.oracle_batch_results.argtypes = [P, P, P, P, P, P, I]
+    lib.oracle_batch_results.argtypes = [P, P, P, P, P, P, P, I]
     lib.oracle_batch_layer.restype = I
     lib.oracle_batch_layer.argtypes = [P]
     lib.oracle_batch_max_bond.restype = I
@@ -147,9 +147,11 @@ class Batch:
         s = np.zeros(B)
         eps = np.zeros(B)
         br = np.zeros((B, 2 * int(self._keep[0][layer])), dtype=np.int32)   # two noise sites per gate run
-        if self.lib.oracle_batch_results(self.h, _ptr(z), _ptr(zz), _ptr(s), _ptr(eps), _ptr(br), threads) != 0:
+        gap = np.zeros(B)
+        if self.lib.oracle_batch_results(self.h, _ptr(z), _ptr(zz), _ptr(s), _ptr(eps), _ptr(br), _ptr(gap),
+                                         threads) != 0:
             raise ValueError("oracle_batch_results: the trajectories are not at one common layer")
-        return {"z": z, "zz": zz, "s_half": s, "eps_bound": eps, "branch": br}
+        return {"z": z, "zz": zz, "s_half": s, "eps_bound": eps, "branch": br, "min_gap": gap}
 
     def max_bond(self) -> int:
         return self.lib.oracle_batch_max_bond(self.h)

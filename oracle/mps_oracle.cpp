@@ -629,6 +629,9 @@ struct Trajectory {
   double eps_tot = 0.0;
   int layer = 0;
   std::vector<int32_t> branch;
+  // smallest relative gap (w_keep - w_keep+1) / w_1 of the squared Schmidt
+  // values at a truncating cut (1 when no cut truncated)
+  double min_gap = 1.0;
   // outputs
   std::vector<double> z, zz;
   double s_half = 0.0, eps_bound = 0.0;
@@ -771,6 +774,8 @@ double split(Trajectory& T, int q, const std::vector<cd>& th, int dl, int dr, in
   }
   double disc = 0.0;
   for (int k = keep; k < (int)s.size(); ++k) disc += s[k] * s[k];
+  if (keep < (int)s.size())   // a truncating cut: its conditioning
+    T.min_gap = std::min(T.min_gap, (s[keep - 1] * s[keep - 1] - s[keep] * s[keep]) / (s[0] * s[0]));
   const double eps = disc / tot;
   const double nrm = 1.0 / std::sqrt(kept);
   Site& A = T.a[q];
@@ -1047,10 +1052,11 @@ int oracle_batch_run_range(void* hb, int64_t i0, int64_t i1, int l0, int l1, int
 
 // Observables and the error bound of every trajectory: z [n_traj][n], zz
 // [n_traj][n-1], s_half [n_traj], eps_bound [n_traj], branch [n_traj][2 *
-// gates run] (any output may be NULL).  Every trajectory must be at the same
-// layer (-1 otherwise).
+// gates run], min_gap [n_traj] (the smallest relative gap of the squared
+// Schmidt values at a truncating cut; 1 if none) (any output may be NULL).
+// Every trajectory must be at the same layer (-1 otherwise).
 int oracle_batch_results(void* hb, double* z, double* zz, double* s_half, double* eps_bound, int32_t* branch,
-                         int n_threads) {
+                         double* min_gap, int n_threads) {
   Batch* b = static_cast<Batch*>(hb);
   if (!b) return -1;
   for (const auto& t : b->T)   // the branch rows need one common layer
@@ -1069,6 +1075,7 @@ int oracle_batch_results(void* hb, double* z, double* zz, double* s_half, double
     if (s_half) s_half[i] = T.s_half;
     if (eps_bound) eps_bound[i] = T.eps_tot <= b->eps_max - 2.0 ? T.eps_tot : b->eps_max;
     if (branch) std::copy(T.branch.begin(), T.branch.end(), branch + i * (int64_t)T.branch.size());
+    if (min_gap) min_gap[i] = T.min_gap;
   }
   (void)n_threads;
   return 0;

@@ -231,6 +231,42 @@ def test_ad_dephasing_n32_chi64(L):
         assert close(resm["s_half"][t], ref.s_half, 1e-4)
 
 
+def test_ad_dephasing_config_against_cpp_oracle(L):
+    """The AD-then-dephasing configuration at its shape (n=32, depth 20,
+    chi=64, composed 4-Kraus channel), 32 trajectories against the C++ FP64
+    oracle on the same Philox streams: every branch sequence equal; FP64
+    observables and error bounds to 1e-10; mixed observables to 1e-4, or to
+    1e-6 over the trajectory's smallest relative cut gap where a truncation
+    falls between close Schmidt values (the conditioning reading of the mixed
+    tolerance)."""
+    from oracle import cpp
+    w = I.workload_ad_dephasing(seed=0, n_traj=32)
+    circ = w["circuit"]
+    n_traj = 32
+    ref = cpp.mps_trajectories(circ, 0, n_traj, 0, 64, 1e-20)
+    sim, res, br = run_gpu(L, circ, 64, n_traj, seed=0)
+    sim.destroy()
+    simm, resm, brm = run_gpu(L, circ, 64, n_traj, seed=0, precision="mixed")
+    simm.destroy()
+    worst64 = worstm = 0.0
+    loose = 0
+    for t in range(n_traj):
+        assert list(br[t]) == list(ref["branch"][t]), t
+        assert list(brm[t]) == list(ref["branch"][t]), t
+        e64 = max(np.abs(res["z"][t] - ref["z"][t]).max(), np.abs(res["zz"][t] - ref["zz"][t]).max(),
+                  abs(res["s_half"][t] - ref["s_half"][t]))
+        assert e64 < 1e-10, (t, e64)
+        assert abs(res["eps_bound"][t] - ref["eps_bound"][t]) <= bound_tol(ref["eps_bound"][t], "fp64")
+        tol = max(1e-4, 1e-6 / max(ref["min_gap"][t], 1e-300))
+        loose += tol > 1e-4
+        em = max(np.abs(resm["z"][t] - ref["z"][t]).max(), np.abs(resm["zz"][t] - ref["zz"][t]).max(),
+                 abs(resm["s_half"][t] - ref["s_half"][t]))
+        assert em < tol, (t, em, tol)
+        worst64, worstm = max(worst64, e64), max(worstm, em)
+    print(f"config 2 vs C++ oracle: FP64 worst {worst64:.2e}, mixed worst {worstm:.2e}, "
+          f"trajectories with a cut gap below 1e-2: {loose}")
+
+
 def test_coin_noise_full_depolarizing(L):
     """Two-qubit depolarizing reading: with probability p both qubits are fully
     depolarized (optimal unraveling of each), otherwise nothing happens."""

@@ -70,7 +70,13 @@ def test_untruncated_coin_noise_equals_dense_state_vector():
 
 
 def test_truncated_trajectories_equal_python_mps_oracle():
-    _compare(I.random_brickwork(10, 10, I.depolarizing_kraus(0.05), seed=4), 4, 1e-14, 12, 3, tol=1e-10)
+    circ = I.random_brickwork(10, 10, I.depolarizing_kraus(0.05), seed=4)
+    _compare(circ, 4, 1e-14, 12, 3, tol=1e-10)
+    # the smallest relative cut gap (the conditioning of the truncations)
+    r = cpp.mps_trajectories(circ, 0, 12, 3, 4, 1e-14)
+    for t in range(12):
+        gaps = T.mps_trajectory(circ, t, 3, 4, 1e-14).cut_gaps
+        assert abs(r["min_gap"][t] - (min(gaps) if gaps else 1.0)) < 1e-9
 
 
 @pytest.mark.parametrize("mode,layering", [("given", "local"), ("haar_optimal", "local"), ("optimal", "global")])
