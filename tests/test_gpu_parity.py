@@ -267,6 +267,32 @@ def test_ad_dephasing_config_against_cpp_oracle(L):
           f"trajectories with a cut gap below 1e-2: {loose}")
 
 
+@pytest.mark.parametrize("chi", [100, 127])
+def test_mixed_non_power_of_two_chi_against_cpp_oracle(L, chi):
+    """Mixed mode at chi_max = 100 (even site capacities of 100: the tensor-core
+    contraction with ragged tile boxes, K chunks past the slot width) and
+    chi_max = 127 (odd capacities: the SIMT contraction), n = 18, depth 12,
+    8 trajectories, against the C++ FP64 oracle: the same branches, and
+    observables within 1e-4 (or 1e-6 over the smallest relative cut gap)."""
+    from oracle import cpp
+    circ = I.random_brickwork(18, 12, I.depolarizing_kraus(0.05), seed=11)
+    n_traj = 8
+    ref = cpp.mps_trajectories(circ, 0, n_traj, 4, chi, 1e-12)
+    sim, res, br = run_gpu(L, circ, chi, n_traj, seed=4, precision="mixed", cutoff=1e-12)
+    _, bonds = sim.export_mps(0)
+    sim.destroy()
+    assert bonds.max() == chi
+    worst = 0.0
+    for t in range(n_traj):
+        assert list(br[t]) == list(ref["branch"][t]), t
+        tol = max(1e-4, 1e-6 / max(ref["min_gap"][t], 1e-300))
+        e = max(np.abs(res["z"][t] - ref["z"][t]).max(), np.abs(res["zz"][t] - ref["zz"][t]).max(),
+                abs(res["s_half"][t] - ref["s_half"][t]))
+        assert e < tol, (t, e, tol)
+        worst = max(worst, e)
+    print(f"chi={chi}: mixed worst {worst:.2e}")
+
+
 def test_coin_noise_full_depolarizing(L):
     """Two-qubit depolarizing reading: with probability p both qubits are fully
     depolarized (optimal unraveling of each), otherwise nothing happens."""
