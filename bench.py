@@ -737,7 +737,8 @@ def main_reference(args):
           "impl": "C++17 FP64 oracle (oracle/mps_oracle.cpp), OpenMP over trajectories",
           "sample": f"{args.steps} timed steps (after {args.warmup} untimed), each one layer of one n in {sizes} "
                     f"(in turn) for {cores} trajectories, one per core, after {args.pre_layers} untimed layers"}
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "device": f"host cores ({cores}); no GPU work",
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * el / max(args.steps, 1),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "trajectories": cores * len(sizes), "by_n": {str(n): cores for n in sizes},
