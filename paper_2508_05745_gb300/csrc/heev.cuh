@@ -1000,9 +1000,24 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
     }
   }
   // ---- phase 4: Gram-Schmidt in descending eigenvalue order -----------------
+  // In the back-transformation type RG = RB: in FP64 mode in place on Zg; in
+  // mixed mode on an FP32 copy of the vectors (placed after the first n^2
+  // doubles of this trajectory's Gram slot), since the vectors go on to the
+  // complex64 back-transformation and the split (orthonormal to ~eps_32
+  // either way) while the eigenvalues and the inverse iteration, which depend
+  // on the gaps, stay FP64.
+  using RG = RB;
+  RG* Zs;
+  if constexpr (std::is_same<RG, R>::value) {
+    Zs = reinterpret_cast<RG*>(Zg);
+  } else {
+    Zs = reinterpret_cast<RG*>(Zg + (size_t)n * n);
+    for (int e = threadIdx.x; e < keep * n; e += blockDim.x) Zs[e] = (RG)Zg[e];
+    __syncthreads();
+  }
   // Blocks of NB = 16 vectors are orthonormalized in turn (block classical
   // Gram-Schmidt).  The block is staged in shared memory; the earlier vectors
-  // stay in Zg (L2-resident, 256 KB per trajectory at n = 256, keep = 128).
+  // stay in Zs (L2-resident, 256 KB per trajectory at n = 256, keep = 128).
   // Projection: the coefficients <z_a, z_b> by one warp per earlier vector a
   // (lanes along i, 16 sums per lane, one reduce-scatter butterfly), then
   // z_b -= sum_a c_ab z_a with the z_a streamed from L2, coalesced.  Then
@@ -1012,32 +1027,33 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
   // more than half of some vector's squared norm, or a Cholesky pivot fell
   // below half of its diagonal entry); inverse-iteration vectors of
   // well-separated eigenvalues pass with one.  A block whose pivots show
-  // near-dependence (pivot < 1e-8 of the squared norm) is redone vector by
-  // vector, each projected twice against everything before it.
+  // near-dependence (pivot < 1e-8 (FP64) or 1e-4 (FP32) of the squared norm)
+  // is redone vector by vector, each projected twice against everything
+  // before it.
   {
     constexpr int NB = 16;
     const int ldb = n + 2;                       // row stride of the staged block
-    R* Zb = reinterpret_cast<R*>(heev_smem);     // [NB][ldb]
-    R* cb = Zb + NB * ldb;                       // [128][NB] projection coefficients
-    R* gq = cb + 128 * NB;                       // [NB][NB] block Gram matrix
-    R* lq = gq + NB * NB;                        // [NB][NB] its Cholesky factor
+    RG* Zb = reinterpret_cast<RG*>(heev_smem);     // [NB][ldb]
+    RG* cb = Zb + NB * ldb;                       // [128][NB] projection coefficients
+    RG* gq = cb + 128 * NB;                       // [NB][NB] block Gram matrix
+    RG* lq = gq + NB * NB;                        // [NB][NB] its Cholesky factor
     __shared__ int s_fail, s_redo;
-    __shared__ R s_n0[NB];                       // squared norms before the projection
-    const R tol = (R)1e-8;
+    __shared__ RG s_n0[NB];                       // squared norms before the projection
+    const RG tol = (RG)(sizeof(RG) == 4 ? 1e-4 : 1e-8);   // near-dependence of a block
     const int nper = (n + 31) >> 5;
     // c[a][b] = <z_a, Zb_b> for a in [a0, a1): warp per a
     auto coeffs = [&](int a0, int a1, int nbk) {
       for (int a = a0 + warp; a < a1; a += nwarp) {
-        R za[8];
+        RG za[8];
 #pragma unroll
         for (int t2 = 0; t2 < 8; ++t2) {
           const int i = lane + 32 * t2;
-          za[t2] = (t2 < nper && i < n) ? Zg[(size_t)a * n + i] : (R)0;
+          za[t2] = (t2 < nper && i < n) ? Zs[(size_t)a * n + i] : (RG)0;
         }
-        R d[NB];
+        RG d[NB];
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
-          R acc = 0;
+          RG acc = 0;
 #pragma unroll
           for (int t2 = 0; t2 < 8; ++t2) {
             const int i = lane + 32 * t2;
@@ -1045,7 +1061,7 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
           }
           d[b] = acc;
         }
-        const R tot = warp_reduce_scatter<NB>(d, lane);
+        const RG tot = warp_reduce_scatter<NB>(d, lane);
         if ((lane & 1) == 0) cb[(a - a0) * NB + Scatter<NB>::index(lane)] = tot;
       }
     };
@@ -1053,13 +1069,13 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
     auto subtract = [&](int a0, int a1, int nbk) {
       const int i = threadIdx.x & 255, h = threadIdx.x >> 8;
       if (i < n && h < 2) {
-        R y[NB / 2];
+        RG y[NB / 2];
 #pragma unroll
-        for (int q2 = 0; q2 < NB / 2; ++q2) y[q2] = (h * NB / 2 + q2 < nbk) ? Zb[(h * NB / 2 + q2) * ldb + i] : (R)0;
+        for (int q2 = 0; q2 < NB / 2; ++q2) y[q2] = (h * NB / 2 + q2 < nbk) ? Zb[(h * NB / 2 + q2) * ldb + i] : (RG)0;
 #pragma unroll 2
         for (int a = a0; a < a1; ++a) {
-          const R za = Zg[(size_t)a * n + i];
-          const R* c = cb + (a - a0) * NB + h * NB / 2;
+          const RG za = Zs[(size_t)a * n + i];
+          const RG* c = cb + (a - a0) * NB + h * NB / 2;
 #pragma unroll
           for (int q2 = 0; q2 < NB / 2; ++q2) y[q2] = fma(-c[q2], za, y[q2]);
         }
@@ -1072,13 +1088,13 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
       const int nbk = min(NB, keep - kb);
       for (int e = threadIdx.x; e < NB * n; e += blockDim.x) {
         const int b = e / n, i = e - b * n;
-        Zb[b * ldb + i] = (b < nbk) ? Zg[(size_t)(kb + b) * n + i] : (R)0;
+        Zb[b * ldb + i] = (b < nbk) ? Zs[(size_t)(kb + b) * n + i] : (RG)0;
       }
       __syncthreads();
       for (int rep = 0; rep < 2; ++rep) {
         if (kb > 0) {
           if (rep == 0 && warp < nbk) {
-            R acc = 0;
+            RG acc = 0;
             for (int i = lane; i < n; i += 32) acc = fma(Zb[warp * ldb + i], Zb[warp * ldb + i], acc);
             acc = warp_sum(acc);
             if (lane == 0) s_n0[warp] = acc;
@@ -1096,7 +1112,7 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
         {
           const int ent = threadIdx.x >> 1, h = threadIdx.x & 1;
           const int bb = ent / NB, cc2 = ent % NB;
-          R acc = 0;
+          RG acc = 0;
           if (bb < nbk && cc2 < nbk)
             for (int i = h; i < n; i += 2) acc = fma(Zb[bb * ldb + i], Zb[cc2 * ldb + i], acc);
           acc += __shfl_xor_sync(0xffffffffu, acc, 1);
@@ -1105,24 +1121,24 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
         __syncthreads();
         // Cholesky G = L L^T by warp 0 (lane i owns row i)
         if (warp == 0) {
-          R li[NB];
+          RG li[NB];
 #pragma unroll
           for (int c = 0; c < NB; ++c) li[c] = 0;
           int fail = 0, redo = 0;
-          const R gii = (lane < nbk) ? gq[lane * NB + lane] : (R)1;
+          const RG gii = (lane < nbk) ? gq[lane * NB + lane] : (RG)1;
 #pragma unroll
           for (int j = 0; j < NB; ++j) {
             if (j < nbk) {
-              R sj = (lane < nbk) ? gq[lane * NB + j] : (R)0;
+              RG sj = (lane < nbk) ? gq[lane * NB + j] : (RG)0;
 #pragma unroll
               for (int c = 0; c < j; ++c) sj -= li[c] * __shfl_sync(0xffffffffu, li[c], j);
-              const R piv = __shfl_sync(0xffffffffu, sj, j);
-              const R gjj = __shfl_sync(0xffffffffu, gii, j);
-              if (!(piv > tol * gjj) || !(gjj > (R)0)) fail = 1;
-              if (!(piv >= (R)0.5 * gjj) || (kb > 0 && !(gjj >= (R)0.5 * s_n0[j]))) redo = 1;
-              const R ljj = sqrt(fmax(piv, (R)0));
+              const RG piv = __shfl_sync(0xffffffffu, sj, j);
+              const RG gjj = __shfl_sync(0xffffffffu, gii, j);
+              if (!(piv > tol * gjj) || !(gjj > (RG)0)) fail = 1;
+              if (!(piv >= (RG)0.5 * gjj) || (kb > 0 && !(gjj >= (RG)0.5 * s_n0[j]))) redo = 1;
+              const RG ljj = sqrt(fmax(piv, (RG)0));
               if (lane == j) li[j] = ljj;
-              else if (lane > j) li[j] = (ljj > 0) ? sj / ljj : (R)0;
+              else if (lane > j) li[j] = (ljj > 0) ? sj / ljj : (RG)0;
             }
           }
           if (lane < NB)
@@ -1137,41 +1153,41 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
         if (s_fail) {
           // vector by vector: project twice against all earlier vectors and
           // the block's earlier members, then normalize
-          R* cv = cb;   // coefficients, [kb + NB]
+          RG* cv = cb;   // coefficients, [kb + NB]
           for (int b = 0; b < nbk; ++b) {
             for (int pass = 0; pass < 2; ++pass) {
               for (int a = warp; a < kb + b; a += nwarp) {
-                const R* za = (a < kb) ? Zg + (size_t)a * n : Zb + (a - kb) * ldb;
-                R acc = 0;
+                const RG* za = (a < kb) ? Zs + (size_t)a * n : Zb + (a - kb) * ldb;
+                RG acc = 0;
                 for (int i = lane; i < n; i += 32) acc = fma(za[i], Zb[b * ldb + i], acc);
                 acc = warp_sum(acc);
                 if (lane == 0) cv[a] = acc;
               }
               __syncthreads();
               for (int i = threadIdx.x; i < n; i += blockDim.x) {
-                R v = Zb[b * ldb + i];
-                for (int a = 0; a < kb + b; ++a) v = fma(-cv[a], (a < kb) ? Zg[(size_t)a * n + i] : Zb[(a - kb) * ldb + i], v);
+                RG v = Zb[b * ldb + i];
+                for (int a = 0; a < kb + b; ++a) v = fma(-cv[a], (a < kb) ? Zs[(size_t)a * n + i] : Zb[(a - kb) * ldb + i], v);
                 Zb[b * ldb + i] = v;
               }
               __syncthreads();
             }
-            R part = 0;
+            RG part = 0;
             for (int i = threadIdx.x; i < n; i += blockDim.x) part = fma(Zb[b * ldb + i], Zb[b * ldb + i], part);
-            const R nn = block_sum(part, red);
-            const R inv = nn > 0 ? (R)1 / sqrt(nn) : (R)0;
+            const RG nn = block_sum(part, reinterpret_cast<RG*>(red));
+            const RG inv = nn > 0 ? (RG)1 / sqrt(nn) : (RG)0;
             for (int i = threadIdx.x; i < n; i += blockDim.x) Zb[b * ldb + i] *= inv;
             __syncthreads();
           }
         } else {
           // Zb <- L^{-1} Zb, one row entry i per thread
           for (int i = threadIdx.x; i < n; i += blockDim.x) {
-            R x[NB];
+            RG x[NB];
 #pragma unroll
-            for (int b = 0; b < NB; ++b) x[b] = (b < nbk) ? Zb[b * ldb + i] : (R)0;
+            for (int b = 0; b < NB; ++b) x[b] = (b < nbk) ? Zb[b * ldb + i] : (RG)0;
 #pragma unroll
             for (int b = 0; b < NB; ++b) {
               if (b < nbk) {
-                R v = x[b];
+                RG v = x[b];
 #pragma unroll
                 for (int c = 0; c < b; ++c) v = fma(-lq[b * NB + c], x[c], v);
                 x[b] = v / lq[b * NB + b];
@@ -1187,7 +1203,7 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
       }
       for (int e = threadIdx.x; e < nbk * n; e += blockDim.x) {
         const int b = e / n, i = e - b * n;
-        Zg[(size_t)(kb + b) * n + i] = Zb[b * ldb + i];
+        Zs[(size_t)(kb + b) * n + i] = Zb[b * ldb + i];
       }
       __syncthreads();
     }
@@ -1206,7 +1222,7 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
   constexpr int NCOL = sizeof(RB) == 4 ? 4 : 2;
   const int nper = (n + 31) >> 5;
   const int ldv = 32 * nper;
-  const size_t zbytes = 0;   // the vectors are read from Zg
+  const size_t zbytes = 0;   // the vectors are read from Zs
   const int rc = min(32, (int)((HeevSmem<R>::kBytes - zbytes) / (2 * (size_t)ldv * sizeof(cpx<RB>))));
   if (rc < 1) {   // cannot happen for n <= 256 (the z copy leaves >= 8 n entries)
     if (threadIdx.x == 0) atomicOr(s.status + t, (int32_t)TS_SHAPE);
@@ -1255,7 +1271,7 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
 #pragma unroll
       for (int a = 0; a < PER; ++a) {
         const int i = lane + 32 * a;
-        y[c][a] = (i < n && k0 + c < keep) ? cast<RB>(sph[i] * Zg[(size_t)(k0 + c) * n + i]) : mk<RB>(0, 0);
+        y[c][a] = (i < n && k0 + c < keep) ? cast<RB>(sph[i]) * Zs[(size_t)(k0 + c) * n + i] : mk<RB>(0, 0);
       }
     for (int c = 0; c < nch; ++c) {
       const int g = pass * nch + c;
