@@ -210,6 +210,8 @@ class Arm:
         self.sims = {}
         self.plan = LayerPlan(args.depth, args.pre_layers)
         self.resets = 0
+        self.tiles = {}       # GEMM tiles per size chosen by the library's autotuner (sim_tiles)
+        self.tune_ms = 0.0    # host time sim_create spent tuning (outside every timed region)
 
     def reset(self):
         torch = self.torch
@@ -220,6 +222,9 @@ class Arm:
             self.sims[n] = self.L.Simulation(n, self.args.chi, b, seed=self.args.seed, precision=self.precision,
                                              cutoff=self.cutoff, traj_offset=self.offsets.get(n, 0),
                                              log_capacity=self.w["circuits"][n].n_gates, stream=torch.cuda.Stream())
+            t = self.sims[n].tiles()
+            self.tune_ms += t["tune_ms"]
+            self.tiles[n] = t
         self.resets += 1
 
     def apply(self, l):
@@ -614,6 +619,7 @@ def main():
     value = total_updates / (ms / 1000.0)
     e2e = None if args.no_e2e else mixed.e2e(min(args.e2e_steps, args.steps))
     prof, work, prof_updates = mixed.profile_step()
+    autotune = tile_summary(mixed)
     observables = merged_observables(mixed.measure(), world)
     mixed.destroy()
 
@@ -664,7 +670,7 @@ def main():
                                          "d2h_bytes_per_step": e2e["d2h"], "steps": e2e["steps"]},
         "gpu_launches": gpu_launches(prof, args.steps),
         "kernel_share": {k: round(v[0] / total_prof, 4) for k, v in prof.items() if total_prof > 0},
-        "roofline": rl, "clocks": clk,
+        "roofline": rl, "clocks": clk, "autotune": autotune,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args, args.pre_layers, args.cpu_sample_s)
@@ -675,6 +681,20 @@ def main():
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(line))
+
+
+def tile_summary(arm):
+    """How often each GEMM tile shape was chosen, over the gate positions of
+    every size (SIMT contraction and the two Gram sides; tensor-core
+    positions left out), and the time sim_create spent tuning."""
+    out = {}
+    for kind, key in (("contract", "contract_simt"), ("gram_left", "gram"), ("gram_right", "gram")):
+        for t in arm.tiles.values():
+            for bm, bn in t[kind]:
+                if bm:
+                    d = out.setdefault(key, {})
+                    d[f"{bm}x{bn}"] = d.get(f"{bm}x{bn}", 0) + 1
+    return {"tiles": out, "tune_ms": round(arm.tune_ms, 1)}
 
 
 def merged_observables(res, world):

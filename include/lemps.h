@@ -122,6 +122,13 @@ typedef struct {
                              complex64, the precision they are used in (the
                              eigenvalues, the truncation and the tridiagonal
                              eigenvectors are FP64 either way) */
+  int32_t gemm_tile;      /* output tile (rows x columns) of the SIMT GEMMs of
+                             the two-site contraction and of the Gram matrix:
+                             0 = picked per problem size by the autotuner of
+                             sim_create (see sim_tiles); 1..4 = fixed shape:
+                             complex128 64x64, 32x64, 64x32, 32x32; complex64
+                             64x64, 128x64, 64x128, 32x32.  Every shape gives
+                             the same results bit for bit */
 } lemps_config;
 
 typedef struct {
@@ -286,6 +293,25 @@ lemps_status unravel_descend(const double* rho_a, const double* p, int64_t batch
  * allocating routine is called. */
 lemps_status unravel_grad_noalloc(const void* theta, int32_t theta_fp64, int64_t batch, int32_t chi,
                                   const double* p, const double* h, double* cost, double* grad, void* stream);
+
+/* GEMM tile shapes of the handle (Sec. IV.A's contraction and Gram
+ * products; the tile is an implementation choice the paper does not make).
+ * Per gate position q = 0..n-2 (the pair (q, q+1)): row 0 of the outputs is
+ * the two-site contraction, row 1 the Gram matrix of the left side (centre
+ * moving right), row 2 that of the right side.  tile_m, tile_n: host [3][n-1],
+ * the output tile's rows and columns, 0 where the tensor-core contraction runs
+ * instead (mixed precision, site capacities 64..128).  tune_ms: host,
+ * optional: milliseconds sim_create spent timing candidates.
+ * Autotuning (gemm_tile = 0): for each kernel and each distinct triple of site
+ * capacities (cap_q, cap_q+1, cap_q+2), sim_create times every candidate
+ * shape on min(n_traj, 2 x the SM count) trajectories with every bond at its
+ * capacity and zero operands (one warm-up and three timed launches, CUDA events
+ * on the handle's stream, before the state is initialized) and keeps the
+ * fastest; the default 64x64 stays unless another shape is at least 3 % faster.
+ * The choice is kept per device and precision for the life of the process, so
+ * later handles with the same capacities reuse it without timing.  Since every
+ * shape gives the same results, the choice never changes an output. */
+lemps_status sim_tiles(lemps_handle h, int32_t* tile_m, int32_t* tile_n, double* tune_ms);
 
 /* Per-kernel timing with CUDA events recorded on the handle's stream around
  * every launch made by apply_layer (enable = 1 starts a fresh record,

@@ -4,9 +4,13 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <array>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -100,6 +104,12 @@ struct lemps_sim {
   // all trajectories, with the A box (16 x 128) and the B box (cap[k+1] x 32).
   std::vector<CUtensorMap> map_a, map_b;
   std::vector<char> tc_site;
+  // GEMM tile per kernel (0 contraction, 1 left Gram, 2 right Gram) and gate
+  // position q: [3][n-1] indices into GemmTileShape, -1 where the tensor-core
+  // contraction runs; chosen by the autotuner in sim_create (or fixed).
+  std::vector<int8_t> tiles;
+  double tune_ms = 0.0;
+  int tile_of(int kind, int q) const { return tiles.empty() ? 0 : tiles[(size_t)kind * (n - 1) + q]; }
   bool profiling = false;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof;  // (kind, (start, stop))
   double prof_ms[LEMPS_NUM_KERNEL_KINDS] = {0};
@@ -288,9 +298,148 @@ void launch_heev(lemps_sim* h, int q, int mode, double cutoff, int keep_max, int
   else launch_heev_as<float>(h, heev_view(sv), q, mode, cutoff, keep_max, vectors);
 }
 
+// The SIMT contraction and the Gram kernel with the GEMM tile `tile`
+// (an index into GemmTileShape<R, .>).
+template <class R>
+void contract_simt(const SimView<R>& sv, int q, int tile, cudaStream_t st) {
+  const unsigned g = (unsigned)sv.B;
+  switch (tile) {
+    case 1: k_contract<R, 1><<<g, kThreads, 0, st>>>(sv, q); break;
+    case 2: k_contract<R, 2><<<g, kThreads, 0, st>>>(sv, q); break;
+    case 3: k_contract<R, 3><<<g, kThreads, 0, st>>>(sv, q); break;
+    default: k_contract<R, 0><<<g, kThreads, 0, st>>>(sv, q);
+  }
+}
+
+template <class R>
+void apply_gram(const SimView<R>& sv, int q, int side, int tile, cudaStream_t st) {
+  const unsigned g = (unsigned)sv.B;
+  switch (tile) {
+    case 1: k_apply_gram<R, 1><<<g, kThreads, 0, st>>>(sv, q, side); break;
+    case 2: k_apply_gram<R, 2><<<g, kThreads, 0, st>>>(sv, q, side); break;
+    case 3: k_apply_gram<R, 3><<<g, kThreads, 0, st>>>(sv, q, side); break;
+    default: k_apply_gram<R, 0><<<g, kThreads, 0, st>>>(sv, q, side);
+  }
+}
+
+void tile_shape(int prec, int id, int& bm, int& bn) {
+  static const int f[kNumGemmTiles][2] = {{GemmTileShape<float, 0>::BM, GemmTileShape<float, 0>::BN},
+                                          {GemmTileShape<float, 1>::BM, GemmTileShape<float, 1>::BN},
+                                          {GemmTileShape<float, 2>::BM, GemmTileShape<float, 2>::BN},
+                                          {GemmTileShape<float, 3>::BM, GemmTileShape<float, 3>::BN}};
+  static const int d[kNumGemmTiles][2] = {{GemmTileShape<double, 0>::BM, GemmTileShape<double, 0>::BN},
+                                          {GemmTileShape<double, 1>::BM, GemmTileShape<double, 1>::BN},
+                                          {GemmTileShape<double, 2>::BM, GemmTileShape<double, 2>::BN},
+                                          {GemmTileShape<double, 3>::BM, GemmTileShape<double, 3>::BN}};
+  const int(*t)[2] = (prec == LEMPS_FP64) ? d : f;
+  bm = t[id][0];
+  bn = t[id][1];
+}
+
+// Tiles chosen so far in this process: (device, precision, kernel, full-SM
+// batch, cap_q, cap_q+1, cap_q+2) -> tile index.
+std::mutex g_tile_mu;
+std::map<std::array<int, 7>, int> g_tile_record;
+
+// GEMM tile autotuner, run by sim_create before the state is initialized.
+// For each kernel (contraction, left Gram, right Gram) and each distinct
+// triple of site capacities not yet in the process record, every candidate
+// tile is timed on min(Bcap, 2 x #SMs) trajectories whose bonds are all at
+// their capacities (operands zeroed; values do not change the timing): one
+// warm-up launch, then three launches between CUDA events on the handle's
+// stream.  The fastest is kept if it beats the default 64 x 64 by 3 %.
+// All candidates compute the same results bit for bit (each output entry is
+// accumulated over k in order), so the choice only affects speed.
+template <class R>
+lemps_status autotune_tiles(lemps_sim* h) {
+  const int n = h->n, np = n - 1;
+  h->tiles.assign((size_t)3 * np, 0);
+  h->tune_ms = 0.0;
+  for (int q = 0; q < np; ++q)
+    if (sizeof(R) == 4 && !h->tc_site.empty() && h->tc_site[q] && h->tc_site[q + 1]) h->tiles[q] = -1;
+  if (h->cfg.gemm_tile > 0) {
+    for (auto& t : h->tiles)
+      if (t >= 0) t = (int8_t)(h->cfg.gemm_tile - 1);
+    return LEMPS_OK;
+  }
+  int dev = 0, sms = 1;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return check_cuda(h, "sim_create: autotune device query");
+  const int64_t Bt = std::min<int64_t>(h->Bcap, 2 * (int64_t)sms);
+  auto key_of = [&](int kind, int q) {
+    return std::array<int, 7>{dev, h->prec, kind, Bt >= sms ? 1 : 0, h->cap_h[q], h->cap_h[q + 1], h->cap_h[q + 2]};
+  };
+  std::vector<std::pair<int, int>> todo;   // (kind, first position) of each key still to time
+  {
+    std::lock_guard<std::mutex> lk(g_tile_mu);
+    std::map<std::array<int, 7>, int> seen;
+    for (int kind = 0; kind < 3; ++kind)
+      for (int q = 0; q < np; ++q) {
+        if (h->tiles[(size_t)kind * np + q] < 0) continue;
+        const auto key = key_of(kind, q);
+        if (g_tile_record.count(key) || seen.count(key)) continue;
+        seen[key] = 1;
+        todo.push_back({kind, q});
+      }
+  }
+  if (!todo.empty()) {
+    const auto t0 = std::chrono::steady_clock::now();
+    std::vector<int32_t> bonds((size_t)Bt * (n + 1));
+    for (int64_t t = 0; t < Bt; ++t)
+      for (int k = 0; k <= n; ++k) bonds[(size_t)t * (n + 1) + k] = h->cap_h[k];
+    cudaMemcpyAsync(h->bond, bonds.data(), sizeof(int32_t) * bonds.size(), cudaMemcpyHostToDevice, h->stream);
+    cudaMemsetAsync(h->mps, 0, h->mps_bytes, h->stream);
+    cudaMemsetAsync(h->ws[0], 0, h->elem * h->ws_stride * Bt, h->stream);
+    cudaMemsetAsync(h->top, 0, sizeof(zd) * 16 * Bt, h->stream);
+    SimView<R> v = h->view<R>();
+    v.B = Bt;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    std::vector<std::pair<std::array<int, 7>, int>> found;
+    for (const auto& kq : todo) {
+      const int kind = kq.first, q = kq.second;
+      auto launch = [&](int tile) {
+        if (kind == 0) contract_simt<R>(v, q, tile, h->stream);
+        else apply_gram<R>(v, q, kind - 1, tile, h->stream);
+      };
+      float ms[kNumGemmTiles];
+      for (int c = 0; c < kNumGemmTiles; ++c) {
+        launch(c);
+        cudaEventRecord(e0, h->stream);
+        for (int r = 0; r < 3; ++r) launch(c);
+        cudaEventRecord(e1, h->stream);
+        cudaEventSynchronize(e1);
+        ms[c] = 0.f;
+        cudaEventElapsedTime(&ms[c], e0, e1);
+      }
+      int best = 0;
+      for (int c = 1; c < kNumGemmTiles; ++c)
+        if (ms[c] < ms[best]) best = c;
+      if (!(ms[best] < 0.97f * ms[0])) best = 0;
+      found.push_back({key_of(kind, q), best});
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamSynchronize(h->stream);   // the bond copy's host buffer
+    lemps_status st = check_cuda(h, "sim_create: autotune");
+    if (st != LEMPS_OK) return st;
+    std::lock_guard<std::mutex> lk(g_tile_mu);
+    for (const auto& f : found) g_tile_record.emplace(f.first, f.second);   // the first record of a key wins
+    h->tune_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  }
+  std::lock_guard<std::mutex> lk(g_tile_mu);
+  for (int kind = 0; kind < 3; ++kind)
+    for (int q = 0; q < np; ++q) {
+      int8_t& t = h->tiles[(size_t)kind * np + q];
+      if (t >= 0) t = (int8_t)g_tile_record.at(key_of(kind, q));
+    }
+  return LEMPS_OK;
+}
+
 // Two-site contraction of the pair (q, q+1): on the tensor cores in mixed
 // precision when all three site capacities lie in [64, 128] (and are even),
-// else the SIMT kernel.
+// else the SIMT kernel with the handle's tile for q.
 template <class R>
 void launch_contract(lemps_sim* h, int q) {
   SimView<R> sv = h->view<R>();
@@ -306,7 +455,7 @@ void launch_contract(lemps_sim* h, int q) {
     });
     return;
   }
-  h->timed(LEMPS_K_CONTRACT, [&] { k_contract<R><<<(unsigned)h->B, kThreads, 0, h->stream>>>(sv, q); });
+  h->timed(LEMPS_K_CONTRACT, [&] { contract_simt<R>(sv, q, h->tile_of(0, q), h->stream); });
 }
 
 template <class R>
@@ -368,7 +517,7 @@ lemps_status apply_layer_t(lemps_sim* h, const lemps_layer* L) {
     gs.status = h->status;
     gs.B = h->B;
     h->timed(LEMPS_K_UNRAVEL, [&] { launch_unravel_gate(gs, ld, h->stream); });
-    h->timed(LEMPS_K_GRAM, [&] { k_apply_gram<R><<<(unsigned)h->B, kThreads, 0, h->stream>>>(sv, q, side); });
+    h->timed(LEMPS_K_GRAM, [&] { apply_gram<R>(sv, q, side, h->tile_of(1 + side, q), h->stream); });
     launch_heev<R>(h, q, side, h->cfg.trunc_cutoff, keep_max, 1);
     h->timed(LEMPS_K_SPLIT, [&] { k_split<R><<<(unsigned)h->B, kThreads, 0, h->stream>>>(sv, q, side); });
     h->center = (side == 0) ? q + 1 : q;
@@ -514,6 +663,8 @@ lemps_status sim_create(const lemps_config* cfg, lemps_handle* out) {
   if ((cfg->alloc == nullptr) != (cfg->free == nullptr)) return fail(LEMPS_EINVAL, "sim_create: alloc and free go together");
   if (cfg->max_traj_in_flight < 0) return fail(LEMPS_EINVAL, "sim_create: max_traj_in_flight must be >= 0");
   if (cfg->eigvec_fp64 != 0 && cfg->eigvec_fp64 != 1) return fail(LEMPS_EINVAL, "sim_create: eigvec_fp64 must be 0 or 1");
+  if (cfg->gemm_tile < 0 || cfg->gemm_tile > kNumGemmTiles)
+    return fail(LEMPS_EINVAL, "sim_create: gemm_tile must be 0 (autotune) or 1..4");
   lemps_sim* h = new lemps_sim();
   h->cfg = *cfg;
   h->n = cfg->n_qubits;
@@ -631,6 +782,15 @@ lemps_status sim_create(const lemps_config* cfg, lemps_handle* out) {
     static const zd kEye4[16] = {{1, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}, {1, 0}, {0, 0}, {0, 0},
                                  {0, 0}, {0, 0}, {1, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}, {1, 0}};
     cudaMemcpyAsync(h->eye4, kEye4, sizeof(kEye4), cudaMemcpyHostToDevice, h->stream);
+  }
+  {
+    lemps_status ts = (h->prec == LEMPS_FP64) ? autotune_tiles<double>(h) : autotune_tiles<float>(h);
+    if (ts != LEMPS_OK) {
+      cudaStreamSynchronize(h->stream);
+      h->release();
+      delete h;
+      return ts;
+    }
   }
   reset_wave(h, 0);
   lemps_status st = check_cuda(h, "sim_create");
@@ -929,6 +1089,21 @@ lemps_status sim_profile(lemps_handle h, int32_t enable, double* ms, int64_t* la
   }
   h->profiling = enable != 0;
   return check_cuda(h, "sim_profile");
+}
+
+lemps_status sim_tiles(lemps_handle h, int32_t* tile_m, int32_t* tile_n, double* tune_ms) {
+  if (!h || !tile_m || !tile_n) return fail(LEMPS_EINVAL, "sim_tiles: null argument");
+  const int np = h->n - 1;
+  for (int kind = 0; kind < 3; ++kind)
+    for (int q = 0; q < np; ++q) {
+      const int id = h->tile_of(kind, q);
+      int bm = 0, bn = 0;
+      if (id >= 0) tile_shape(h->prec, id, bm, bn);
+      tile_m[kind * np + q] = bm;
+      tile_n[kind * np + q] = bn;
+    }
+  if (tune_ms) *tune_ms = h->tune_ms;
+  return LEMPS_OK;
 }
 
 lemps_status destroy(lemps_handle h) {

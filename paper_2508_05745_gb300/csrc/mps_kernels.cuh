@@ -598,12 +598,14 @@ __device__ __forceinline__ void contract_rho12(const SimView<R>& s, int64_t t, c
   }
 }
 
-template <class R>
+// TILE selects the GEMM tile shape (GemmTileShape<R, TILE>); every shape
+// gives the same result bit for bit.
+template <class R, int TILE = 0>
 __global__ void __launch_bounds__(kGemmThreads) k_contract(SimView<R> s, int q) {
   const int64_t t = blockIdx.x;
   if (t >= s.B) return;
   __shared__ double red[32];
-  __shared__ GemmSmem<R> sm;
+  __shared__ GemmSmem<R, GemmTileShape<R, TILE>::BM, GemmTileShape<R, TILE>::BN> sm;
   const int32_t* bd = s.bond + t * (s.n + 1);
   const int dl = bd[q], dm = bd[q + 1], dr = bd[q + 2];
   const int capm = s.cap[q + 1], capr = s.cap[q + 2];
@@ -671,11 +673,12 @@ __global__ void __launch_bounds__(tc::kThreads, 1) k_contract_tc(const __grid_co
 // ---- apply T to Theta and build the Gram matrix ------------------------------
 // side = 0: left Gram  G = Theta Theta^dagger (2dl x 2dl)
 // side = 1: right Gram G = Theta^dagger Theta (2dr x 2dr)
-template <class R>
+// TILE selects the GEMM tile shape of the Gram product, as in k_contract.
+template <class R, int TILE = 0>
 __global__ void __launch_bounds__(kGemmThreads) k_apply_gram(SimView<R> s, int q, int side) {
   const int64_t t = blockIdx.x;
   if (t >= s.B) return;
-  __shared__ GemmSmem<R> sm;
+  __shared__ GemmSmem<R, GemmTileShape<R, TILE>::BM, GemmTileShape<R, TILE>::BN> sm;
   const int32_t* bd = s.bond + t * (s.n + 1);
   const int dl = bd[q], dr = bd[q + 2];
   cpx<R>* th = s.ws0 + t * s.ws_stride;
@@ -751,7 +754,10 @@ HeevView<double> heev_view(const SimView<R>& s) {
 //   A_q = B / ||B||.
 // The discarded weight is eps = ||R||_F^2 / ||Theta||_F^2, accumulated in FP64
 // from the residual itself, which keeps it accurate in complex64 (a sum of
-// discarded eigenvalues would carry an error of ~ n eps_32).
+// discarded eigenvalues would carry an error of ~ n eps_32).  The split keeps
+// the default GEMM tile: its norms are summed per thread inside the GEMM
+// epilogues, so another tile shape would change their rounding (and the
+// normalization of the new site tensor with it).
 template <class R>
 __global__ void __launch_bounds__(kGemmThreads) k_split(SimView<R> s, int q, int side) {
   const int64_t t = blockIdx.x;

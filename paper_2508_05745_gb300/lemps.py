@@ -27,7 +27,7 @@ ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, c
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 
 EXPORTED = ["sim_create", "apply_layer", "unravel_opt", "sample_branch", "measure", "sim_export_mps", "sim_waves",
-            "sim_sync", "sim_profile", "destroy", "unravel_grad", "unravel_descend", "unravel_grad_noalloc",
+            "sim_sync", "sim_profile", "sim_tiles", "destroy", "unravel_grad", "unravel_descend", "unravel_grad_noalloc",
             "sample_bitstrings", "eps_concentrated", "lemps_last_error"]
 KERNEL_KINDS = ["move", "contract", "unravel", "gram", "eig", "split", "other"]
 
@@ -44,7 +44,8 @@ class Config(ctypes.Structure):
                 ("precision", ctypes.c_int32), ("unravel_mode", ctypes.c_int32), ("log_capacity", ctypes.c_int32),
                 ("eps_max", ctypes.c_double), ("cuda_stream", ctypes.c_void_p), ("alloc", ALLOC_FN),
                 ("free", FREE_FN), ("alloc_ctx", ctypes.c_void_p), ("layering", ctypes.c_int32),
-                ("max_traj_in_flight", ctypes.c_int64), ("eigvec_fp64", ctypes.c_int32)]
+                ("max_traj_in_flight", ctypes.c_int64), ("eigvec_fp64", ctypes.c_int32),
+                ("gemm_tile", ctypes.c_int32)]
 
 
 class LayerStruct(ctypes.Structure):
@@ -94,6 +95,7 @@ def load(build_if_missing: bool = False) -> ctypes.CDLL:
     lib.sim_sync.argtypes = [vp]
     lib.sim_waves.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i32)]
     lib.sim_profile.argtypes = [vp, i32, dp, ctypes.POINTER(i64)]
+    lib.sim_tiles.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), dp]
     lib.destroy.argtypes = [vp]
     lib.unravel_grad.argtypes = [vp, i32, i64, i32, vp, vp, vp, vp, vp, vp]
     lib.unravel_descend.argtypes = [vp, vp, i64, i32, ctypes.c_double, vp, vp, vp]
@@ -127,7 +129,8 @@ class Simulation:
     def __init__(self, n_qubits: int, chi_max: int, n_traj: int, seed: int = 0, precision: str = "fp64",
                  unravel: str = "optimal", cutoff: Optional[float] = None, traj_offset: int = 0,
                  log_capacity: int = 0, eps_max: float = 4.0, stream=None, torch_allocator: bool = True,
-                 layering: str = "local", max_traj_in_flight: int = 0, eigvec_fp64: bool = False):
+                 layering: str = "local", max_traj_in_flight: int = 0, eigvec_fp64: bool = False,
+                 gemm_tile: int = 0):
         torch = _require_cuda()
         lib = load()
         self.n, self.chi, self.B = int(n_qubits), int(chi_max), int(n_traj)
@@ -149,6 +152,7 @@ class Simulation:
         cfg.eps_max = float(eps_max)
         cfg.max_traj_in_flight = int(max_traj_in_flight)
         cfg.eigvec_fp64 = 1 if eigvec_fp64 else 0
+        cfg.gemm_tile = int(gemm_tile)
         cfg.cuda_stream = self.stream.cuda_stream
         self._cb = None
         if torch_allocator:
@@ -242,6 +246,19 @@ class Simulation:
     def sync(self) -> int:
         return load().sim_sync(self._h)
 
+    def tiles(self):
+        """GEMM tile shapes of the handle (sim_tiles): {"contract", "gram_left",
+        "gram_right"} -> int32 [n-1, 2] (rows, columns of the output tile per
+        gate position; (0, 0) where the tensor-core contraction runs), and
+        "tune_ms", the time sim_create spent timing candidates."""
+        m = np.zeros(3 * (self.n - 1), dtype=np.int32)
+        k = np.zeros(3 * (self.n - 1), dtype=np.int32)
+        ms = ctypes.c_double(0.0)
+        _check(load().sim_tiles(self._h, _ptr(m, ctypes.c_int32), _ptr(k, ctypes.c_int32), ctypes.byref(ms)),
+               "sim_tiles")
+        shape = np.stack([m, k], axis=1).reshape(3, self.n - 1, 2)
+        return {"contract": shape[0], "gram_left": shape[1], "gram_right": shape[2], "tune_ms": ms.value}
+
     def profile(self, enable: bool, collect: bool = False):
         """Start/stop CUDA-event timing of every kernel launch; with collect=True
         return {kind: (total_ms, launches)}."""
@@ -287,6 +304,10 @@ def eps_concentrated(sim: Simulation, kind: str, param: float):
 
 def measure(sim: Simulation, per_trajectory: bool = True) -> dict:
     return sim.measure(per_trajectory)
+
+
+def sim_tiles(sim: Simulation) -> dict:
+    return sim.tiles()
 
 
 def destroy(sim: Simulation) -> None:

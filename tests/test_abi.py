@@ -100,3 +100,21 @@ def test_eigvec_fp64_flag_is_validated(lib_path):
     assert lib.sim_create(ctypes.byref(cfg), ctypes.byref(h)) == L.LEMPS_EINVAL
     assert b"eigvec_fp64" in lib.lemps_last_error()
     assert h.value is None
+
+
+def test_gemm_tile_is_validated(lib_path):
+    """lemps_config.gemm_tile takes 0 (autotune) or 1..4 (a fixed tile shape);
+    any other value fails sim_create with LEMPS_EINVAL before any device call
+    (host only)."""
+    import ctypes
+    from paper_2508_05745_gb300 import lemps as L
+    lib = L.load()
+    for bad in (-1, 5):
+        cfg = L.Config(n_qubits=8, chi_max=16, trunc_cutoff=1e-12, n_traj=4, traj_offset=0, seed=1,
+                       precision=L.LEMPS_FP64, unravel_mode=L.LEMPS_UNRAVEL_OPTIMAL, log_capacity=0, eps_max=2.0,
+                       cuda_stream=None, alloc=L.ALLOC_FN(0), free=L.FREE_FN(0), alloc_ctx=None,
+                       layering=L.LEMPS_LAYER_LOCAL, max_traj_in_flight=4, eigvec_fp64=0, gemm_tile=bad)
+        h = ctypes.c_void_p()
+        assert lib.sim_create(ctypes.byref(cfg), ctypes.byref(h)) == L.LEMPS_EINVAL
+        assert b"gemm_tile" in lib.lemps_last_error()
+        assert h.value is None

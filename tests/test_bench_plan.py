@@ -106,6 +106,12 @@ class _Sim:
     def profile(self, enable, collect=False):
         return {k: (1.0, 1) for k in ("move", "contract", "unravel", "gram", "eig", "split", "other")} if collect else None
 
+    def tiles(self):
+        t = np.tile(np.array([[64, 64]], np.int32), (self.n - 1, 1))
+        c = t.copy()
+        c[self.n // 2] = 0   # a tensor-core position
+        return {"contract": c, "gram_left": t, "gram_right": t, "tune_ms": 1.5 if len(_Sim.created) == 1 else 0.0}
+
     def measure(self):
         return {}
 
@@ -135,3 +141,7 @@ def test_arm_runs_the_driver_schedule(steps, warmup):
     expect = sum(sum(len(w["circuits"][n].layers[l].left_qubits) for l in layers) * b
                  for n, b in {24: 3, 48: 2, 64: 1}.items())
     assert upd == expect
+    tiles = bench.tile_summary(arm)
+    assert tiles["tune_ms"] == 1.5
+    assert tiles["tiles"]["gram"] == {"64x64": 2 * (23 + 47 + 63)}
+    assert tiles["tiles"]["contract_simt"] == {"64x64": 22 + 46 + 62}

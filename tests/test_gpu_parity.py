@@ -543,6 +543,72 @@ def test_waves_equal_one_big_handle(L, precision):
     wav.destroy()
 
 
+# --- GEMM tile autotuner ----------------------------------------------------------------
+
+TILE_SHAPES = {"fp64": [(64, 64), (32, 64), (64, 32), (32, 32)],
+               "mixed": [(64, 64), (128, 64), (64, 128), (32, 32)]}
+
+
+@pytest.mark.parametrize("precision,n,chi", [("fp64", 12, 40), ("mixed", 16, 100)])
+def test_gemm_tiles_give_identical_results(L, precision, n, chi):
+    """Every GEMM tile shape the autotuner can pick (gemm_tile = 1..4) and the
+    autotuned choice (gemm_tile = 0) give the same run bit for bit: branch
+    sequences, observables, error bounds and MPS tensors.  The circuit (depth
+    9 Haar brickwork, depolarizing p = 0.05) drives the middle bonds to chi, so
+    the products span several tiles of every shape with ragged edges: Gram
+    sides up to 80 (FP64, chi = 40) and 200 (mixed, chi = 100, where the
+    middle contractions run on the tensor cores and the outer ones on the
+    SIMT kernel)."""
+    circ = I.random_brickwork(n, 9, I.depolarizing_kraus(0.05), seed=5)
+    runs = []
+    for tile in range(5):
+        sim = L.Simulation(n, chi, 24, seed=9, precision=precision, log_capacity=circ.n_gates, gemm_tile=tile)
+        sim.run(circ)
+        res = sim.measure()
+        br = np.array([sim.sample_branch(g, s) for g in range(circ.n_gates) for s in range(2)])
+        mps = [sim.export_mps(t) for t in (0, 11, 23)]
+        tiles = sim.tiles()
+        sim.destroy()
+        assert res["n_failed"] == 0
+        runs.append((res, br, mps, tiles))
+    assert max(b.max() for _, b in runs[0][2]) == chi
+    shapes = TILE_SHAPES[precision]
+    for tile, (res, br, mps, tiles) in enumerate(runs):
+        for kind in ("contract", "gram_left", "gram_right"):
+            got = {tuple(x) for x in tiles[kind] if tuple(x) != (0, 0)}
+            assert got, (tile, kind)
+            assert got <= set(shapes), (tile, kind, got)
+            if tile > 0:
+                assert got == {shapes[tile - 1]}, (tile, kind, got)
+        if precision == "mixed":
+            assert (tiles["contract"] == 0).all(axis=1).any()   # tensor-core positions
+        if tile == 0:
+            continue
+        ref_res, ref_br, ref_mps, _ = runs[0]
+        assert np.array_equal(br, ref_br), tile
+        for key in ("z", "zz", "s_half", "eps_bound", "status", "z_mean", "zz_mean"):
+            assert np.array_equal(res[key], ref_res[key]), (tile, key)
+        for (ts, bonds), (rts, rbonds) in zip(mps, ref_mps):
+            assert np.array_equal(bonds, rbonds), tile
+            for a, b in zip(ts, rts):
+                assert np.array_equal(a, b), tile
+
+
+def test_autotuner_reuses_its_record(L):
+    """The autotuner times each (kernel, capacity triple) once per process:
+    a second handle with the same capacities, precision and batch class
+    spends no time tuning and gets the same tiles."""
+    a = L.Simulation(10, 24, 16, seed=1, precision="fp64")
+    b = L.Simulation(10, 24, 16, seed=2, precision="fp64")
+    ta, tb = a.tiles(), b.tiles()
+    a.destroy()
+    b.destroy()
+    assert tb["tune_ms"] == 0.0
+    for kind in ("contract", "gram_left", "gram_right"):
+        assert np.array_equal(ta[kind], tb[kind]), kind
+        assert {tuple(x) for x in ta[kind]} <= set(TILE_SHAPES["fp64"])
+
+
 # --- edge cases ---------------------------------------------------------------------
 
 def test_two_qubits_single_trajectory(L):
