@@ -456,7 +456,9 @@ def cpu_baseline(args, pre_layers, budget_s):
 # layer for one trajectory, per kernel kind, from the bond dimensions b[] of
 # the state before the layer (each split is assumed to grow the bond to
 # min(chi, 2 dl, 2 dr)).  Gate on (q, q+1) with dl, dm, dr = b[q], b[q+1],
-# b[q+2]; n_g = 2 d_s is the Gram side chosen by the next gate, d_o the other:
+# b[q+2]; n_g = 2 d_s is the Gram side the library picks (the smaller one
+# when the site capacities cap[q], cap[q+2] differ, else the side that
+# leaves the centre next to the following gate), d_o the other:
 #   contract  (2 dl x dm)(dm x 2 dr):                 4 dl dm dr
 #   gram      one triangle of n_g x n_g, K = 2 d_o:   n_g^2 d_o
 #   eig       Hermitian tridiagonalization (2/3) n_g^3 (FP64); the
@@ -465,10 +467,26 @@ def cpu_baseline(args, pre_layers, budget_s):
 #   split     U^dagger Theta and the residual:        4 keep n_g d_o
 #   move      per centre move, Householder QR of m x n (m n^2 - n^3 / 3),
 #             explicit Q (m r^2 - r^3 / 3), triangular merge into the
-#             neighbour (r n d_next, half of the r x n by n x 2 d_next product)
+#             neighbour (r n d_next, half of the r x n by n x 2 d_next product);
+#             the moves before the layer's first gate are not counted
 def _qr_work(m, n, d_next):
     r = min(m, n)
     return (m * n * n - n ** 3 / 3.0) + (m * r * r - r ** 3 / 3.0) + r * n * d_next
+
+
+def split_sides(left_qubits, nq, chi):
+    """Per gate of a layer, True when the split uses the left Gram (centre
+    moves to q+1), as the library decides it (local layering, capacities
+    cap[k] = min(chi, 2^min(k, n-k)))."""
+    cap = [min(chi, 2 ** min(k, nq - k)) for k in range(nq + 1)]
+    qs = [int(q) for q in left_qubits]
+    out = []
+    for i, q in enumerate(qs):
+        if cap[q] != cap[q + 2]:
+            out.append(cap[q] < cap[q + 2])
+        else:
+            out.append((qs[i + 1] > q) if i + 1 < len(qs) else (i == 0 or qs[i - 1] < q))
+    return out
 
 
 def layer_work(left_qubits, bonds, chi):
@@ -476,17 +494,18 @@ def layer_work(left_qubits, bonds, chi):
     nq = len(b) - 1
     w = {"contract": 0.0, "gram": 0.0, "eig": 0.0, "eig_bt": 0.0, "split": 0.0, "move": 0.0}
     qs = [int(q) for q in left_qubits]
+    sides = split_sides(qs, nq, chi)
+    centre = None
     for i, q in enumerate(qs):
-        if i > 0:
-            p = qs[i - 1]
-            if q > p:   # centre at p+1 moves right to q
-                for k in range(p + 1, q):
+        if centre is not None:
+            if centre < q:        # the centre moves right to q
+                for k in range(centre, q):
                     w["move"] += _qr_work(2 * b[k], b[k + 1], b[min(k + 2, nq)])
-            else:       # centre at p moves left to q+1
-                for k in range(p, q + 1, -1):
+            elif centre > q + 1:  # the centre moves left to q+1
+                for k in range(centre, q + 1, -1):
                     w["move"] += _qr_work(2 * b[k + 1], b[k], b[max(k - 1, 0)])
         dl, dm, dr = b[q], b[q + 1], b[q + 2]
-        right = (qs[i + 1] > q) if i + 1 < len(qs) else (i == 0 or qs[i - 1] < q)
+        right = sides[i]
         ds, do = (dl, dr) if right else (dr, dl)
         ng = 2 * ds
         keep = min(chi, 2 * dl, 2 * dr)
@@ -496,6 +515,7 @@ def layer_work(left_qubits, bonds, chi):
         w["eig_bt"] += ng * ng * keep
         w["split"] += 4.0 * keep * ng * do
         b[q + 1] = keep
+        centre = q + 1 if right else q
     return w
 
 

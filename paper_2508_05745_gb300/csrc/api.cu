@@ -492,9 +492,9 @@ lemps_status apply_layer_t(lemps_sim* h, const lemps_layer* L) {
   const unsigned grid_t = (unsigned)((h->B + kThreads - 1) / kThreads);
   SimView<R> sv = h->view<R>();
   // One pair step: centre onto (q, q+1), contraction, gate and noise sites
-  // (coin_p = 0: no noise, the gate alone), Gram on the side that leaves the
-  // centre next to the following pair, eigensolve keeping at most keep_max,
-  // split.  gate_global keys the Philox counters of the noise sites.
+  // (coin_p = 0: no noise, the gate alone), Gram on the given side,
+  // eigensolve keeping at most keep_max, split.  gate_global keys the Philox
+  // counters of the noise sites.
   auto pair_step = [&](int q, const zd* gate, int gate_local, double coin_p, int64_t gate_global, bool log,
                        int keep_max, int side) {
     if (h->center < q) move_center_to<R>(h, q);
@@ -529,6 +529,18 @@ lemps_status apply_layer_t(lemps_sim* h, const lemps_layer* L) {
     if (g > 0) return (q > L->left_qubit[g - 1]) ? 0 : 1;
     return 0;
   };
+  // Gram side of a gate's split in the local layering: the smaller Gram matrix
+  // when the site capacities around the pair differ (the eigensolve costs ~
+  // size^3, and a centre left one site away from the next pair costs one more
+  // QR move, far less), else the side that leaves the centre next to the
+  // following pair.  Both sides give the same truncated split (Sec. IV.A's
+  // SVD re-split seen from either side), up to rounding.
+  auto split_side = [&](int g) {
+    const int q = L->left_qubit[g];
+    const int cl = h->cap_h[q], cr = h->cap_h[q + 2];
+    if (cl != cr) return cl < cr ? 0 : 1;
+    return side_of(g);
+  };
   if (h->cfg.layering == LEMPS_LAYER_GLOBAL) {
     // all gates (no noise, bonds up to 2 chi), then the noise on every gated
     // pair with the identity gate and the same Philox counters as the local
@@ -541,7 +553,7 @@ lemps_status apply_layer_t(lemps_sim* h, const lemps_layer* L) {
     for (int k = 0; k + 1 < h->n; ++k) pair_step(k, h->eye4, 0, 0.0, h->gates_done, false, h->chi, 0);
   } else {
     for (int g = 0; g < ng; ++g)
-      pair_step(L->left_qubit[g], h->layer_buf, g, L->coin_p, h->gates_done + g, true, h->chi, side_of(g));
+      pair_step(L->left_qubit[g], h->layer_buf, g, L->coin_p, h->gates_done + g, true, h->chi, split_side(g));
   }
   double* hist = (h->layers_done < kEpsHistLayers) ? h->eps_hist : nullptr;
   h->timed(LEMPS_K_OTHER, [&] {

@@ -485,8 +485,35 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
   // A step reads its column with that correction and forms v; then one pass
   // over the trailing triangle writes the corrected entries back and forms
   // y = A v (both halves); three barriers per step.
+  // The warps add their partial sums of y in 64-bit fixed point, 2^-60 ||G||
+  // at most per unit (the scale is a power of two with tr * scale < 2^60):
+  // integer adds are exact and associative, so y does not depend on the
+  // order in which the warps add (the run is deterministic) and its error is
+  // the rounding of each partial sum to the unit.  Every partial sum of
+  // (A v)_r over a subset of columns is at most ||A||_2 ||v|| <= tr (A is
+  // similar to a block of the Gram matrix, v a unit vector), so the sums stay
+  // below 2^61; the unit, 2^-60 tr <= 2^-60 n ||G||_2, is far below the FP64
+  // rounding of the dot products themselves.  The y slots hold the integers
+  // (re, im) in place of the complex value; zero has the same bits in both.
   __shared__ cpx<R> sy2[256];
   __shared__ R redn[32], reds[32];
+  // scale and its inverse (powers of two) in shared memory: registers are
+  // scarce at 512 threads
+  __shared__ double s_ysc[2];
+  if (threadIdx.x == 0) {
+    int tr_exp = 0;
+    (void)frexp(s_tr, &tr_exp);
+    s_ysc[0] = (s_tr > 0.0 && isfinite(s_tr)) ? ldexp(1.0, 60 - tr_exp) : 1.0;
+    s_ysc[1] = 1.0 / s_ysc[0];
+  }
+  auto yget = [&](const cpx<R>* y, int X) {
+    const long long* yi = reinterpret_cast<const long long*>(y) + 2 * X;
+    return mk<R>((R)(__ll2double_rn(yi[0]) * s_ysc[1]), (R)(__ll2double_rn(yi[1]) * s_ysc[1]));
+  };
+  auto yadd = [&](cpx<R>* y, int X, int comp, double v) {
+    atomicAdd(reinterpret_cast<unsigned long long*>(y) + 2 * X + comp,
+              (unsigned long long)__double2ll_rn(v * s_ysc[0]));
+  };
   for (int i = threadIdx.x; i < M0; i += blockDim.x) {
     sv[i] = mk<R>(0, 0); sw[i] = mk<R>(0, 0);
     sph[i] = mk<R>(0, 0); sy2[i] = mk<R>(0, 0);
@@ -502,7 +529,7 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
     const cpx<R>* yP = pb ? sy2 : sph;
     cpx<R>* vN = qb ? sw : sv;
     cpx<R>* yN = qb ? sy2 : sph;
-    auto wprev = [&](int X) { return (R)2 * yP[X] - ((R)2 * ssP) * vP[X]; };
+    auto wprev = [&](int X) { return (R)2 * yget(yP, X) - ((R)2 * ssP) * vP[X]; };
     const cpx<R> vPj = vP[jl], wPj = wprev(jl);
     // column jl below the diagonal (one entry per thread; m < blockDim.x)
     const int i = threadIdx.x;
@@ -603,8 +630,8 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
         d[2 * cc + 1] = qv.im;
       }
       if (any) {
-        atomicAdd(&yN[Rr].re, acc.re);
-        atomicAdd(&yN[Rr].im, acc.im);
+        yadd(yN, Rr, 0, acc.re);
+        yadd(yN, Rr, 1, acc.im);
         ssp = fma(nr.re, acc.re, fma(nr.im, acc.im, ssp));
       }
       const R tot = warp_reduce_scatter<NVQ>(d, lane);
@@ -612,10 +639,10 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
       const int Cc = cb + (e >> 1);
       if ((lane & ((1 << (5 - LGQ)) - 1)) == 0 && Cc > jl && Cc < M0) {
         if (e & 1) {
-          atomicAdd(&yN[Cc].im, tot);
+          yadd(yN, Cc, 1, tot);
           ssp = fma(vN[Cc].im, tot, ssp);
         } else {
-          atomicAdd(&yN[Cc].re, tot);
+          yadd(yN, Cc, 0, tot);
           ssp = fma(vN[Cc].re, tot, ssp);
         }
       }
@@ -630,7 +657,7 @@ __global__ void __launch_bounds__(512) k_heev(HeevView<R> s, int q, int mode, do
     // the last two rows, with the pending update of the last step
     const cpx<R>* vP = pb ? sw : sv;
     const cpx<R>* yP = pb ? sy2 : sph;
-    auto wprev = [&](int X) { return (R)2 * yP[X] - ((R)2 * ssP) * vP[X]; };
+    auto wprev = [&](int X) { return (R)2 * yget(yP, X) - ((R)2 * ssP) * vP[X]; };
     auto aeff = [&](int X, int Y) { return Lp[pidx(X, Y)] - vP[X] * conj(wprev(Y)) - wprev(X) * conj(vP[Y]); };
     const int a = n - 2 - j0, b = n - 1 - j0;   // local indices of the last two rows
     if (n >= 2) {

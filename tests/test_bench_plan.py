@@ -145,3 +145,21 @@ def test_arm_runs_the_driver_schedule(steps, warmup):
     assert tiles["tune_ms"] == 1.5
     assert tiles["tiles"]["gram"] == {"64x64": 2 * (23 + 47 + 63)}
     assert tiles["tiles"]["contract_simt"] == {"64x64": 22 + 46 + 62}
+
+
+def test_work_model_follows_the_gram_side_rule():
+    """The bench's algorithmic-work model picks the split's Gram side as the
+    library does: the smaller Gram where the site capacities around the pair
+    differ, else the side that leaves the centre next to the following gate.
+    On a saturated n=24, chi=128 state the eigensolver work of an ascending
+    layer is then sum_q (2/3) min(2 cap_q, 2 cap_q+2)^3."""
+    n, chi = 24, 128
+    cap = [min(chi, 2 ** min(k, n - k)) for k in range(n + 1)]
+    asc = list(range(0, n - 1, 2))
+    sides = bench.split_sides(asc, n, chi)
+    assert sides == [q < 16 for q in asc]
+    desc = list(range(1, n - 1, 2))[::-1]
+    assert bench.split_sides(desc, n, chi) == [q < 7 for q in desc]
+    w = bench.layer_work(asc, cap, chi)
+    expect = sum((2.0 / 3.0) * min(2 * cap[q], 2 * cap[q + 2]) ** 3 for q in asc)
+    assert abs(w["eig"] - expect) <= 1e-12 * expect
