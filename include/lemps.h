@@ -25,6 +25,11 @@
  *    Philox4x64-10(counter = (t, g, s, 0), key = (seed, 0x4C454D5053545241)),
  *    first output word >> 11, times 2^-53.  Results therefore do not depend on
  *    how trajectories are batched or sharded (traj_offset).
+ *  - Runs are deterministic: each trajectory is computed by its own thread
+ *    blocks with a fixed order of operations (the eigensolver's shared sums
+ *    are exact fixed-point integer adds), so the same configuration and calls
+ *    give the same results bit for bit, whatever the batch, the wave size or
+ *    the GEMM tile setting.
  */
 #ifndef LEMPS_H
 #define LEMPS_H

@@ -609,6 +609,31 @@ def test_autotuner_reuses_its_record(L):
         assert {tuple(x) for x in ta[kind]} <= set(TILE_SHAPES["fp64"])
 
 
+@pytest.mark.slow
+def test_runs_are_deterministic_at_chi128(L):
+    """At the benchmark's bond dimension (chi = 128, Gram matrices of 256, so
+    the eigensolver runs both its blocked and its packed phase) a run is
+    reproducible bit for bit: two handles with the same configuration give
+    the same MPS tensors, observables and error bounds, and so does a handle
+    that holds the same 12 trajectories in three waves (5, 5 and 2)."""
+    circ = I.random_brickwork(16, 12, I.depolarizing_kraus(0.02), seed=8)
+    out = []
+    for wave in (0, 0, 5):
+        sim = L.Simulation(16, 128, 12, seed=4, precision="mixed", max_traj_in_flight=wave)
+        sim.run(circ)
+        res = sim.measure()
+        mps = sim.export_mps(3) if wave == 0 else None
+        sim.destroy()
+        assert res["n_failed"] == 0
+        out.append((res, mps))
+    assert out[0][1][1].max() == 128
+    for res, _ in out[1:]:
+        for key in ("z", "zz", "s_half", "eps_bound", "status"):
+            assert np.array_equal(res[key], out[0][0][key]), key
+    for a, b in zip(out[0][1][0], out[1][1][0]):
+        assert np.array_equal(a, b)
+
+
 # --- edge cases ---------------------------------------------------------------------
 
 def test_two_qubits_single_trajectory(L):
