@@ -101,7 +101,12 @@ typedef void (*lemps_free_fn)(void* ptr, size_t bytes, void* stream, void* ctx);
 
 typedef struct {
   int32_t n_qubits;       /* >= 2 */
-  int32_t chi_max;        /* maximum bond dimension, 1..128 */
+  int32_t chi_max;        /* maximum bond dimension, 1..512 (above 128 the
+                             centre moves and eigensolves of sites whose
+                             capacity exceeds 128 run unblocked kernels that
+                             keep their matrices in global memory: Gram
+                             matrices up to 1024; sample_bitstrings then needs
+                             chi_max <= 256) */
   double trunc_cutoff;    /* keep Schmidt weights > cutoff * total (Sec. II truncation) */
   int64_t n_traj;         /* trajectories held by this handle */
   int64_t traj_offset;    /* global id of the handle's first trajectory */
@@ -134,6 +139,11 @@ typedef struct {
                              complex128 64x64, 32x64, 64x32, 32x32; complex64
                              64x64, 128x64, 64x128, 32x32.  Every shape gives
                              the same results bit for bit */
+  int32_t big_kernels;    /* 0 = the centre moves and eigensolves run the
+                             global-memory kernels only where a site capacity
+                             exceeds 128 (their on-chip counterparts stop
+                             there); 1 = everywhere (slower; a check of those
+                             kernels against the oracle on small cases) */
 } lemps_config;
 
 typedef struct {
@@ -224,7 +234,7 @@ lemps_status sim_waves(lemps_handle h, int64_t* wave_size, int32_t* n_waves);
  * Random numbers: Philox counter (trajectory id, 2^62 + shot, site, 0), a
  * domain the noise sites never use.  Moves the orthogonality centre to site
  * 0; keeps one device buffer of the largest request (through the handle's
- * allocator); synchronizes the stream. */
+ * allocator); synchronizes the stream.  LEMPS_EINVAL when chi_max > 256. */
 lemps_status sample_bitstrings(lemps_handle h, int32_t n_shots, uint8_t* bits_out);
 
 /* Concentration-improved error bound (Sec. III.C; appendix on concentration
@@ -310,7 +320,7 @@ lemps_status unravel_grad_noalloc(const void* theta, int32_t theta_fp64, int64_t
  * Autotuning (gemm_tile = 0): for each kernel and each distinct triple of site
  * capacities (cap_q, cap_q+1, cap_q+2), sim_create times every candidate
  * shape on min(n_traj, 2 x the SM count) trajectories with every bond at its
- * capacity and zero operands (one warm-up and three timed launches, CUDA events
+ * capacity (capacity triples up to 128; larger ones keep 64x64) and zero operands (one warm-up and three timed launches, CUDA events
  * on the handle's stream, before the state is initialized) and keeps the
  * fastest; the default 64x64 stays unless another shape is at least 3 % faster.
  * The choice is kept per device and precision for the life of the process, so

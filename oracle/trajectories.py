@@ -44,6 +44,10 @@ class TrajectoryRecord:
     # the squared Schmidt values at the cut (MPS only): the conditioning of
     # the kept subspace, which moves by about (perturbation / gap)
     cut_gaps: List[float] = dataclasses.field(default_factory=list)
+    # worst-case change of the state when a split is computed from the Gram
+    # matrix with unit roundoff u instead of by SVD, summed over the splits:
+    # {u: bound} for u = 2^-53 and 2^-24 (MPS only; see gram_route_bound)
+    gram_bound: dict = dataclasses.field(default_factory=dict)
     z: np.ndarray = None       # <Z_i>
     zz: np.ndarray = None      # <Z_i Z_{i+1}>
     s_half: float = 0.0        # entropy of bond n/2 (nats)
@@ -272,6 +276,30 @@ def _svd(a, **kw):
         return sla.svd(a, lapack_driver="gesvd", **kw)
 
 
+GRAM_UNITS = (2.0 ** -53, 2.0 ** -24)
+
+
+def gram_route_bound(w, keep, ng, u):
+    """Worst-case norm of the change of a truncated split (Eq.
+    MPS_truncation_error keeps the top chi' squared Schmidt values w) when
+    the split comes from a Hermitian eigensolve of the n_g x n_g Gram matrix
+    in arithmetic of unit roundoff u instead of from the SVD.  The Gram
+    route perturbs the squared values by about tau = n_g u w_1, so (i) kept
+    values below tau are not resolved at all: their vectors may turn
+    completely, moving the state by up to sqrt(their weight); (ii) where the
+    cut itself lies above tau, the kept subspace turns by at most tau / (w_chi'
+    - w_chi'+1) (Davis-Kahan), moving the state by that times sqrt(w_chi').
+    Weights are relative to sum w."""
+    r = np.asarray(w, dtype=float) / float(np.sum(w))
+    tau = ng * u * r[0]
+    kept = r[:keep]
+    b = math.sqrt(float(np.sum(kept[kept < tau])))
+    if keep < len(r) and r[keep - 1] >= tau:
+        gap = r[keep - 1] - r[keep]
+        b += math.sqrt(r[keep - 1]) * min(1.0, tau / gap if gap > 0 else 1.0)
+    return b
+
+
 def _split(m, q, th, cap, cutoff, rec):
     """SVD split of the pair (Eq. MPS_truncation_error): keep
     chi' = min(cap, #{s_k^2 > cutoff * sum s^2}) values, renormalize, centre on
@@ -286,6 +314,8 @@ def _split(m, q, th, cap, cutoff, rec):
     rec.discarded.append(eps)
     if keep < len(w):
         rec.cut_gaps.append(float((w[keep - 1] - w[keep]) / w[0]))
+    for unit in GRAM_UNITS:
+        rec.gram_bound[unit] = rec.gram_bound.get(unit, 0.0) + gram_route_bound(w, keep, 2 * max(dl, dr), unit)
     kept = math.sqrt(np.sum(w[:keep]))
     m.a[q] = u[:, :keep].reshape(dl, 2, keep)
     m.a[q + 1] = (s[:keep, None] * vh[:keep, :] / kept).reshape(keep, 2, dr)

@@ -4,6 +4,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <array>
 #include <chrono>
 #include <cmath>
@@ -15,6 +16,7 @@
 #include <vector>
 
 #include "../../include/lemps.h"
+#include "big_kernels.cuh"
 #include "mps_kernels.cuh"
 #include "unravel_iface.h"
 
@@ -252,8 +254,24 @@ void reset_wave(lemps_sim* h, int w) {
   else k_init_state<float><<<(unsigned)h->B, 64, 0, h->stream>>>(h->view<float>());
 }
 
+// Centre moves and eigensolves whose matrices exceed the on-chip kernels
+// (site capacities above 128) run the global-memory kernels of big_kernels.cuh.
+bool big_move(const lemps_sim* h, int k) {
+  return h->cfg.big_kernels || std::max(h->cap_h[k], h->cap_h[k + 1]) > 128;
+}
+bool big_gram(const lemps_sim* h, int q, int mode) {
+  const int n = mode == 0 ? 2 * h->cap_h[q] : (mode == 1 ? 2 * h->cap_h[q + 2] : h->cap_h[q + 1]);
+  return h->cfg.big_kernels || n > 256;
+}
+
 template <class R>
 void launch_move(lemps_sim* h, int k, int dir) {
+  if (big_move(h, k)) {
+    h->timed(LEMPS_K_MOVE, [&] {
+      k_move_center_big<R><<<(unsigned)h->B, kThreads, BigMoveSmem<R>::kBytes, h->stream>>>(h->view<R>(), k, dir);
+    });
+    return;
+  }
   const size_t smem = sizeof(QrSmem<R>);
   static bool attr = false;  // one opt-in per instantiation
   if (!attr) {
@@ -291,9 +309,28 @@ void launch_heev_as(lemps_sim* h, const HeevView<double>& v, int q, int mode, do
   });
 }
 
+template <class RB>
+void launch_heev_big(lemps_sim* h, const HeevView<double>& v, int q, int mode, double cutoff, int keep_max,
+                     int vectors) {
+  const size_t smem = sizeof(BigHeevSmem);
+  static bool attr = false;  // one opt-in per instantiation
+  if (!attr) {
+    cudaFuncSetAttribute(k_heev_big<RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    attr = true;
+  }
+  h->timed(LEMPS_K_EIG, [&] {
+    k_heev_big<RB><<<(unsigned)h->B, kBigHeevThreads, smem, h->stream>>>(v, q, mode, cutoff, keep_max, vectors);
+  });
+}
+
 template <class R>
 void launch_heev(lemps_sim* h, int q, int mode, double cutoff, int keep_max, int vectors) {
   const SimView<R> sv = h->view<R>();
+  if (big_gram(h, q, mode)) {
+    if (sv.u_fp64) launch_heev_big<double>(h, heev_view(sv), q, mode, cutoff, keep_max, vectors);
+    else launch_heev_big<float>(h, heev_view(sv), q, mode, cutoff, keep_max, vectors);
+    return;
+  }
   if (sv.u_fp64) launch_heev_as<double>(h, heev_view(sv), q, mode, cutoff, keep_max, vectors);
   else launch_heev_as<float>(h, heev_view(sv), q, mode, cutoff, keep_max, vectors);
 }
@@ -348,6 +385,8 @@ std::map<std::array<int, 7>, int> g_tile_record;
 // their capacities (operands zeroed; values do not change the timing): one
 // warm-up launch, then three launches between CUDA events on the handle's
 // stream.  The fastest is kept if it beats the default 64 x 64 by 3 %.
+// Capacity triples above 128 keep the default: there one timing launch of a
+// complex128 Gram product can take half a second.
 // All candidates compute the same results bit for bit (each output entry is
 // accumulated over k in order), so the choice only affects speed.
 template <class R>
@@ -369,13 +408,14 @@ lemps_status autotune_tiles(lemps_sim* h) {
   auto key_of = [&](int kind, int q) {
     return std::array<int, 7>{dev, h->prec, kind, Bt >= sms ? 1 : 0, h->cap_h[q], h->cap_h[q + 1], h->cap_h[q + 2]};
   };
+  auto tuned = [&](int q) { return std::max(h->cap_h[q], std::max(h->cap_h[q + 1], h->cap_h[q + 2])) <= 128; };
   std::vector<std::pair<int, int>> todo;   // (kind, first position) of each key still to time
   {
     std::lock_guard<std::mutex> lk(g_tile_mu);
     std::map<std::array<int, 7>, int> seen;
     for (int kind = 0; kind < 3; ++kind)
       for (int q = 0; q < np; ++q) {
-        if (h->tiles[(size_t)kind * np + q] < 0) continue;
+        if (h->tiles[(size_t)kind * np + q] < 0 || !tuned(q)) continue;
         const auto key = key_of(kind, q);
         if (g_tile_record.count(key) || seen.count(key)) continue;
         seen[key] = 1;
@@ -432,7 +472,7 @@ lemps_status autotune_tiles(lemps_sim* h) {
   for (int kind = 0; kind < 3; ++kind)
     for (int q = 0; q < np; ++q) {
       int8_t& t = h->tiles[(size_t)kind * np + q];
-      if (t >= 0) t = (int8_t)g_tile_record.at(key_of(kind, q));
+      if (t >= 0 && tuned(q)) t = (int8_t)g_tile_record.at(key_of(kind, q));
     }
   return LEMPS_OK;
 }
@@ -661,7 +701,7 @@ lemps_status sim_create(const lemps_config* cfg, lemps_handle* out) {
   if (!cfg || !out) return fail(LEMPS_EINVAL, "sim_create: null argument");
   *out = nullptr;
   if (cfg->n_qubits < 2 || cfg->n_qubits > 4096) return fail(LEMPS_EINVAL, "sim_create: n_qubits out of range");
-  if (cfg->chi_max < 1 || cfg->chi_max > 128) return fail(LEMPS_EINVAL, "sim_create: chi_max must be in 1..128");
+  if (cfg->chi_max < 1 || cfg->chi_max > 512) return fail(LEMPS_EINVAL, "sim_create: chi_max must be in 1..512");
   if (cfg->n_traj < 1) return fail(LEMPS_EINVAL, "sim_create: n_traj must be positive");
   if (cfg->precision != LEMPS_FP64 && cfg->precision != LEMPS_MIXED) return fail(LEMPS_EINVAL, "sim_create: bad precision");
   if (cfg->unravel_mode != LEMPS_UNRAVEL_OPTIMAL && cfg->unravel_mode != LEMPS_UNRAVEL_GIVEN &&
@@ -675,6 +715,7 @@ lemps_status sim_create(const lemps_config* cfg, lemps_handle* out) {
   if ((cfg->alloc == nullptr) != (cfg->free == nullptr)) return fail(LEMPS_EINVAL, "sim_create: alloc and free go together");
   if (cfg->max_traj_in_flight < 0) return fail(LEMPS_EINVAL, "sim_create: max_traj_in_flight must be >= 0");
   if (cfg->eigvec_fp64 != 0 && cfg->eigvec_fp64 != 1) return fail(LEMPS_EINVAL, "sim_create: eigvec_fp64 must be 0 or 1");
+  if (cfg->big_kernels != 0 && cfg->big_kernels != 1) return fail(LEMPS_EINVAL, "sim_create: big_kernels must be 0 or 1");
   if (cfg->gemm_tile < 0 || cfg->gemm_tile > kNumGemmTiles)
     return fail(LEMPS_EINVAL, "sim_create: gemm_tile must be 0 (autotune) or 1..4");
   lemps_sim* h = new lemps_sim();
@@ -893,6 +934,7 @@ lemps_status sample_bitstrings(lemps_handle h, int32_t n_shots, uint8_t* bits_ou
   if (!h || !bits_out || n_shots < 1 || n_shots > 65535) return fail(LEMPS_EINVAL, "sample_bitstrings: bad argument");
   if (h->n_waves > 1) return fail(LEMPS_ESTATE, "sample_bitstrings: the handle runs in waves; per-trajectory inspection needs n_traj <= max_traj_in_flight");
   if (h->sticky) return fail(LEMPS_ECUDA, "sample_bitstrings: sticky CUDA error");
+  if (h->cap_max > 256) return fail(LEMPS_EINVAL, "sample_bitstrings: bond dimensions above 256 are not supported");
   const size_t bytes = (size_t)h->B * (size_t)n_shots * (size_t)h->n;
   if (bytes > h->bits_cap) {
     uint8_t* p = (uint8_t*)h->dalloc(bytes);

@@ -45,7 +45,7 @@ class Config(ctypes.Structure):
                 ("eps_max", ctypes.c_double), ("cuda_stream", ctypes.c_void_p), ("alloc", ALLOC_FN),
                 ("free", FREE_FN), ("alloc_ctx", ctypes.c_void_p), ("layering", ctypes.c_int32),
                 ("max_traj_in_flight", ctypes.c_int64), ("eigvec_fp64", ctypes.c_int32),
-                ("gemm_tile", ctypes.c_int32)]
+                ("gemm_tile", ctypes.c_int32), ("big_kernels", ctypes.c_int32)]
 
 
 class LayerStruct(ctypes.Structure):
@@ -130,7 +130,7 @@ class Simulation:
                  unravel: str = "optimal", cutoff: Optional[float] = None, traj_offset: int = 0,
                  log_capacity: int = 0, eps_max: float = 4.0, stream=None, torch_allocator: bool = True,
                  layering: str = "local", max_traj_in_flight: int = 0, eigvec_fp64: bool = False,
-                 gemm_tile: int = 0):
+                 gemm_tile: int = 0, big_kernels: bool = False):
         torch = _require_cuda()
         lib = load()
         self.n, self.chi, self.B = int(n_qubits), int(chi_max), int(n_traj)
@@ -153,6 +153,7 @@ class Simulation:
         cfg.max_traj_in_flight = int(max_traj_in_flight)
         cfg.eigvec_fp64 = 1 if eigvec_fp64 else 0
         cfg.gemm_tile = int(gemm_tile)
+        cfg.big_kernels = 1 if big_kernels else 0
         cfg.cuda_stream = self.stream.cuda_stream
         self._cb = None
         if torch_allocator:

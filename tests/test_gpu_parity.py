@@ -34,10 +34,10 @@ def L():
 
 
 def run_gpu(L, circ, chi, n_traj, seed, precision="fp64", unravel="optimal", cutoff=None, traj_offset=0,
-            layering="local", eigvec_fp64=False):
+            layering="local", eigvec_fp64=False, big_kernels=False):
     sim = L.Simulation(circ.n_qubits, chi, n_traj, seed=seed, precision=precision, unravel=unravel,
                        cutoff=cutoff, log_capacity=circ.n_gates, traj_offset=traj_offset, layering=layering,
-                       eigvec_fp64=eigvec_fp64)
+                       eigvec_fp64=eigvec_fp64, big_kernels=big_kernels)
     sim.run(circ)
     res = sim.measure()
     branches = np.zeros((n_traj, 2 * circ.n_gates), dtype=np.int32)
@@ -671,6 +671,13 @@ def test_invalid_inputs_are_rejected(L):
     sim.destroy()
     with pytest.raises(L.LempsError):
         L.Simulation(4, 0, 2)
+    with pytest.raises(L.LempsError):
+        L.Simulation(4, 513, 2)
+    big = L.Simulation(20, 512, 1)
+    with pytest.raises(L.LempsError) as e:
+        big.sample_bitstrings(1)   # the sampler holds bonds of at most 256
+    assert e.value.status == L.LEMPS_EINVAL
+    big.destroy()
 
 
 # --- differentiation --------------------------------------------------------------------
@@ -911,3 +918,145 @@ def test_mixed_and_fp64_means_agree_within_3_se(L, config):
     z = _mean_z_scores(out["mixed"], out["fp64"])
     print(f"{config}: |z| max {np.abs(z).max():.3e}, median {np.median(np.abs(z)):.3e} over {z.size} observables")
     assert np.all(np.abs(z) < 3.0), z
+
+
+# --- bond dimensions above 128 (chi_max up to 512) --------------------------------------
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_global_memory_kernels_match_oracle(L, precision):
+    """The global-memory eigensolver and QR centre move, which run where a site
+    capacity exceeds 128, forced at every size (big_kernels = 1) on the
+    truncated chi = 4 run of test_truncated_run_matches_oracle_mps: the same
+    branch sequences and the same bars (FP64 1e-10, mixed mixed_tol)."""
+    circ = I.random_brickwork(10, 10, I.depolarizing_kraus(0.05), seed=4)
+    n_traj = 16
+    sim, res, br = run_gpu(L, circ, 4, n_traj, seed=3, precision=precision, cutoff=1e-14, big_kernels=True)
+    sim.destroy()
+    for t in range(n_traj):
+        ref = T.mps_trajectory(circ, t, 3, chi_max=4, cutoff=1e-14)
+        assert list(br[t]) == ref.branch, t
+        tol = 1e-10 if precision == "fp64" else mixed_tol(ref)
+        assert close(res["z"][t], ref.z, tol), t
+        assert close(res["zz"][t], ref.zz, tol), t
+        assert close(res["s_half"][t], ref.s_half, tol), t
+        assert abs(res["eps_bound"][t] - ref.eps_bound) <= bound_tol(ref.eps_bound, precision), t
+
+
+@pytest.mark.slow
+def test_global_memory_kernels_at_chi128(L):
+    """The global-memory kernels forced on the chi = 128 benchmark circuit (the
+    n = 48 circuit of the uneven workload, 14 layers, Gram matrices of 256):
+    two FP64 trajectories to 1e-10 and eight mixed ones to 1e-4 against the
+    oracle's FP64 MPS trajectories, as the on-chip kernels are held in
+    test_chi128_workload_sampled_against_oracle."""
+    w = I.workload_uneven(seed=0, n_traj=8, depth=32)
+    full = w["circuits"][48]
+    circ = I.Circuit(full.n_qubits, full.layers[:14])
+    seed = 11
+    for precision, cutoff, n_traj, tol in (("fp64", 1e-20, 2, 1e-10), ("mixed", 1e-12, 8, 1e-4)):
+        sim, res, br = run_gpu(L, circ, 128, n_traj, seed=seed, precision=precision, cutoff=cutoff,
+                               big_kernels=True)
+        _, bonds = sim.export_mps(0)
+        sim.destroy()
+        assert bonds.max() == 128 and res["n_failed"] == 0
+        refs = oracle_mps_many(circ, range(n_traj), seed, 128, cutoff)
+        for t, (branch, z, zz, s_half, eps_bound) in enumerate(refs):
+            assert list(br[t]) == branch, (precision, t)
+            assert close(res["z"][t], z, tol), (precision, t, np.abs(res["z"][t] - z).max())
+            assert close(res["zz"][t], zz, tol), (precision, t)
+            assert close(res["s_half"][t], s_half, tol), (precision, t)
+            assert abs(res["eps_bound"][t] - eps_bound) <= bound_tol(eps_bound, precision), (precision, t)
+
+
+def _oracle_gap_job(args):
+    circ, t, seed, chi, cutoff = args
+    r = T.mps_trajectory(circ, t, seed, chi_max=chi, cutoff=cutoff)
+    return r.branch, r.z, r.zz, r.s_half, r.eps_bound, dict(r.gram_bound)
+
+
+def oracle_jobs(jobs):
+    """Oracle MPS trajectories for (circ, t, seed, chi, cutoff) jobs in a spawn
+    pool, the host's BLAS threads shared out among the jobs."""
+    ctx = multiprocessing.get_context("spawn")
+    keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+    saved = {k: os.environ.get(k) for k in keys}
+    os.environ.update({k: str(max(1, (os.cpu_count() or 1) // len(jobs))) for k in keys})
+    try:
+        with concurrent.futures.ProcessPoolExecutor(min(len(jobs), os.cpu_count() or 1), mp_context=ctx) as ex:
+            return list(ex.map(_oracle_gap_job, jobs))
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+
+
+def entropy_tol(b, d):
+    """Fannes-Audenaert: reduced states of pure states at distance <= b are
+    within trace distance T = min(1, b), so their entropies differ by at most
+    T ln(d - 1) + h(T) (d = Schmidt rank bound)."""
+    tt = min(1.0, b)
+    h = 0.0 if tt in (0.0, 1.0) else -tt * math.log(tt) - (1 - tt) * math.log(1 - tt)
+    return tt * math.log(max(d - 1, 1)) + h
+
+
+LARGE_CHI_CASES = {
+    # Haar brickwork whose middle bonds reach 512: Gram matrices up to 1024
+    "haar_n20_chi512": (lambda: I.random_brickwork(20, 12, I.depolarizing_kraus(0.01), seed=3), 512),
+    # the kicked-Ising family (RZZ(pi/4 + noise), RX kicks, two-qubit
+    # depolarizing p = 0.01) at n = 20, 22 periods: bonds truncated at 256
+    "kicked_ising_n20_chi256": (lambda: I.kicked_ising(20, 22, I.depolarizing_kraus(1.0), 0.01, seed=2), 256),
+}
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("case", list(LARGE_CHI_CASES))
+def test_large_bond_dimensions_against_oracle(L, case):
+    """chi_max above 128 (the global-memory eigensolver with Gram matrices up to
+    1024 and the global-memory QR): two trajectories per precision against the
+    oracle's FP64 MPS trajectories with the same cutoff.  Identical branch
+    sequences.  FP64: observables within the worst-case change of a split
+    computed from the Gram matrix instead of by SVD, summed over the splits
+    (the oracle's gram_bound for unit roundoff 2^-53: unresolved kept weight
+    and Davis-Kahan at the cut): 2 b for <Z>, <ZZ> and the error bound, the
+    Fannes-Audenaert bound for S(n/2), never below 1e-10.  Mixed: the same
+    bound for 2^-24 exceeds 1 here, so the observables are held to the mixed
+    target of 1e-4 per trajectory (the error bound to the Gram-route bound).
+    The FP64 bounds are loose (the errors printed are far below them); the
+    global-memory kernels are held to the strict bars in
+    test_global_memory_kernels_match_oracle and _at_chi128."""
+    make, chi = LARGE_CHI_CASES[case]
+    circ = make()
+    seed = 5
+    cuts = {"fp64": 1e-20, "mixed": 1e-12}
+    units = {"fp64": 2.0 ** -53, "mixed": 2.0 ** -24}
+    floors = {"fp64": 1e-10, "mixed": 1e-4}
+    jobs = [(circ, t, seed, chi, cuts[p]) for p in ("fp64", "mixed") for t in range(2)]
+    refs = oracle_jobs(jobs)
+    refs = {"fp64": refs[:2], "mixed": refs[2:]}
+    out = {}
+    for precision in ("fp64", "mixed"):
+        sim, res, br = run_gpu(L, circ, chi, 2, seed=seed, precision=precision, cutoff=cuts[precision])
+        _, bonds = sim.export_mps(0)
+        sim.destroy()
+        assert res["n_failed"] == 0
+        assert bonds.max() > 128, bonds
+        for t, (branch, z, zz, s_half, eps_bound, gb) in enumerate(refs[precision]):
+            assert list(br[t]) == branch, (precision, t)
+            b = gb[units[precision]]
+            if precision == "fp64":
+                tol_o = max(floors[precision], 2 * b)
+                tol_s = max(floors[precision], entropy_tol(b, chi))
+            else:
+                tol_o = tol_s = 1e-4
+            err = max(np.abs(res["z"][t] - z).max(), np.abs(res["zz"][t] - zz).max())
+            assert err <= tol_o, (precision, t, err, tol_o)
+            assert abs(res["s_half"][t] - s_half) <= tol_s, (precision, t, res["s_half"][t] - s_half, tol_s)
+            assert abs(res["eps_bound"][t] - eps_bound) <= max(bound_tol(eps_bound, precision), 2 * b)
+            print(f"{case} {precision} traj {t}: max bond {bonds.max()}, <Z>/<ZZ> error {err:.2e} (bound {tol_o:.1e}), "
+                  f"S error {abs(res['s_half'][t] - s_half):.2e} (bound {tol_s:.1e})")
+        out[precision] = res
+    mid = circ.n_qubits // 2
+    for p in ("mixed", "fp64"):
+        print(f"{case} {p}: <Z_{mid}> {out[p]['z'][:, mid]}, S(n/2) {out[p]['s_half']}")

@@ -379,3 +379,52 @@ def test_svd_fallback_gives_the_same_decomposition(monkeypatch):
     assert np.allclose((u * s) @ vh, a, atol=1e-12)
     assert np.allclose(u.conj().T @ u, np.eye(24), atol=1e-12)
     assert np.allclose(T._svd(a, compute_uv=False), ref, atol=1e-12)
+
+
+# --- the Gram-route bound recorded for the large-bond-dimension tests ----------------
+
+def test_gram_route_bound_closed_forms():
+    """gram_route_bound: zero when every kept value is resolved and nothing is
+    cut; sqrt of the unresolved kept weight; the Davis-Kahan term tau / gap
+    times sqrt(w_chi') at a resolved cut; a full turn (sqrt(w_chi')) when the
+    cut falls between equal values."""
+    u = 2.0 ** -53
+    assert T.gram_route_bound([3.0, 1.0], 2, 4, u) == 0.0
+    w = np.array([1.0, 1e-18, 1e-19])
+    assert math.isclose(T.gram_route_bound(w, 3, 4, u), math.sqrt((1e-18 + 1e-19) / w.sum()), rel_tol=1e-12)
+    w = np.array([1.0, 0.5, 1e-20])
+    r = w / w.sum()
+    tau = 4 * u * r[0]
+    assert math.isclose(T.gram_route_bound(w, 2, 4, u), math.sqrt(r[1]) * tau / (r[1] - r[2]), rel_tol=1e-12)
+    w = np.array([1.0, 0.25, 0.25])
+    assert math.isclose(T.gram_route_bound(w, 2, 4, u), math.sqrt(0.25 / 1.5), rel_tol=1e-12)
+
+
+def test_gram_route_bound_holds_for_a_perturbed_gram_matrix(rng):
+    """Davis-Kahan, checked: a two-site matrix Theta with a chosen spectrum
+    (a resolved cut with a modest gap), its Gram matrix perturbed by a random
+    Hermitian E of norm tau = n_g u ||G|| with u = 2^-24, the top chi' vectors
+    of the perturbed matrix kept: the truncated state moves by no more than
+    the bound (and by a visible amount, so the check is not vacuous)."""
+    n, keep, u = 16, 6, 2.0 ** -24
+    s = np.sqrt(np.concatenate([np.linspace(1.0, 0.3, keep), [0.3 - 2e-5], np.linspace(0.1, 0.01, n - keep - 1)]))
+    qa, _ = np.linalg.qr(rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)))
+    qb, _ = np.linalg.qr(rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)))
+    th = (qa * s) @ qb.conj().T
+    th /= np.linalg.norm(th)
+    g = th @ th.conj().T
+    w = np.sort(np.linalg.eigvalsh(g))[::-1]
+    tau = n * u * w[0]
+    e = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    e = e + e.conj().T
+    e *= tau / np.linalg.norm(e, 2)
+
+    def truncated(mat):
+        vals, vecs = np.linalg.eigh(mat)
+        p = vecs[:, ::-1][:, :keep]
+        return p @ (p.conj().T @ th)
+
+    moved = np.linalg.norm(truncated(g + e) - truncated(g))
+    bound = T.gram_route_bound(w, keep, n, u)
+    assert 0 < moved <= bound, (moved, bound)
+    assert moved > 1e-3 * bound
