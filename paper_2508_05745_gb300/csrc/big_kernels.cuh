@@ -36,8 +36,10 @@ struct BigHeevSmem {
 // U (column-major n x keep, cpx<RB>) at the start of the trajectory's ws2
 // slot; the reflectors (sqrt(2) v_j in row j, in cpx<RB>) go to ws3.
 //  1. Householder tridiagonalization in FP64, one column per step: v from the
-//     column below the diagonal, y = A v by one warp per row, w = 2 (y - (v^H
-//     y) v), A <- A - v w^H - w v^H on the whole trailing block.
+//     column below the diagonal, y = A v by one warp per row (the lower
+//     triangle read along the row, the upper part as the conjugate of the
+//     lower triangle's column), w = 2 (y - (v^H y) v), A <- A - v w^H - w v^H
+//     on the lower triangle of the trailing block only.
 //  2. Phases D with T_real = D^H T D real (|e_j| off the diagonal).
 //  3. Each kept eigenvalue by bisection on Sturm counts of T_real / ||T||
 //     (one thread per eigenvalue) to 4 eps ||T||.
@@ -115,11 +117,15 @@ __global__ void __launch_bounds__(kBigHeevThreads) k_heev_big(HeevView<double> s
       __syncthreads();
       continue;
     }
-    // y = A v over the trailing block (rows and columns j+1 .. n-1)
+    // y = A v over the trailing block (rows and columns j+1 .. n-1); only the
+    // lower triangle is current: A[r][c] for c <= r along row r, conj(A[c][r])
+    // for c > r down column r
     for (int r = warp; r < m; r += nwarp) {
       const zd* row = G + (int64_t)(j + 1 + r) * n + (j + 1);
+      const zd* colr = G + (int64_t)(j + 1) * n + (j + 1 + r);   // A[c][r] at colr[c * n]
       zd acc = mk(0.0, 0.0);
-      for (int c = lane; c < m; c += 32) cfma(acc, row[c], sm.v[c]);
+      for (int c = lane; c <= r; c += 32) cfma(acc, row[c], sm.v[c]);
+      for (int c = r + 1 + lane; c < m; c += 32) cfmac(acc, colr[(int64_t)c * n], sm.v[c]);
       acc.re = warp_sum(acc.re);
       acc.im = warp_sum(acc.im);
       if (lane == 0) sm.y[r] = acc;
@@ -134,7 +140,7 @@ __global__ void __launch_bounds__(kBigHeevThreads) k_heev_big(HeevView<double> s
     for (int r = warp; r < m; r += nwarp) {
       zd* row = G + (int64_t)(j + 1 + r) * n + (j + 1);
       const zd vr = sm.v[r], wr = sm.w[r];
-      for (int c = lane; c < m; c += 32) row[c] = rank2_sub(row[c], vr, sm.w[c], wr, sm.v[c]);
+      for (int c = lane; c <= r; c += 32) row[c] = rank2_sub(row[c], vr, sm.w[c], wr, sm.v[c]);
     }
     __syncthreads();
   }
