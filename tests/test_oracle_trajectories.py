@@ -428,3 +428,38 @@ def test_gram_route_bound_holds_for_a_perturbed_gram_matrix(rng):
     bound = T.gram_route_bound(w, keep, n, u)
     assert 0 < moved <= bound, (moved, bound)
     assert moved > 1e-3 * bound
+
+
+def test_kicked_ising_gates_and_folding():
+    """The kicked-Ising circuit family (the chi_max = 512 workload): RZZ(theta)
+    = exp(-i theta/2 Z(x)Z) and RX(phi) = exp(-i phi/2 X) against matrix
+    exponentials of their generators; and, without noise (coin 0), the circuit
+    with each period's RX kicks folded into the next period's even-bond RZZ
+    gates (the last period's kicks as a final layer of RX (x) RX) prepares the
+    same state as the periods applied as written, RZZ on the even bonds, on the
+    odd bonds, then RX on every qubit, with the same angles."""
+    from scipy.linalg import expm
+    zz = np.kron(np.diag([1.0, -1.0]), np.diag([1.0, -1.0]))
+    x = np.array([[0.0, 1.0], [1.0, 0.0]])
+    for th in (0.3, math.pi / 4, -1.1):
+        assert np.allclose(I.rzz(th), expm(-0.5j * th * zz), atol=1e-14)
+        assert np.allclose(I.rx(th), expm(-0.5j * th * x), atol=1e-14)
+    n, depth, seed = 6, 3, 7
+    circ = I.kicked_ising(n, depth, I.depolarizing_kraus(1.0), 0.0, seed)
+    assert len(circ.layers) == 2 * depth + 1 and circ.layers[-1].coin_p == 0.0
+    psi = np.zeros(2 ** n, complex)
+    psi[0] = 1.0
+    for layer in circ.layers:
+        for q, g in zip(layer.left_qubits, layer.gates):
+            psi = T.apply_2q(psi, g, int(q), n)
+    # the same angles, drawn in the generator's order, applied as written
+    rng = np.random.default_rng(np.random.SeedSequence([seed, 0x4B49, n, depth]))
+    ref = np.zeros(2 ** n, complex)
+    ref[0] = 1.0
+    for _ in range(depth):
+        for sub in range(2):
+            for q in I.brickwork_bonds(n, sub):
+                ref = T.apply_2q(ref, I.rzz(math.pi / 4 + 0.05 * rng.standard_normal()), int(q), n)
+        for q in range(n):
+            ref = T.apply_1q(ref, I.rx(rng.uniform(0.0, math.pi)), q, n)
+    assert np.allclose(psi, ref, atol=1e-12)
